@@ -1,0 +1,182 @@
+"""The oracle: a plain CPU implementation of the MOLC high-order sweep (Sec. 3), in double and binary128.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  It never imports the CUDA library's package, and the library never imports it.
+
+``build()`` compiles ``molc_oracle.cpp`` with g++ into ``oracle/_build/``; everything else is ctypes glue
+that hands numpy arrays to the C++ code and returns numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import platform
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "molc_oracle.cpp")
+_OUT = os.path.join(_HERE, "_build", "libmolc_oracle.so")
+_lib = None
+
+MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy", "Nzz", "absFx", "absFy", "absNxy")
+PREC = {"double": 0, "quad": 1}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (g++, -O2, IEEE arithmetic; libquadmath on x86-64)."""
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", _OUT + ".tmp", _SRC]
+    if platform.machine() in ("x86_64", "AMD64"):
+        cmd.append("-lquadmath")
+    subprocess.run(cmd, check=True)
+    os.replace(_OUT + ".tmp", _OUT)
+    return _OUT
+
+
+class _Geom(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("lx", C.c_double), ("ly", C.c_double), ("ndir", C.c_int),
+                ("mu", C.POINTER(C.c_double)), ("cos_phi", C.POINTER(C.c_double)),
+                ("sin_phi", C.POINTER(C.c_double)), ("w", C.POINTER(C.c_double)),
+                ("spacing", C.c_double), ("layout", C.c_int), ("renorm", C.c_int)]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        i64p = C.POINTER(C.c_int64)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        lib.oracle_count.argtypes = [C.POINTER(_Geom), i64p]
+        lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp]
+        lib.oracle_sweep.argtypes = [C.POINTER(_Geom), C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
+                                     ip, C.c_int, dp, dp, dp, C.c_int]
+        for f in (lib.oracle_count, lib.oracle_tracks, lib.oracle_sweep):
+            f.restype = C.c_int
+        lib.oracle_real_bits.argtypes = [C.c_int]
+        lib.oracle_real_bits.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+@dataclass
+class Geometry:
+    """Material grid, angular quadrature and characteristic-grid rule."""
+    nx: int
+    ny: int
+    lx: float
+    ly: float
+    mu: np.ndarray
+    cos_phi: np.ndarray
+    sin_phi: np.ndarray
+    w: np.ndarray
+    spacing: float
+    layout: int = 0          # 0 uniform parallel rays, 1 the paper's vertex bands halved to <= spacing
+    renorm: int = 1
+    x0: float = 0.0
+    y0: float = 0.0
+
+    def _c(self):
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (self.mu, self.cos_phi, self.sin_phi,
+                                                                            self.w)]
+        return _Geom(self.nx, self.ny, self.x0, self.y0, self.lx, self.ly, int(self.mu.size),
+                     *[_dp(a) for a in self._keep], self.spacing, self.layout, self.renorm)
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny
+
+    @classmethod
+    def from_workload(cls, wl, quad=None, spacing=None, layout=0, renorm=1):
+        q = quad if quad is not None else wl.quadrature()
+        return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w,
+                   wl.spacing if spacing is None else spacing, layout, renorm)
+
+
+def counts(geom: Geometry):
+    """(characteristics, segments), both summed over directions."""
+    lib = _load()
+    g = geom._c()
+    out = np.zeros(2, dtype=np.int64)
+    rc = lib.oracle_count(C.byref(g), out.ctypes.data_as(C.POINTER(C.c_int64)))
+    if rc:
+        raise RuntimeError(f"oracle_count failed ({rc})")
+    return int(out[0]), int(out[1])
+
+
+def tracks(geom: Geometry, precision: str = "quad") -> dict:
+    """The characteristic grid in canonical order (direction, characteristic by offset, segment)."""
+    lib = _load()
+    nr, ns = counts(geom)
+    g = geom._c()
+    d = dict(dir_ray_off=np.zeros(geom.mu.size + 1, np.int64), ray_seg_off=np.zeros(nr + 1, np.int64),
+             width=np.zeros(nr), entry=np.zeros(nr, np.int32), cell=np.zeros(ns, np.int32), len=np.zeros(ns),
+             area=np.zeros(ns))
+    i64 = C.POINTER(C.c_int64)
+    ip = C.POINTER(C.c_int)
+    rc = lib.oracle_tracks(C.byref(g), PREC[precision], d["dir_ray_off"].ctypes.data_as(i64),
+                           d["ray_seg_off"].ctypes.data_as(i64), _dp(d["width"]), d["entry"].ctypes.data_as(ip),
+                           d["cell"].ctypes.data_as(ip), _dp(d["len"]), _dp(d["area"]))
+    if rc:
+        raise RuntimeError(f"oracle_tracks failed ({rc})")
+    return d
+
+
+def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
+          want_I=True, want_exit=False, threads=None) -> dict:
+    """One backward-Euler sweep.  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
+    (I^{n-1} = B of the segment's cell).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
+    plus 'I' (canonical [nseg][Gsub] segment averages) and 'I_exit' ([nrays][Gsub]) when asked."""
+    lib = _load()
+    kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    bnd = np.ascontiguousarray(bnd, dtype=np.float64)
+    G = kappa.shape[0]
+    assert kappa.shape == (G, geom.ncell) and B.shape == kappa.shape and bnd.shape == (4, G)
+    gl = None
+    if groups is not None:
+        gl = np.ascontiguousarray(groups, dtype=np.int32)
+    Gsub = G if gl is None else gl.size
+    nr, ns = counts(geom)
+    if I_prev is not None:
+        I_prev = np.ascontiguousarray(I_prev, dtype=np.float64)
+        assert I_prev.shape == (ns, Gsub)
+    out = np.zeros((len(MOMENTS), Gsub, geom.ncell))
+    I_new = np.zeros((ns, Gsub)) if want_I else None
+    I_exit = np.zeros((nr, Gsub)) if want_exit else None
+    g = geom._c()
+    nthreads = threads or max(1, min(os.cpu_count() or 1, 64))
+    rc = lib.oracle_sweep(C.byref(g), PREC[precision], G, _dp(kappa), _dp(B), float(c), float(dt), _dp(bnd),
+                          _dp(I_prev), gl.ctypes.data_as(C.POINTER(C.c_int)) if gl is not None else None,
+                          0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads))
+    if rc:
+        raise RuntimeError(f"oracle_sweep failed ({rc})")
+    res = {k: out[i] for i, k in enumerate(MOMENTS)}
+    if want_I:
+        res["I"] = I_new
+    if want_exit:
+        res["I_exit"] = I_exit
+    return res
+
+
+def closure(E, Nxx, Nxy, Nyy, c):
+    """Eddington factors f = N / (c E) (Eq. 7 / Eq. 15); f_zz = 1 - f_xx - f_yy."""
+    cE = c * np.asarray(E)
+    fxx = np.asarray(Nxx) / cE
+    fxy = np.asarray(Nxy) / cE
+    fyy = np.asarray(Nyy) / cE
+    return fxx, fxy, fyy
+
+
+def real_bits(precision: str) -> int:
+    return _load().oracle_real_bits(PREC[precision])

@@ -1,0 +1,458 @@
+// TEST INFRASTRUCTURE ONLY — the oracle.
+//
+// A plain, slow, CPU-only implementation of the high-order sweep of the method of long characteristics
+// (Coale & Anistratov, "Multilevel method for thermal radiative transfer problems with method of long
+// characteristics for the Boltzmann transport equation", Sec. 3).  Only the tests, the smoke check and the
+// benchmark's CPU-baseline leg may load this library.  It shares no code, header or table with the CUDA
+// library; both sides only consume the same seeded input arrays.
+//
+// Everything is templated on the real type R and instantiated twice: R = double, and R = IEEE binary128
+// (__float128 with libquadmath on x86-64, long double on AArch64).  The binary128 instance is the reference
+// the GPU paths are judged against; the double instance is the timed CPU baseline.
+//
+// What it computes, in the paper's order and notation (Sec. 3):
+//   * characteristic grid: for each direction, parallel characteristics of width w_k, cut into segments at
+//     every crossing with a material-cell boundary; l is the in-plane segment length (Sec. 3, paragraph
+//     on the construction of the characteristic grid; reading: l is measured in the x-y plane and the 3D
+//     path is l / sin(zeta), which is the only reading consistent with Eq. (13));
+//   * per segment: kappa~ = kappa + 1/(c dt), Q = kappa B + I^{n-1}/(c dt)                  (Eq. 11)
+//                  tau = kappa~ l / sin(zeta), alpha = 1/tau - e^-tau / (1 - e^-tau)       (Eq. 13)
+//                  I_{s+1} = I_s e^-tau + (Q/kappa~)(1 - e^-tau), Ibar = alpha I_s + (1-alpha) I_{s+1}  (Eq. 12)
+//                  A = l w                                                                 (Eq. 14)
+//   * cell moments with weights omega_m A: E = (1/c) int I dOmega, F = int Omega I dOmega (Sec. 2, after
+//     Eq. 4) and the Eddington-tensor numerator int Omega Omega I dOmega (Eq. 7 / Eq. 15), all cell averages.
+// Readings where the paper is silent: I^{n-1} in Q is the previous step's segment average on the same
+// segment, direction and group; the cell tensor of Eq. (15) uses the segment average Ibar; each direction
+// with mu > 0 also stands for its mirror through the x-y plane (weights sum to 4 pi).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#if defined(__aarch64__)
+typedef long double real128;  // IEEE binary128 on AArch64 Linux
+static inline real128 q_exp(real128 x) { return expl(x); }
+static inline real128 q_expm1(real128 x) { return expm1l(x); }
+static inline real128 q_sqrt(real128 x) { return sqrtl(x); }
+static inline real128 q_floor(real128 x) { return floorl(x); }
+static inline real128 q_ceil(real128 x) { return ceill(x); }
+#else
+extern "C" {
+#include <quadmath.h>
+}
+typedef __float128 real128;
+static inline real128 q_exp(real128 x) { return expq(x); }
+static inline real128 q_expm1(real128 x) { return expm1q(x); }
+static inline real128 q_sqrt(real128 x) { return sqrtq(x); }
+static inline real128 q_floor(real128 x) { return floorq(x); }
+static inline real128 q_ceil(real128 x) { return ceilq(x); }
+#endif
+
+template <class R> struct Fn;
+template <> struct Fn<double> {
+  static double exp(double x) { return std::exp(x); }
+  static double expm1(double x) { return std::expm1(x); }
+  static double sqrt(double x) { return std::sqrt(x); }
+  static double floor(double x) { return std::floor(x); }
+  static double ceil(double x) { return std::ceil(x); }
+};
+template <> struct Fn<real128> {
+  static real128 exp(real128 x) { return q_exp(x); }
+  static real128 expm1(real128 x) { return q_expm1(x); }
+  static real128 sqrt(real128 x) { return q_sqrt(x); }
+  static real128 floor(real128 x) { return q_floor(x); }
+  static real128 ceil(real128 x) { return q_ceil(x); }
+};
+template <class R> static inline R rabs(R x) { return x < 0 ? -x : x; }
+
+extern "C" {
+// Problem geometry and angular quadrature, as plain arrays (host memory).
+typedef struct {
+  int nx, ny;                 // material cells; cell index = iy * nx + ix
+  double x0, y0, lx, ly;      // domain [x0, x0+lx] x [y0, y0+ly], cm
+  int ndir;                   // directions with mu > 0
+  const double *mu;           // cos(zeta)
+  const double *cos_phi;      // in-plane direction (normalised here)
+  const double *sin_phi;
+  const double *w;            // omega_m, sum 4 pi
+  double spacing;             // h_moc: ray spacing (uniform layout) or maximum width (paper layout)
+  int layout;                 // 0: uniform parallel rays, 1: paper's vertex-band construction
+  int renorm;                 // 1: scale areas so that sum_{C(i,m)} A = V_i
+} oracle_geom;
+}
+
+enum { EDGE_L = 0, EDGE_R = 1, EDGE_B = 2, EDGE_T = 3 };
+
+// One characteristic of one direction.
+template <class R> struct Ray {
+  R width;
+  int entry;                  // edge the characteristic enters through
+  std::vector<int> cell;      // segments in traversal order
+  std::vector<R> len;         // in-plane length l
+  std::vector<R> area;        // A = l w (after optional renormalisation)
+};
+
+template <class R> struct Dir {
+  R dx, dy;                   // unit in-plane direction
+  std::vector<Ray<R>> rays;   // ordered by increasing offset along n = (-dy, dx)
+};
+
+// Offsets t (along the normal n) and widths of the characteristics of one direction.
+template <class R>
+static void characteristic_offsets(const oracle_geom &g, R dx, R dy, std::vector<R> &t, std::vector<R> &w) {
+  const R x0 = g.x0, y0 = g.y0, x1 = R(g.x0) + R(g.lx), y1 = R(g.y0) + R(g.ly);
+  auto proj = [&](R x, R y) { return -dy * x + dx * y; };
+  t.clear();
+  w.clear();
+  if (g.layout == 0) {
+    R c[4] = {proj(x0, y0), proj(x1, y0), proj(x0, y1), proj(x1, y1)};
+    R tmin = c[0], tmax = c[0];
+    for (int i = 1; i < 4; ++i) { tmin = std::min(tmin, c[i]); tmax = std::max(tmax, c[i]); }
+    R Lp = tmax - tmin;
+    long n = (long)Fn<R>::ceil(Lp / R(g.spacing) - R(1e-9));
+    if (n < 1) n = 1;
+    R wk = Lp / R(n);
+    for (long k = 0; k < n; ++k) { t.push_back(tmin + (R(k) + R(0.5)) * wk); w.push_back(wk); }
+    return;
+  }
+  // Paper layout: project every vertex of the material grid onto n; each gap between consecutive distinct
+  // projections is one initial characteristic (it contains no vertex).  Halve until w <= h_moc.
+  const R hx = R(g.lx) / R(g.nx), hy = R(g.ly) / R(g.ny);
+  std::vector<R> v;
+  v.reserve((size_t)(g.nx + 1) * (g.ny + 1));
+  for (int b = 0; b <= g.ny; ++b)
+    for (int a = 0; a <= g.nx; ++a) v.push_back(proj(R(g.x0) + R(a) * hx, R(g.y0) + R(b) * hy));
+  std::sort(v.begin(), v.end());
+  const R Lp = v.back() - v.front();
+  const R merge = R(1e-13) * Lp;
+  std::vector<R> u;
+  for (R x : v)
+    if (u.empty() || x - u.back() > merge) u.push_back(x);
+  for (size_t i = 0; i + 1 < u.size(); ++i) {
+    R gap = u[i + 1] - u[i];
+    long pieces = 1;
+    while (gap / R(pieces) > R(g.spacing)) pieces *= 2;
+    R wk = gap / R(pieces);
+    for (long p = 0; p < pieces; ++p) { t.push_back(u[i] + (R(p) + R(0.5)) * wk); w.push_back(wk); }
+  }
+}
+
+// Cut the line {p : p.n = t} into segments at every crossing with a grid line (Sec. 3).  Crossing
+// parameters closer than eps are one crossing (the characteristic passes through a vertex); the cell of a
+// segment is the cell holding its midpoint.
+template <class R>
+static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
+  const R hx = R(g.lx) / R(g.nx), hy = R(g.ly) / R(g.ny);
+  const R x0 = g.x0, y0 = g.y0, x1 = R(g.x0) + R(g.lx), y1 = R(g.y0) + R(g.ly);
+  const R eps = R(1e-12) * std::min(hx, hy);
+  // p(u) = t n + u d with n = (-dy, dx): x(u) = -t dy + u dx, y(u) = t dx + u dy
+  const R bx = -t * dy, by = t * dx;
+  R ulo = R(-1e300), uhi = R(1e300);
+  R ux = R(-1e300), uy = R(-1e300);
+  if (dx != R(0)) {
+    R a = (x0 - bx) / dx, b = (x1 - bx) / dx;
+    if (a > b) std::swap(a, b);
+    ux = a;
+    ulo = std::max(ulo, a);
+    uhi = std::min(uhi, b);
+  } else if (bx < x0 || bx > x1) {
+    return false;
+  }
+  if (dy != R(0)) {
+    R a = (y0 - by) / dy, b = (y1 - by) / dy;
+    if (a > b) std::swap(a, b);
+    uy = a;
+    ulo = std::max(ulo, a);
+    uhi = std::min(uhi, b);
+  } else if (by < y0 || by > y1) {
+    return false;
+  }
+  if (uhi - ulo <= eps) return false;
+  // Entry edge: the boundary whose entry parameter is the larger; on a tie, the vertical (x) edge.
+  bool xedge = (dy == R(0)) || (dx != R(0) && ux >= uy - eps);
+  ray.entry = xedge ? (dx > R(0) ? EDGE_L : EDGE_R) : (dy > R(0) ? EDGE_B : EDGE_T);
+  std::vector<R> cut;
+  cut.push_back(ulo);
+  if (dx != R(0))
+    for (int i = 1; i < g.nx; ++i) {
+      R u = (R(g.x0) + R(i) * hx - bx) / dx;
+      if (u > ulo && u < uhi) cut.push_back(u);
+    }
+  if (dy != R(0))
+    for (int j = 1; j < g.ny; ++j) {
+      R u = (R(g.y0) + R(j) * hy - by) / dy;
+      if (u > ulo && u < uhi) cut.push_back(u);
+    }
+  cut.push_back(uhi);
+  std::sort(cut.begin(), cut.end());
+  ray.width = width;
+  ray.cell.clear();
+  ray.len.clear();
+  ray.area.clear();
+  for (size_t i = 0; i + 1 < cut.size(); ++i) {
+    R a = cut[i], b = cut[i + 1];
+    if (b - a <= eps) continue;
+    R m = R(0.5) * (a + b);
+    long ix = (long)Fn<R>::floor((bx + m * dx - x0) / hx);
+    long iy = (long)Fn<R>::floor((by + m * dy - y0) / hy);
+    ix = std::min<long>(std::max<long>(ix, 0), g.nx - 1);
+    iy = std::min<long>(std::max<long>(iy, 0), g.ny - 1);
+    ray.cell.push_back((int)(iy * g.nx + ix));
+    ray.len.push_back(b - a);
+    ray.area.push_back((b - a) * width);
+  }
+  return !ray.cell.empty();
+}
+
+template <class R> static void unit_dir(const oracle_geom &g, int m, R &dx, R &dy) {
+  R c = g.cos_phi[m], s = g.sin_phi[m];
+  R n = Fn<R>::sqrt(c * c + s * s);
+  dx = c / n;
+  dy = s / n;
+}
+
+template <class R> static int build_dir(const oracle_geom &g, int m, Dir<R> &d) {
+  unit_dir<R>(g, m, d.dx, d.dy);
+  std::vector<R> t, w;
+  characteristic_offsets<R>(g, d.dx, d.dy, t, w);
+  d.rays.clear();
+  for (size_t k = 0; k < t.size(); ++k) {
+    Ray<R> r;
+    if (trace<R>(g, d.dx, d.dy, t[k], w[k], r)) d.rays.push_back(std::move(r));
+  }
+  if (g.renorm) {
+    const R V = (R(g.lx) / R(g.nx)) * (R(g.ly) / R(g.ny));
+    std::vector<R> sum((size_t)g.nx * g.ny, R(0));
+    for (auto &r : d.rays)
+      for (size_t s = 0; s < r.cell.size(); ++s) sum[r.cell[s]] += r.area[s];
+    for (size_t i = 0; i < sum.size(); ++i)
+      if (!(sum[i] > R(0))) return -3;  // a cell no characteristic of this direction crosses
+    for (auto &r : d.rays)
+      for (size_t s = 0; s < r.cell.size(); ++s) r.area[s] = r.area[s] * (V / sum[r.cell[s]]);
+  }
+  return 0;
+}
+
+static int check_geom(const oracle_geom *g) {
+  if (!g || g->nx < 1 || g->ny < 1 || !(g->lx > 0) || !(g->ly > 0) || g->ndir < 1 || !(g->spacing > 0)) return -1;
+  if (!g->mu || !g->cos_phi || !g->sin_phi || !g->w) return -1;
+  for (int m = 0; m < g->ndir; ++m) {
+    if (!(g->mu[m] > 0 && g->mu[m] <= 1)) return -1;
+    if (g->cos_phi[m] == 0 && g->sin_phi[m] == 0) return -1;
+  }
+  return 0;
+}
+
+// Geometry is identical for directions with the same in-plane direction; build it once per distinct one.
+template <class R> struct Geometry {
+  std::vector<Dir<R>> dirs;        // distinct in-plane directions
+  std::vector<int> of;             // direction m -> index into dirs
+  int build(const oracle_geom &g) {
+    of.assign(g.ndir, -1);
+    for (int m = 0; m < g.ndir; ++m) {
+      for (int j = 0; j < m; ++j)
+        if (g.cos_phi[j] == g.cos_phi[m] && g.sin_phi[j] == g.sin_phi[m]) { of[m] = of[j]; break; }
+      if (of[m] >= 0) continue;
+      of[m] = (int)dirs.size();
+      dirs.emplace_back();
+      int rc = build_dir<R>(g, m, dirs.back());
+      if (rc) return rc;
+    }
+    return 0;
+  }
+};
+
+// Segment counts per direction (canonical order: direction m, then its characteristics by increasing
+// offset along n = (-dy, dx), then segments in traversal order).
+template <class R> static void canonical_offsets(const oracle_geom &g, const Geometry<R> &geo,
+                                                 std::vector<int64_t> &seg_dir_off) {
+  seg_dir_off.assign(g.ndir + 1, 0);
+  for (int m = 0; m < g.ndir; ++m) {
+    int64_t n = 0;
+    for (auto &r : geo.dirs[geo.of[m]].rays) n += (int64_t)r.cell.size();
+    seg_dir_off[m + 1] = seg_dir_off[m] + n;
+  }
+}
+
+// Moments accumulated per block of directions (fixed blocks, merged in block order: results do not depend
+// on the number of threads).
+enum { MOM_D = 0, MOM_FX, MOM_FY, MOM_NXX, MOM_NXY, MOM_NYY, MOM_NZZ, MOM_AFX, MOM_AFY, MOM_ANXY, N_MOM };
+
+template <class R>
+static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
+                            const double *kappa, const double *B, R inv_cdt, const double *bnd,
+                            const double *I_prev, int64_t seg0, double *I_new, double *I_exit, int64_t ray0,
+                            int Gsub, std::vector<R> *acc) {
+  const Dir<R> &d = geo.dirs[geo.of[m]];
+  const int64_t ncell = (int64_t)g.nx * g.ny;
+  const R mu = g.mu[m];
+  const R sinz = Fn<R>::sqrt(R(1) - mu * mu);
+  const R om = g.w[m];
+  const R Ox = sinz * d.dx, Oy = sinz * d.dy;
+  const double *kap = kappa + (int64_t)gsel * ncell;
+  const double *Bg = B + (int64_t)gsel * ncell;
+  int64_t seg = seg0;
+  for (size_t k = 0; k < d.rays.size(); ++k) {
+    const Ray<R> &r = d.rays[k];
+    R I = bnd[r.entry * G + gsel];                 // I_{k,1}: isotropic incoming boundary intensity
+    for (size_t s = 0; s < r.cell.size(); ++s, ++seg) {
+      const int i = r.cell[s];
+      const R kap_i = kap[i];
+      const R B_i = Bg[i];
+      const R Iprev = I_prev ? R(I_prev[seg * Gsub + gi]) : B_i;
+      const R kt = kap_i + inv_cdt;                                 // Eq. (11)
+      const R Q = kap_i * B_i + inv_cdt * Iprev;                    // Eq. (11)
+      const R tau = kt * r.len[s] / sinz;                           // Eq. (13)
+      const R one_m_e = -Fn<R>::expm1(-tau);                        // 1 - e^-tau
+      const R e = Fn<R>::exp(-tau);
+      const R Iout = I * e + (Q / kt) * one_m_e;                    // Eq. (12)
+      const R alpha = R(1) / tau - e / one_m_e;                     // Eq. (13)
+      const R Ibar = alpha * I + (R(1) - alpha) * Iout;             // Eq. (12)
+      const R wA = om * r.area[s];                                  // omega_m A_{k,s}, Eq. (14)-(15)
+      const R dev = rabs(Ibar - B_i);
+      R *a = acc->data();
+      a[MOM_D * ncell + i] += wA * Ibar;
+      a[MOM_FX * ncell + i] += wA * Ox * Ibar;
+      a[MOM_FY * ncell + i] += wA * Oy * Ibar;
+      a[MOM_NXX * ncell + i] += wA * Ox * Ox * Ibar;
+      a[MOM_NXY * ncell + i] += wA * Ox * Oy * Ibar;
+      a[MOM_NYY * ncell + i] += wA * Oy * Oy * Ibar;
+      a[MOM_NZZ * ncell + i] += wA * mu * mu * Ibar;
+      a[MOM_AFX * ncell + i] += wA * rabs(Ox) * dev;
+      a[MOM_AFY * ncell + i] += wA * rabs(Oy) * dev;
+      a[MOM_ANXY * ncell + i] += wA * rabs(Ox * Oy) * dev;
+      if (I_new) I_new[seg * Gsub + gi] = (double)Ibar;
+      I = Iout;
+    }
+    if (I_exit) I_exit[(ray0 + (int64_t)k) * Gsub + gi] = (double)I;
+  }
+}
+
+template <class R>
+static int run_sweep(const oracle_geom *g, int G, const double *kappa, const double *B, double c, double dt,
+                     const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
+                     double *I_new, double *I_exit, int nthreads) {
+  if (check_geom(g)) return -1;
+  if (G < 1 || !kappa || !B || !bnd || !(c > 0) || !(dt > 0) || !out) return -1;
+  Geometry<R> geo;
+  int rc = geo.build(*g);
+  if (rc) return rc;
+  std::vector<int> gl;
+  if (groups) {
+    for (int i = 0; i < ngroups; ++i) {
+      if (groups[i] < 0 || groups[i] >= G) return -1;
+      gl.push_back(groups[i]);
+    }
+  } else {
+    for (int i = 0; i < G; ++i) gl.push_back(i);
+  }
+  const int Gsub = (int)gl.size();
+  std::vector<int64_t> seg_off;
+  canonical_offsets<R>(*g, geo, seg_off);
+  std::vector<int64_t> ray_off(g->ndir + 1, 0);
+  for (int m = 0; m < g->ndir; ++m) ray_off[m + 1] = ray_off[m] + (int64_t)geo.dirs[geo.of[m]].rays.size();
+  const int64_t ncell = (int64_t)g->nx * g->ny;
+  const R inv_cdt = R(1) / (R(c) * R(dt));
+  const R V = (R(g->lx) / R(g->nx)) * (R(g->ly) / R(g->ny));
+  const int nblk = std::min(g->ndir, 16);
+  if (nthreads < 1) nthreads = 1;
+  std::vector<std::vector<R>> acc(nblk);
+  for (int gi = 0; gi < Gsub; ++gi) {
+    for (auto &a : acc) a.assign((size_t)N_MOM * ncell, R(0));
+    auto work = [&](int tid) {
+      for (int b = tid; b < nblk; b += nthreads) {
+        int m0 = (int)((int64_t)g->ndir * b / nblk), m1 = (int)((int64_t)g->ndir * (b + 1) / nblk);
+        for (int m = m0; m < m1; ++m)
+          sweep_direction<R>(*g, geo, m, gi, G, gl[gi], kappa, B, inv_cdt, bnd, I_prev, seg_off[m], I_new,
+                             I_exit, ray_off[m], Gsub, &acc[b]);
+      }
+    };
+    int nt = std::min(nthreads, nblk);
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto &t : th) t.join();
+    std::vector<R> tot((size_t)N_MOM * ncell, R(0));
+    for (int b = 0; b < nblk; ++b)
+      for (size_t q = 0; q < tot.size(); ++q) tot[q] += acc[b][q];
+    // Cell averages: E = (1/(c V)) sum omega A Ibar;  F, N, |.|-moments = (1/V) sum ...   (Sec. 2, Eq. 15)
+    for (int q = 0; q < N_MOM; ++q) {
+      double *o = out + ((int64_t)q * Gsub + gi) * ncell;
+      const R scale = q == MOM_D ? R(1) / (R(c) * V) : R(1) / V;
+      for (int64_t i = 0; i < ncell; ++i) o[i] = (double)(tot[(size_t)q * ncell + i] * scale);
+    }
+  }
+  return 0;
+}
+
+template <class R>
+static int run_tracks(const oracle_geom *g, int64_t *counts, int64_t *dir_ray_off, int64_t *ray_seg_off,
+                      double *width, int *entry, int *cell, double *len, double *area) {
+  if (check_geom(g)) return -1;
+  Geometry<R> geo;
+  int rc = geo.build(*g);
+  if (rc) return rc;
+  int64_t nr = 0, ns = 0;
+  for (int m = 0; m < g->ndir; ++m)
+    for (auto &r : geo.dirs[geo.of[m]].rays) { nr++; ns += (int64_t)r.cell.size(); }
+  if (counts) { counts[0] = nr; counts[1] = ns; }
+  if (!dir_ray_off) return 0;
+  int64_t ri = 0, si = 0;
+  dir_ray_off[0] = 0;
+  ray_seg_off[0] = 0;
+  for (int m = 0; m < g->ndir; ++m) {
+    for (auto &r : geo.dirs[geo.of[m]].rays) {
+      width[ri] = (double)r.width;
+      entry[ri] = r.entry;
+      for (size_t s = 0; s < r.cell.size(); ++s, ++si) {
+        cell[si] = r.cell[s];
+        len[si] = (double)r.len[s];
+        area[si] = (double)r.area[s];
+      }
+      ray_seg_off[++ri] = si;
+    }
+    dir_ray_off[m + 1] = ri;
+  }
+  return 0;
+}
+
+extern "C" {
+
+// Sizes of the characteristic grid: counts[0] = characteristics summed over directions, counts[1] = segments
+// summed over directions (the length of the canonical per-group intensity array).  Returns 0 on success.
+int oracle_count(const oracle_geom *g, int64_t *counts) {
+  return run_tracks<double>(g, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+}
+
+// The characteristic grid in canonical order.  precision: 0 = double, 1 = binary128 (values rounded to double).
+int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int64_t *ray_seg_off,
+                  double *width, int *entry, int *cell, double *len, double *area) {
+  if (!dir_ray_off || !ray_seg_off || !width || !entry || !cell || !len || !area) return -1;
+  int64_t counts[2];
+  return precision ? run_tracks<real128>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area)
+                   : run_tracks<double>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area);
+}
+
+// One backward-Euler sweep of every direction, characteristic and (selected) group.
+//   kappa, B   [G][ncell]        opacity (cm^-1) and group Planck intensity
+//   bnd        [4][G]            isotropic incoming intensity per edge (left, right, bottom, top)
+//   I_prev     [nseg][Gsub]      canonical previous-step segment averages, or NULL for I^{n-1} = B of the cell
+//   groups     [ngroups]         subset of groups to sweep, or NULL for all (Gsub = G)
+//   out        [10][Gsub][ncell] E, Fx, Fy, Nxx, Nxy, Nyy, Nzz, then the conditioning magnitudes
+//                                (1/V) sum omega A |Omega_x| |Ibar - B|, same with |Omega_y|, |Omega_x Omega_y|
+//   I_new      [nseg][Gsub]      canonical segment averages Ibar (may be NULL)
+//   I_exit     [nrays][Gsub]     intensity leaving each characteristic (may be NULL)
+int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa, const double *B, double c,
+                 double dt, const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
+                 double *I_new, double *I_exit, int nthreads) {
+  return precision ? run_sweep<real128>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
+                                       nthreads)
+                   : run_sweep<double>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
+                                       nthreads);
+}
+
+int oracle_real_bits(int precision) { return precision ? (int)(sizeof(real128) * 8) : 64; }
+
+}  // extern "C"
