@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the MOLC high-order sweep (Sec. 3) on one or more GB300 GPUs.
+
+One step = one backward-Euler sweep of every direction, characteristic and group (FP32 production path,
+molc_sweep) followed by the Eddington closure (molc_closure), on the 512 x 512-cell, 17-group, 4 x 32-direction,
+h/2-spacing synthetic Fleck-Cummings-shaped workload with three tanh fronts.  The intensity state (5.8 GB) is
+far larger than L2, so no cache flush is needed between steps.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead (double precision, all host
+cores, one group of the same workload per step).  Under torchrun every rank sweeps its own instance (seed =
+rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "fc512_g17_d128"
+METRIC = "segment×group updates/s"
+# ncu dram bytes (read + write) of one sweep_fp32_kernel launch on this workload, from the capture summarised in
+# profiles/sweep_fp32_fc512.md; None until that capture matches the current kernel.
+SWEEP_FP32_DRAM_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_sample(wl, d, max_seconds=12.0):
+    """The double oracle, as it stands, on whole groups of the workload until about max_seconds."""
+    import oracle
+    geom = oracle.Geometry.from_workload(wl)
+    _, nseg = oracle.counts(geom)
+    cores = os.cpu_count() or 1
+    done_updates = 0
+    groups = []
+    t0 = time.perf_counter()
+    g = wl.G // 2
+    while True:
+        oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=[g], precision="double",
+                     want_I=False, threads=cores)
+        done_updates += nseg
+        groups.append(g)
+        g = (g + 1) % wl.G
+        if time.perf_counter() - t0 > max_seconds or len(groups) >= wl.G:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done_updates / dt, "unit": "updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"double-precision oracle, {len(groups)} of {wl.G} groups of one step of {wl.name} "
+                      f"({done_updates:.3e} updates, {dt:.1f} s, characteristic grid rebuilt per call)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[args.workload]
+    d = wl.inputs(0)
+    import oracle
+    geom = oracle.Geometry.from_workload(wl)
+    _, nseg = oracle.counts(geom)
+    cores = os.cpu_count() or 1
+    g = wl.G // 2
+
+    def step(i):
+        oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=[(g + i) % wl.G],
+                     precision="double", want_I=False, threads=cores)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = time.perf_counter() - t0
+    value = nseg * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, "
+                                   f"{wl.n_polar}x{wl.n_azim} directions, spacing h/{wl.spacing_div}",
+                       "sample_per_step": "one group of one sweep (groups rotate)"},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one of {wl.G} groups per step, {nseg:.3e} updates per step"},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2305_11998_gb300 as molc
+
+    wl = synth.WORKLOADS[args.workload]
+    d = wl.inputs(seed=rank)
+    P = molc.Plan.from_workload(wl)
+    info = P.info
+    G, ncell = wl.G, wl.ncell
+    k_h = torch.tensor(d["kappa"]).pin_memory()
+    B_h = torch.tensor(d["B"]).pin_memory()
+    bnd_h = torch.tensor(d["bnd"]).pin_memory()
+    k_d, B_d, bnd_d = k_h.to(dev), B_h.to(dev), bnd_h.to(dev)
+    I = P.new_intensity("fp32", dev)
+    P.intensity_init("fp32", I, B_d)
+    mom = P.new_moments(dev)
+
+    def step():
+        P.sweep("fp32", k_d, B_d, wl.c, wl.dt, I, bnd_d, out=mom)
+        return P.closure(mom, wl.c)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    sampler = ClockSampler() if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    P.kernel_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        f = step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = P.kernel_time()
+    P.kernel_timing(False)
+    clocks = sampler.stop() if sampler else None
+    status = P.device_status()
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * info.n_updates * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (the FP32 sweep): algorithmic bytes per launch / average launch time
+    per_update = 8.0   # the FP32 deviation state: 4 B read + 4 B written per update
+    gc = info.fp32_groups_per_warp
+    n_chunks = -(-G // gc)
+    extras = (16.0 * info.n_track_segments * n_chunks      # segment records, once per group chunk
+              + 20.0 * ncell * G                            # cell table {kappa~, r, B_hi, B_lo, dB}
+              + 48.0 * ncell * G)                           # FP64 accumulators written back
+    alg_bytes = per_update * info.n_updates + extras
+    kern_avg = kern_ms / max(kern_n, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kern_avg / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": SWEEP_FP32_DRAM_BYTES, "kernel": "sweep_fp32_kernel", "kernel_ms": kern_avg,
+                "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # end to end through the public API: pinned host inputs copied in, moments and factors copied out
+    e2e = None
+    if not args.no_e2e:
+        outs_h = {k: torch.empty((G, ncell), dtype=torch.float64).pin_memory() for k in
+                  ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy", "fxx", "fxy", "fyy")}
+        h2d = (k_h.numel() + B_h.numel() + bnd_h.numel()) * 8
+        d2h = sum(v.numel() for v in outs_h.values()) * 8
+
+        def e2e_step():
+            k_d.copy_(k_h, non_blocking=True)
+            B_d.copy_(B_h, non_blocking=True)
+            bnd_d.copy_(bnd_h, non_blocking=True)
+            P.sweep("fp32", k_d, B_d, wl.c, wl.dt, I, bnd_d, out=mom)
+            fe = P.closure(mom, wl.c)
+            for k in ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy"):
+                outs_h[k].copy_(mom[k], non_blocking=True)
+            for k in ("fxx", "fxy", "fyy"):
+                outs_h[k].copy_(fe[k], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ws * info.n_updates * args.steps / (ems / 1e3), "unit": "updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / args.steps}
+
+    # the plain FP64 GPU sweep on the same workload (the speed-up denominator)
+    fp64 = None
+    if not args.no_fp64:
+        del I
+        torch.cuda.empty_cache()
+        I64 = P.new_intensity("fp64", dev)
+        P.intensity_init("fp64", I64, B_d)
+        P.sweep("fp64", k_d, B_d, wl.c, wl.dt, I64, bnd_d, out=mom)
+        torch.cuda.synchronize()
+        n64 = 2
+        e0.record()
+        for _ in range(n64):
+            P.sweep("fp64", k_d, B_d, wl.c, wl.dt, I64, bnd_d, out=mom)
+            P.closure(mom, wl.c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        fp64 = {"value": info.n_updates / (ms64 / 1e3), "unit": "updates/s", "ms_per_step": ms64,
+                "speedup_fp32_over_fp64": (info.n_updates / (ms_step / 1e3)) / (info.n_updates / (ms64 / 1e3))}
+        del I64
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(wl, d)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {G} groups, {wl.n_polar}x{wl.n_azim} "
+                                       f"directions, spacing h/{wl.spacing_div}, three fronts; one instance per GPU",
+                           "updates_per_step_per_gpu": info.n_updates,
+                           "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
+                           "step": "molc_sweep (FP32) + molc_closure"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 4 * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
+        print(json.dumps(line), flush=True)
+    P.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * molc.h — C ABI of libmolc: the high-order sweep of the method of long characteristics (MOLC / ray tracing)
+ * for the backward-Euler multigroup Boltzmann transport equation, on one GB300 (sm_103a) GPU.
+ *
+ * Paper: J. M. Coale and D. Y. Anistratov, "Multilevel method for thermal radiative transfer problems with
+ * method of long characteristics for the Boltzmann transport equation" — Sec. 3 (the MOLC / ray-tracing
+ * scheme, Eqs. 10-16) and Sec. 2 (the moments E_g, F_g and the Eddington tensor, Eqs. 4 and 7).
+ *
+ * Conventions shared by every entry point:
+ *  - Units: lengths in cm, time in shakes, opacity in cm^-1, intensities (B, boundary, I) in one intensity unit;
+ *    E is (1/c) x intensity.
+ *  - Cell index i = iy * nx + ix; per-group arrays are [G][ny*nx] row-major ("[g][cell]").
+ *  - "device" pointers are CUDA device memory of the device current when molc_create() ran; the caller owns
+ *    them (allocates and frees).  "host" pointers are ordinary host memory, read during the call only.
+ *  - Entry points that take a stream are asynchronous on that stream (NULL = legacy default stream), perform
+ *    no device allocation and no host synchronisation, and return MOLC_ERR_CUDA if a launch fails.  Errors the
+ *    kernels detect (non-finite or negative inputs) are recorded in a per-plan device status word that
+ *    molc_device_status() reads; kernels never trap.
+ *  - Every entry point returns a molc_status; on failure molc_last_error() gives a message (thread-local).
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the caller (one stream at a time).
+ */
+#ifndef MOLC_H
+#define MOLC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *molc_stream; /* a cudaStream_t */
+
+typedef enum {
+  MOLC_OK = 0,
+  MOLC_ERR_INVALID_ARG = 1,      /* a host-checkable argument is wrong (sizes, NULLs, quadrature structure) */
+  MOLC_ERR_OUT_OF_MEMORY = 2,    /* molc_create could not allocate the plan's device tables */
+  MOLC_ERR_CUDA = 3,             /* a CUDA runtime call or kernel launch failed */
+  MOLC_ERR_NONFINITE_INPUT = 4,  /* device status: kappa, B or the boundary held NaN/Inf or a negative value */
+  MOLC_ERR_TIMEOUT = 5,          /* reserved: a bounded device wait gave up */
+  MOLC_ERR_INTERNAL = 6
+} molc_status;
+
+typedef enum { MOLC_FP64 = 0, MOLC_FP32 = 1 } molc_precision;
+
+/* Characteristic-grid construction (Sec. 3, last paragraph before the results).
+ *  MOLC_RAYS_UNIFORM: per azimuth, n = ceil(L_perp / spacing) parallel characteristics of equal width
+ *                     w = L_perp / n (L_perp = projected width of the domain), centred at (k + 1/2) w.
+ *  MOLC_RAYS_PAPER:   the paper's rule: the gaps between the projections of all grid vertices are the initial
+ *                     characteristics (no characteristic crosses a vertex); each is halved until w <= spacing. */
+typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
+
+/* flags for molc_create */
+#define MOLC_AREA_RENORM 1u /* scale A_{k,s} per (cell, azimuth) so that sum over C(i,m) of A = cell area */
+#define MOLC_HOST_ONLY 2u   /* build the characteristic grid on the host only (no device memory, no GPU needed):
+                               only molc_plan_get_info, molc_tracks_export and molc_destroy accept such a plan */
+
+typedef struct {
+  int nx, ny;               /* material cells (>= 1) */
+  double x0, y0, lx, ly;    /* domain [x0, x0+lx] x [y0, y0+ly], cm (lx, ly > 0) */
+} molc_grid;
+
+/* Angular quadrature, host arrays of n directions with mu > 0 (the upper hemisphere; each direction also
+ * stands for its mirror through the x-y plane, so the weights sum to 4 pi).  (cos_phi, sin_phi) is the
+ * in-plane direction.  Required structure: every direction has an opposite one with (cos_phi, sin_phi)
+ * exactly negated and the same mu and w, and every azimuth carries the same list of polar cosines. */
+typedef struct {
+  int n;
+  const double *mu;
+  const double *cos_phi;
+  const double *sin_phi;
+  const double *w;
+} molc_quadrature;
+
+typedef struct {
+  int G;                    /* number of frequency groups (>= 1) */
+  const double *edges;      /* host, G+1 group edges in keV, or NULL (metadata only) */
+} molc_groups;
+
+typedef struct molc_plan molc_plan; /* opaque; owns the device characteristic grid and sweep workspace */
+
+/* Cell moments, all device [G][ny*nx] FP64, caller-owned (Sec. 2: E_g = (1/c) int I dOmega,
+ * F_g = int Omega I dOmega; Eq. 7 / Eq. 15: N_g = int Omega Omega I dOmega).  Cell averages. */
+typedef struct {
+  double *E, *Fx, *Fy, *Nxx, *Nxy, *Nyy;
+} molc_moments;
+
+typedef struct {
+  int G, nx, ny;
+  int n_dir;                /* directions (both senses, all polar cosines) */
+  int n_azim_pairs;         /* distinct characteristic families: azimuth phi with phi + pi */
+  int n_polar;              /* polar cosines per azimuth */
+  int64_t n_tracks;         /* characteristics summed over azimuth pairs */
+  int64_t n_track_segments; /* segments summed over azimuth pairs (each walked by 2 senses x n_polar) */
+  int64_t n_segments;       /* segments summed over all directions (= 2 n_polar n_track_segments) */
+  int64_t n_updates;        /* segment x direction x group updates per sweep (= n_segments G) */
+  int fp32_groups_per_warp; /* groups per chunk of the FP32 sweep (chunks run one after another) */
+  size_t device_bytes;      /* device memory the plan holds */
+} molc_plan_info;
+
+/* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,
+ * equal weights) product set, omega = 4 pi w_p / n_azim, direction order m = p * n_azim + j.  n_azim must be a
+ * positive multiple of 4; cos/sin are built by exact reflection from the first octant so the set is exactly
+ * symmetric.  Host output arrays of n_polar * n_azim entries.  (A substitute for the paper's Abu-Shumays set,
+ * Sec. 4, whose table is not available.) */
+molc_status molc_quadrature_product(int n_polar, int n_azim, double *mu, double *cos_phi, double *sin_phi,
+                                    double *w);
+
+/* Build the characteristic grid on the host (Sec. 3) and upload it to the current CUDA device.
+ * ray_spacing: h_moc in cm (> 0).  flags: MOLC_AREA_RENORM or 0.  groups->G fixes the group count of every
+ * later call.  On success *out owns device memory until molc_destroy(). */
+molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, const molc_groups *groups,
+                        double ray_spacing, molc_layout layout, unsigned flags, molc_plan **out);
+
+molc_status molc_plan_get_info(const molc_plan *plan, molc_plan_info *info);
+
+/* The opaque intensity state I^{n-1} of one precision: one element per (segment, direction, group) (FP64: 8
+ * bytes, FP32: 4) holding the deviation of the segment average from the cell's Planck intensity, followed by
+ * that reference Planck intensity per (group, cell) in FP64.  molc_intensity_count gives the elements,
+ * molc_intensity_bytes the bytes to allocate (256-byte aligned device memory).  The layout is private to the
+ * library; use export/import to read or write segment averages. */
+int64_t molc_intensity_count(const molc_plan *plan);
+size_t molc_intensity_bytes(const molc_plan *plan, molc_precision prec);
+
+/* I^{n-1} := B_g of the segment's cell on every segment, direction and group (the state before the first
+ * step).  I: device, molc_intensity_bytes(prec).  B: device [G][cell].  Allocation-free (memset + copy). */
+molc_status molc_intensity_init(molc_plan *plan, molc_precision prec, void *I, const double *B,
+                                molc_stream stream);
+
+/* One backward-Euler step of the high-order sweep (Sec. 3, Eqs. 11-15), for every azimuth pair,
+ * characteristic, sense, polar cosine and group:
+ *   kappa~ = kappa + 1/(c dt),  Q = kappa B + I^{n-1}/(c dt),  tau = kappa~ l / sin(zeta),
+ *   I_{s+1} = I_s e^-tau + (Q/kappa~)(1 - e^-tau),  Ibar = alpha I_s + (1 - alpha) I_{s+1},
+ * I^{n-1} is the previous step's segment average on the same segment, direction and group, and is replaced in
+ * place by this step's Ibar.  Entering intensity: bnd[edge][g] (isotropic per edge; edges left, right,
+ * bottom, top).  Writes the cell moments E, Fx, Fy, Nxx, Nxy, Nyy of every group into *out (the areas
+ * A = l w of Eq. 14 weight the segment averages).
+ *   prec   MOLC_FP64: all arithmetic in FP64.  MOLC_FP32: segment arithmetic in FP32, moment accumulation and
+ *          the cell assembly in FP64.
+ *   kappa, B  device [G][cell] FP64;  c (cm/sh) > 0, dt (sh) > 0;  I: device state of precision prec;
+ *   bnd    device [4][G] FP64;  out: device pointers, each [G][cell] FP64, overwritten.
+ * Asynchronous on `stream`; no allocation. */
+molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa, const double *B, double c,
+                       double dt, void *I, const double *bnd, const molc_moments *out, molc_stream stream);
+
+/* Eddington factors of each cell and group, f = N / (c E) (Eq. 7 with the cell averages of Eq. 15):
+ * fxx, fxy, fyy device [G][cell]; f_zz = 1 - f_xx - f_yy.  f_grey: device [3][cell] or NULL, the
+ * E-weighted spectral average <f>_E = sum_g f_g E_g / sum_g E_g (Sec. 2, Eq. 8) of xx, xy, yy.
+ * A cell with E = 0 gets f = 0. */
+molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c, double *fxx, double *fxy,
+                         double *fyy, double *f_grey, molc_stream stream);
+
+/* Canonical intensity layout: [n_segments][g_count] FP64 segment averages, direction-major in quadrature
+ * order; within a direction, characteristics by increasing offset along (-sin phi, cos phi) and segments in
+ * traversal order.  export: canon := I (groups g_begin .. g_begin+g_count-1).  import: I := canon for the same
+ * groups, with B (device [G][cell]) as the new reference Planck intensity of those groups.  Device memory. */
+molc_status molc_intensity_export(const molc_plan *plan, molc_precision prec, const void *I, int g_begin,
+                                  int g_count, double *canon, molc_stream stream);
+molc_status molc_intensity_import(molc_plan *plan, molc_precision prec, void *I, int g_begin, int g_count,
+                                  const double *canon, const double *B, molc_stream stream);
+
+/* The characteristic grid in the canonical order (host arrays): dir_ray_off[n_dir+1], ray_seg_off[rays+1],
+ * width[rays], entry[rays] (edge 0..3), cell[n_segments], len[n_segments] (in-plane l), area[n_segments]
+ * (A after renormalisation).  rays = 2 n_polar n_tracks. */
+molc_status molc_tracks_export(const molc_plan *plan, int64_t *dir_ray_off, int64_t *ray_seg_off, double *width,
+                               int *entry, int *cell, double *len, double *area);
+
+/* Kernel timing for benchmarks: while enabled, every molc_sweep / molc_batch_sweep records a CUDA event pair
+ * around its sweep kernel (at most 4096 launches are kept).  molc_kernel_time synchronises with the last
+ * recorded event, returns the summed elapsed milliseconds and the number of timed launches, and clears the
+ * record.  Disabled by default; enabling creates the events (no device memory allocation). */
+molc_status molc_kernel_timing(molc_plan *plan, int enable);
+molc_status molc_kernel_time(molc_plan *plan, double *total_ms, int *launches);
+
+/* Read and clear the plan's device status word (synchronises with the device).  *code = MOLC_OK or the first
+ * error the kernels recorded. */
+molc_status molc_device_status(molc_plan *plan, int *code);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *molc_last_error(void);
+
+void molc_destroy(molc_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOLC_H */

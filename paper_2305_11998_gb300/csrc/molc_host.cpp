@@ -1,0 +1,874 @@
+// Host side of libmolc: argument checking, the characteristic-grid planner (Sec. 3) and the C ABI.
+//
+// The planner builds, for every azimuth pair (phi, phi + pi), the parallel characteristics of the chosen
+// layout, cuts each at its crossings with the material grid lines, and stores the segments once per pair:
+// the + sense walks them forward, the - sense backward, and all polar cosines of the pair share them (the
+// in-plane track depends only on the azimuth; the 3D path length is l / sin(zeta), Eq. 13).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "molc_internal.h"
+
+using namespace molc;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+molc_status fail(molc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+molc_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? MOLC_ERR_OUT_OF_MEMORY : MOLC_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+// Compensated (double-double) accumulator for the per-cell geometric moments.
+struct Acc2 {
+  double hi = 0, lo = 0;
+  void add(double x) {
+    double s = hi + x;
+    double bp = s - hi;
+    double err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+  }
+  double value() const { return hi + lo; }
+};
+
+struct HostTrack {
+  double width;
+  int entry_plus, entry_minus;
+  int64_t seg_off;
+  int nseg;
+};
+
+}  // namespace
+
+struct molc_plan {
+  int device = 0;
+  molc_grid grid{};
+  int G = 0, n_dir = 0, n_pairs = 0, n_polar = 0;
+  double spacing = 0;
+  molc_layout layout = MOLC_RAYS_UNIFORM;
+  unsigned flags = 0;
+  bool host_only = false;
+  double hx = 0, hy = 0, V = 0;
+  // host copies of the characteristic grid
+  std::vector<PairDev> pairs;
+  std::vector<PolarDev> polar;                 // [pair][p]
+  std::vector<int64_t> pair_track_off;         // [n_pairs + 1]
+  std::vector<HostTrack> tracks;
+  std::vector<int> seg_cell;
+  std::vector<double> seg_len, seg_afrac;
+  std::vector<int> dir_pair, dir_sense, dir_polar;
+  std::vector<int64_t> dir_seg_off;
+  // device
+  TrackDev *d_tracks = nullptr;
+  int4 *d_seg32 = nullptr;
+  int *d_seg_cell = nullptr;
+  double *d_seg_len = nullptr, *d_seg_afrac = nullptr;
+  PairDev *d_pairs = nullptr;
+  PolarDev *d_polar = nullptr;
+  double *d_geo = nullptr;
+  int64_t *d_dir_seg_off = nullptr;
+  int *d_status = nullptr;
+  float4 *d_cdat = nullptr;
+  float *d_cdB = nullptr;
+  double *d_acc = nullptr;
+  int2 *d_items32 = nullptr;
+  int64_t n_items32 = 0;
+  size_t acc_elems = 0;
+  size_t device_bytes = 0;
+  PlanView view{};
+  // benchmark timing of the sweep kernel
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;   // pairs
+  int n_timed = 0;
+};
+
+namespace {
+
+// RAII guard: make the plan's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) changed = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+// Offsets (along n = (-s, c)) and widths of the characteristics of one azimuth, ordered by offset.
+void characteristic_offsets(const molc_grid &g, double c, double s, double spacing, molc_layout layout,
+                            std::vector<double> &t, std::vector<double> &w) {
+  t.clear();
+  w.clear();
+  const double xs[2] = {g.x0, g.x0 + g.lx}, ys[2] = {g.y0, g.y0 + g.ly};
+  if (layout == MOLC_RAYS_UNIFORM) {
+    double tmin = 1e300, tmax = -1e300;
+    for (double x : xs)
+      for (double y : ys) {
+        double v = -s * x + c * y;
+        tmin = std::min(tmin, v);
+        tmax = std::max(tmax, v);
+      }
+    const double Lp = tmax - tmin;
+    long n = (long)std::ceil(Lp / spacing - 1e-9);
+    if (n < 1) n = 1;
+    const double wk = Lp / (double)n;
+    t.reserve(n);
+    for (long k = 0; k < n; ++k) {
+      t.push_back(tmin + ((double)k + 0.5) * wk);
+      w.push_back(wk);
+    }
+    return;
+  }
+  // The paper's rule: every gap between projections of grid vertices is a characteristic free of vertices;
+  // split into halves until the width is at most h_moc.
+  const double hx = g.lx / g.nx, hy = g.ly / g.ny;
+  std::vector<double> proj;
+  proj.reserve((size_t)(g.nx + 1) * (g.ny + 1));
+  for (int b = 0; b <= g.ny; ++b)
+    for (int a = 0; a <= g.nx; ++a) proj.push_back(-s * (g.x0 + a * hx) + c * (g.y0 + b * hy));
+  std::sort(proj.begin(), proj.end());
+  const double merge = 1e-13 * (proj.back() - proj.front());
+  double last = proj.front();
+  for (size_t i = 1; i < proj.size(); ++i) {
+    if (proj[i] - last <= merge) continue;
+    const double gap = proj[i] - last;
+    long pieces = 1;
+    while (gap / (double)pieces > spacing) pieces *= 2;
+    const double wk = gap / (double)pieces;
+    for (long q = 0; q < pieces; ++q) {
+      t.push_back(last + ((double)q + 0.5) * wk);
+      w.push_back(wk);
+    }
+    last = proj[i];
+  }
+}
+
+// Cut one characteristic into cell segments.  Crossings with vertical and horizontal grid lines are produced
+// as two increasing sequences and merged; a gap <= eps between consecutive cut points is not a segment (the
+// characteristic passes within eps of a vertex, i.e. steps diagonally).  A segment belongs to the cell that
+// contains its midpoint.  Returns false if the line misses the domain.
+bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, double s, double t,
+                        std::vector<int> &cells, std::vector<double> &lens, int &entry_plus, int &entry_minus) {
+  const double eps = 1e-12 * std::min(hx, hy);
+  const double bx = -t * s, by = t * c;  // the point of the line at u = 0
+  const double x1 = g.x0 + g.lx, y1 = g.y0 + g.ly;
+  double xlo = -1e300, xhi = 1e300, ylo = -1e300, yhi = 1e300;
+  if (c != 0.0) {
+    xlo = (g.x0 - bx) / c;
+    xhi = (x1 - bx) / c;
+    if (xlo > xhi) std::swap(xlo, xhi);
+  } else if (bx < g.x0 || bx > x1) {
+    return false;
+  }
+  if (s != 0.0) {
+    ylo = (g.y0 - by) / s;
+    yhi = (y1 - by) / s;
+    if (ylo > yhi) std::swap(ylo, yhi);
+  } else if (by < g.y0 || by > y1) {
+    return false;
+  }
+  const double uin = std::max(xlo, ylo), uout = std::min(xhi, yhi);
+  if (uout - uin <= eps) return false;
+  // entry of the + sense: the larger lower bound (tie -> the vertical edge); exit likewise with upper bounds.
+  const bool x_in = c != 0.0 && (s == 0.0 || xlo >= ylo - eps);
+  entry_plus = x_in ? (c > 0 ? 0 : 1) : (s > 0 ? 2 : 3);
+  const bool x_out = c != 0.0 && (s == 0.0 || xhi <= yhi + eps);
+  entry_minus = x_out ? (c > 0 ? 1 : 0) : (s > 0 ? 3 : 2);
+  // crossing parameters, each list increasing in u
+  std::vector<double> ux, uy;
+  if (c != 0.0) {
+    for (int i = 1; i < g.nx; ++i) {
+      const int ii = c > 0 ? i : g.nx - i;
+      const double u = (g.x0 + ii * hx - bx) / c;
+      if (u > uin && u < uout) ux.push_back(u);
+    }
+  }
+  if (s != 0.0) {
+    for (int j = 1; j < g.ny; ++j) {
+      const int jj = s > 0 ? j : g.ny - j;
+      const double u = (g.y0 + jj * hy - by) / s;
+      if (u > uin && u < uout) uy.push_back(u);
+    }
+  }
+  cells.clear();
+  lens.clear();
+  size_t ix = 0, iy = 0;
+  double a = uin;
+  while (true) {
+    double b;
+    if (ix < ux.size() && (iy >= uy.size() || ux[ix] <= uy[iy]))
+      b = ux[ix++];
+    else if (iy < uy.size())
+      b = uy[iy++];
+    else
+      b = uout;
+    if (b - a > eps) {
+      const double m = 0.5 * (a + b);
+      int cx = (int)std::floor((bx + m * c - g.x0) / hx);
+      int cy = (int)std::floor((by + m * s - g.y0) / hy);
+      cx = std::min(std::max(cx, 0), g.nx - 1);
+      cy = std::min(std::max(cy, 0), g.ny - 1);
+      cells.push_back(cy * g.nx + cx);
+      lens.push_back(b - a);
+    }
+    a = b;
+    if (b == uout) break;
+  }
+  return !cells.empty();
+}
+
+template <class T> molc_status upload(T **dst, const T *src, size_t n, size_t &total, const char *what) {
+  *dst = nullptr;
+  if (n == 0) return MOLC_OK;
+  cudaError_t e = cudaMalloc((void **)dst, n * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  total += n * sizeof(T);
+  if (src) {
+    e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+  }
+  return MOLC_OK;
+}
+
+constexpr int kMaxTimed = 4096;
+
+void free_events(molc_plan *p) {
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  p->ev.clear();
+  p->n_timed = 0;
+}
+
+void free_device(molc_plan *p) {
+  free_events(p);
+  void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
+                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *molc_last_error(void) { return g_last_error.c_str(); }
+
+molc_status molc_quadrature_product(int n_polar, int n_azim, double *mu, double *cos_phi, double *sin_phi,
+                                    double *w) {
+  if (n_polar < 1 || n_polar > 64 || n_azim < 4 || n_azim % 4 || !mu || !cos_phi || !sin_phi || !w)
+    return fail(MOLC_ERR_INVALID_ARG, "quadrature_product: need 1 <= n_polar <= 64, n_azim a multiple of 4");
+  // Gauss-Legendre nodes on (-1, 1): Newton's method on P_n from the guesses cos(pi (i + 3/4) / (n + 1/2)),
+  // P_n and P_{n-1} by the three-term recurrence, weights 2 / ((1 - x^2) P_n'(x)^2); mapped to (0, 1) below.
+  std::vector<double> x(n_polar), W(n_polar);
+  const double pi = 3.14159265358979323846;
+  auto legendre = [n_polar](double z, double &pn, double &dpn) {
+    double p_prev = 1.0, p_cur = z;
+    if (n_polar == 1) {
+      pn = z;
+      dpn = 1.0;
+      return;
+    }
+    for (int k = 1; k < n_polar; ++k) {
+      const double p_next = ((2.0 * k + 1.0) * z * p_cur - k * p_prev) / (k + 1.0);
+      p_prev = p_cur;
+      p_cur = p_next;
+    }
+    pn = p_cur;
+    dpn = n_polar * (z * p_cur - p_prev) / (z * z - 1.0);
+  };
+  for (int i = 0; i < n_polar; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n_polar + 0.5)), pn, dpn;
+    for (int it = 0; it < 100; ++it) {
+      legendre(z, pn, dpn);
+      const double dz = pn / dpn;
+      z -= dz;
+      if (std::fabs(dz) <= 1e-16 * std::fabs(z) + 1e-300) break;
+    }
+    legendre(z, pn, dpn);
+    x[i] = z;
+    W[i] = 2.0 / ((1.0 - z * z) * dpn * dpn);
+  }
+  std::vector<int> order(n_polar);
+  for (int i = 0; i < n_polar; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return x[a] < x[b]; });
+  // Chebyshev azimuths, first octant evaluated, the rest by exact swaps and sign flips.
+  const int Q = n_azim / 4;
+  std::vector<double> c1(Q), s1(Q), c(n_azim), s(n_azim);
+  for (int j = 0; j < (Q + 1) / 2; ++j) {
+    const double phi = (j + 0.5) * 2.0 * pi / n_azim;
+    c1[j] = std::cos(phi);
+    s1[j] = std::sin(phi);
+    c1[Q - 1 - j] = s1[j];
+    s1[Q - 1 - j] = c1[j];
+  }
+  if (Q % 2) c1[Q / 2] = s1[Q / 2] = std::sqrt(0.5);
+  for (int j = 0; j < n_azim; ++j) {
+    if (j < Q) { c[j] = c1[j]; s[j] = s1[j]; }
+    else if (j < 2 * Q) { c[j] = -c1[2 * Q - 1 - j]; s[j] = s1[2 * Q - 1 - j]; }
+    else if (j < 3 * Q) { c[j] = -c1[j - 2 * Q]; s[j] = -s1[j - 2 * Q]; }
+    else { c[j] = c1[4 * Q - 1 - j]; s[j] = -s1[4 * Q - 1 - j]; }
+  }
+  for (int p = 0; p < n_polar; ++p)
+    for (int j = 0; j < n_azim; ++j) {
+      const int m = p * n_azim + j;
+      mu[m] = 0.5 * (x[order[p]] + 1.0);
+      cos_phi[m] = c[j];
+      sin_phi[m] = s[j];
+      w[m] = 4.0 * pi * (0.5 * W[order[p]]) / n_azim;
+    }
+  return MOLC_OK;
+}
+
+molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, const molc_groups *groups,
+                        double ray_spacing, molc_layout layout, unsigned flags, molc_plan **out) {
+  if (!out) return fail(MOLC_ERR_INVALID_ARG, "create: out is NULL");
+  *out = nullptr;
+  if (!grid || !quad || !groups) return fail(MOLC_ERR_INVALID_ARG, "create: NULL argument");
+  const molc_grid g = *grid;
+  if (g.nx < 1 || g.ny < 1 || !finite_pos(g.lx) || !finite_pos(g.ly) || !std::isfinite(g.x0) ||
+      !std::isfinite(g.y0))
+    return fail(MOLC_ERR_INVALID_ARG, "create: bad grid");
+  if ((int64_t)g.nx * g.ny > (int64_t)1 << 28) return fail(MOLC_ERR_INVALID_ARG, "create: grid too large");
+  if (groups->G < 1 || groups->G > 4096) return fail(MOLC_ERR_INVALID_ARG, "create: need 1 <= G <= 4096");
+  if (!finite_pos(ray_spacing)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing must be > 0");
+  if (layout != MOLC_RAYS_UNIFORM && layout != MOLC_RAYS_PAPER) return fail(MOLC_ERR_INVALID_ARG, "create: layout");
+  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY)) return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
+  const int n = quad->n;
+  if (n < 2 || !quad->mu || !quad->cos_phi || !quad->sin_phi || !quad->w)
+    return fail(MOLC_ERR_INVALID_ARG, "create: bad quadrature");
+  for (int m = 0; m < n; ++m) {
+    if (!(quad->mu[m] > 0 && quad->mu[m] < 1) || !std::isfinite(quad->cos_phi[m]) ||
+        !std::isfinite(quad->sin_phi[m]) || (quad->cos_phi[m] == 0 && quad->sin_phi[m] == 0) ||
+        !finite_pos(quad->w[m]))
+      return fail(MOLC_ERR_INVALID_ARG, "create: direction %d: need 0 < mu < 1, a nonzero in-plane vector, w > 0", m);
+  }
+  if (ray_spacing * 1e7 < std::max(g.lx, g.ly)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing too small");
+
+  auto p = new molc_plan();
+  p->grid = g;
+  p->G = groups->G;
+  p->n_dir = n;
+  p->spacing = ray_spacing;
+  p->layout = layout;
+  p->flags = flags;
+  p->host_only = flags & MOLC_HOST_ONLY;
+  p->hx = g.lx / g.nx;
+  p->hy = g.ly / g.ny;
+  p->V = p->hx * p->hy;
+  if (!p->host_only) cudaGetDevice(&p->device);
+
+  // ---- azimuth pairs: + sense has sin > 0 (or sin == 0 and cos > 0); the - sense is its exact negation.
+  std::map<std::pair<double, double>, std::vector<int>> az;
+  std::vector<std::pair<double, double>> az_order;
+  for (int m = 0; m < n; ++m) {
+    auto key = std::make_pair(quad->cos_phi[m], quad->sin_phi[m]);
+    if (!az.count(key)) az_order.push_back(key);
+    az[key].push_back(m);
+  }
+  p->dir_pair.assign(n, -1);
+  p->dir_sense.assign(n, -1);
+  p->dir_polar.assign(n, -1);
+  for (auto &key : az_order) {
+    const double c = key.first, s = key.second;
+    if (!(s > 0 || (s == 0 && c > 0))) continue;
+    auto neg = std::make_pair(-c, -s);
+    if (!az.count(neg)) {
+      delete p;
+      return fail(MOLC_ERR_INVALID_ARG, "create: direction (%g, %g) has no exactly opposite direction", c, s);
+    }
+    const auto &plus = az[key], &minus = az[neg];
+    if (p->n_pairs == 0) p->n_polar = (int)plus.size();
+    if ((int)plus.size() != p->n_polar || minus.size() != plus.size()) {
+      delete p;
+      return fail(MOLC_ERR_INVALID_ARG, "create: every azimuth must carry the same number of polar cosines");
+    }
+    const int j = p->n_pairs++;
+    const double nrm = std::hypot(c, s);
+    PairDev pd;
+    pd.c = c / nrm;
+    pd.s = s / nrm;
+    pd.cf = (float)pd.c;
+    pd.sf = (float)pd.s;
+    p->pairs.push_back(pd);
+    std::vector<bool> used(minus.size(), false);
+    for (int q = 0; q < p->n_polar; ++q) {
+      const int mp = plus[q];
+      int mm = -1;
+      for (size_t r = 0; r < minus.size(); ++r)
+        if (!used[r] && quad->mu[minus[r]] == quad->mu[mp] && quad->w[minus[r]] == quad->w[mp]) {
+          mm = minus[r];
+          used[r] = true;
+          break;
+        }
+      if (mm < 0) {
+        delete p;
+        return fail(MOLC_ERR_INVALID_ARG, "create: direction %d has no opposite with equal mu and w", mp);
+      }
+      PolarDev pl;
+      const double mu = quad->mu[mp];
+      pl.w = quad->w[mp];
+      pl.sinz = std::sqrt(1.0 - mu * mu);
+      pl.inv_sinz = 1.0 / pl.sinz;
+      pl.wf = (float)pl.w;
+      pl.sinzf = (float)pl.sinz;
+      pl.inv_sinzf = (float)pl.inv_sinz;
+      pl.dir_plus = mp;
+      pl.dir_minus = mm;
+      p->polar.push_back(pl);
+      p->dir_pair[mp] = p->dir_pair[mm] = j;
+      p->dir_sense[mp] = 0;
+      p->dir_sense[mm] = 1;
+      p->dir_polar[mp] = p->dir_polar[mm] = q;
+    }
+  }
+  for (int m = 0; m < n; ++m)
+    if (p->dir_pair[m] < 0) {
+      delete p;
+      return fail(MOLC_ERR_INVALID_ARG, "create: direction %d is not paired", m);
+    }
+
+  // ---- characteristics and segments, pair by pair
+  const int ncell = g.nx * g.ny;
+  std::vector<double> t, wv;
+  std::vector<int> cells;
+  std::vector<double> lens;
+  p->pair_track_off.push_back(0);
+  for (int j = 0; j < p->n_pairs; ++j) {
+    const double c = p->pairs[j].c, s = p->pairs[j].s;
+    characteristic_offsets(g, c, s, ray_spacing, layout, t, wv);
+    for (size_t k = 0; k < t.size(); ++k) {
+      int ep, em;
+      if (!cut_characteristic(g, p->hx, p->hy, c, s, t[k], cells, lens, ep, em)) continue;
+      if (cells.size() > (size_t)1 << 30) {
+        delete p;
+        return fail(MOLC_ERR_INVALID_ARG, "create: characteristic too long");
+      }
+      HostTrack ht{wv[k], ep, em, (int64_t)p->seg_cell.size(), (int)cells.size()};
+      p->tracks.push_back(ht);
+      for (size_t q = 0; q < cells.size(); ++q) {
+        p->seg_cell.push_back(cells[q]);
+        p->seg_len.push_back(lens[q]);
+        p->seg_afrac.push_back(lens[q] * wv[k]);  // A for now
+      }
+    }
+    p->pair_track_off.push_back((int64_t)p->tracks.size());
+  }
+  const int64_t T = (int64_t)p->tracks.size();
+  const int64_t S = (int64_t)p->seg_cell.size();
+  if (T == 0) {
+    delete p;
+    return fail(MOLC_ERR_INVALID_ARG, "create: no characteristic crosses the domain");
+  }
+  // ---- areas (Eq. 14), optional renormalisation per (cell, pair), area fractions a = A / V, geometric moments
+  const bool renorm = flags & MOLC_AREA_RENORM;
+  std::vector<double> asum(ncell);
+  std::vector<Acc2> g0(ncell), gxx(ncell), gxy(ncell), gyy(ncell);
+  for (int j = 0; j < p->n_pairs; ++j) {
+    std::fill(asum.begin(), asum.end(), 0.0);
+    const int64_t s0 = p->tracks[p->pair_track_off[j]].seg_off;
+    const int64_t s1 = p->pair_track_off[j + 1] < T ? p->tracks[p->pair_track_off[j + 1]].seg_off : S;
+    for (int64_t q = s0; q < s1; ++q) asum[p->seg_cell[q]] += p->seg_afrac[q];
+    if (renorm) {
+      for (int i = 0; i < ncell; ++i)
+        if (!(asum[i] > 0)) {
+          delete p;
+          return fail(MOLC_ERR_INVALID_ARG,
+                      "create: cell %d is crossed by no characteristic of azimuth pair %d; reduce ray_spacing", i, j);
+        }
+      for (int64_t q = s0; q < s1; ++q) p->seg_afrac[q] /= asum[p->seg_cell[q]];
+    } else {
+      for (int64_t q = s0; q < s1; ++q) p->seg_afrac[q] /= p->V;
+    }
+    // sum over the pair's directions of omega (times Omega components) and over its segments of a
+    double w0 = 0, wxx = 0, wxy = 0, wyy = 0;
+    const double c = p->pairs[j].c, s = p->pairs[j].s;
+    for (int q = 0; q < p->n_polar; ++q) {
+      const PolarDev &pl = p->polar[(size_t)j * p->n_polar + q];
+      const double ww = 2.0 * pl.w, s2 = pl.sinz * pl.sinz;
+      w0 += ww;
+      wxx += ww * s2 * c * c;
+      wxy += ww * s2 * c * s;
+      wyy += ww * s2 * s * s;
+    }
+    for (int i = 0; i < ncell; ++i) {
+      const double a = renorm ? 1.0 : asum[i] / p->V;
+      g0[i].add(w0 * a);
+      gxx[i].add(wxx * a);
+      gxy[i].add(wxy * a);
+      gyy[i].add(wyy * a);
+    }
+  }
+  std::vector<double> geo(4 * (size_t)ncell);
+  for (int i = 0; i < ncell; ++i) {
+    geo[i] = g0[i].value();
+    geo[ncell + i] = gxx[i].value();
+    geo[2 * (size_t)ncell + i] = gxy[i].value();
+    geo[3 * (size_t)ncell + i] = gyy[i].value();
+  }
+
+  // ---- device track table with canonical offsets
+  std::vector<TrackDev> td(T);
+  std::vector<int64_t> pair_nseg(p->n_pairs, 0);
+  for (int j = 0; j < p->n_pairs; ++j)
+    for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) pair_nseg[j] += p->tracks[k].nseg;
+  for (int j = 0; j < p->n_pairs; ++j) {
+    const int64_t seg_base = p->tracks[p->pair_track_off[j]].seg_off;
+    for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) {
+      const HostTrack &h = p->tracks[k];
+      TrackDev &d = td[k];
+      d.seg_off = h.seg_off;
+      d.nseg = h.nseg;
+      d.pair = j;
+      d.entry_plus = h.entry_plus;
+      d.entry_minus = h.entry_minus;
+      d.canon_plus = h.seg_off - seg_base;
+      d.canon_minus = pair_nseg[j] - (h.seg_off - seg_base) - h.nseg;
+    }
+  }
+  p->dir_seg_off.assign(n + 1, 0);
+  for (int m = 0; m < n; ++m) p->dir_seg_off[m + 1] = p->dir_seg_off[m] + pair_nseg[p->dir_pair[m]];
+
+  std::vector<int4> seg32(S);
+  for (int64_t q = 0; q < S; ++q) {
+    float lf = (float)p->seg_len[q], af = (float)p->seg_afrac[q];
+    int4 r;
+    r.x = p->seg_cell[q];
+    std::memcpy(&r.y, &lf, 4);
+    std::memcpy(&r.z, &af, 4);
+    r.w = 0;
+    seg32[q] = r;
+  }
+
+  // ---- FP32 work items: one thread per (track, sense, group).  Groups are tiled in chunks whose cell table
+  // (20 B per cell and group) and FP64 accumulators (48 B) fit in half of the L2 cache; items are ordered
+  // chunk-major, then by decreasing track length, then track, sense and group.
+  int l2_bytes = 0;
+  if (!p->host_only) cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device);
+  if (l2_bytes <= 0) l2_bytes = 128 << 20;
+  const double per_group = 68.0 * ncell;
+  const int gc32 = std::max(1, std::min(p->G, (int)std::floor(0.5 * l2_bytes / per_group)));
+  const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
+  std::vector<int64_t> order(T);
+  for (int64_t k = 0; k < T; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return td[a].nseg > td[b].nseg; });
+  if (T > (int64_t)0x7fffffff) {
+    delete p;
+    return fail(MOLC_ERR_INVALID_ARG, "create: too many characteristics");
+  }
+  std::vector<int2> items;
+  items.reserve((size_t)T * 2 * p->G);
+  for (int ch = 0; ch < nch32; ++ch) {
+    const int gcount = std::min(gc32, p->G - ch * gc32);
+    for (int64_t k : order)
+      for (int sense = 0; sense < 2; ++sense)
+        for (int gi = 0; gi < gcount; ++gi) items.push_back(make_int2((int)k, sense | (gi << 1) | (ch << 16)));
+  }
+  p->n_items32 = (int64_t)items.size();
+  p->acc_elems = (size_t)ncell * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
+
+  PlanView &v = p->view;
+  v.nx = g.nx;
+  v.ny = g.ny;
+  v.ncell = ncell;
+  v.G = p->G;
+  v.n_pairs = p->n_pairs;
+  v.n_polar = p->n_polar;
+  v.n_tracks = T;
+  v.n_track_segments = S;
+  v.gc32 = gc32;
+  if (p->host_only) {
+    *out = p;
+    return MOLC_OK;
+  }
+  // ---- upload
+  molc_status st = MOLC_OK;
+  size_t &tot = p->device_bytes;
+#define UP(dst, src, cnt, what)                            \
+  if (st == MOLC_OK) st = upload(&p->dst, src, cnt, tot, what);
+  UP(d_tracks, td.data(), (size_t)T, "tracks")
+  UP(d_seg32, seg32.data(), (size_t)S, "segments")
+  UP(d_seg_cell, p->seg_cell.data(), (size_t)S, "segment cells")
+  UP(d_seg_len, p->seg_len.data(), (size_t)S, "segment lengths")
+  UP(d_seg_afrac, p->seg_afrac.data(), (size_t)S, "segment areas")
+  UP(d_pairs, p->pairs.data(), p->pairs.size(), "pairs")
+  UP(d_polar, p->polar.data(), p->polar.size(), "polar")
+  UP(d_geo, geo.data(), geo.size(), "geometric moments")
+  UP(d_dir_seg_off, p->dir_seg_off.data(), p->dir_seg_off.size(), "direction offsets")
+  UP(d_status, (const int *)nullptr, 1, "status")
+  UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
+  UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
+  UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
+  UP(d_items32, items.data(), items.size(), "items")
+#undef UP
+  if (st == MOLC_OK) {
+    cudaError_t e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) st = cuda_fail(e, "status");
+  }
+  if (st != MOLC_OK) {
+    free_device(p);
+    delete p;
+    return st;
+  }
+  v.tracks = p->d_tracks;
+  v.seg32 = p->d_seg32;
+  v.seg_cell = p->d_seg_cell;
+  v.seg_len = p->d_seg_len;
+  v.seg_afrac = p->d_seg_afrac;
+  v.pairs = p->d_pairs;
+  v.polar = p->d_polar;
+  v.geo = p->d_geo;
+  v.dir_seg_off = p->d_dir_seg_off;
+  v.status = p->d_status;
+  *out = p;
+  return MOLC_OK;
+}
+
+molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
+  if (!p || !info) return fail(MOLC_ERR_INVALID_ARG, "plan_get_info: NULL argument");
+  info->G = p->G;
+  info->nx = p->grid.nx;
+  info->ny = p->grid.ny;
+  info->n_dir = p->n_dir;
+  info->n_azim_pairs = p->n_pairs;
+  info->n_polar = p->n_polar;
+  info->n_tracks = p->view.n_tracks;
+  info->n_track_segments = p->view.n_track_segments;
+  info->n_segments = 2 * (int64_t)p->n_polar * p->view.n_track_segments;
+  info->n_updates = info->n_segments * p->G;
+  info->fp32_groups_per_warp = p->view.gc32;
+  info->device_bytes = p->device_bytes;
+  return MOLC_OK;
+}
+
+int64_t molc_intensity_count(const molc_plan *p) {
+  return p ? 2 * (int64_t)p->n_polar * p->view.n_track_segments * p->G : 0;
+}
+
+size_t molc_intensity_bytes(const molc_plan *p, molc_precision prec) {
+  if (!p) return 0;
+  return bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4) + (size_t)p->G * p->view.ncell * 8;
+}
+
+static double *bref_of(const molc_plan *p, molc_precision prec, void *I) {
+  return (double *)((char *)I + bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4));
+}
+
+static molc_status check_prec(const molc_plan *p, molc_precision prec, const char *who) {
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "%s: the plan was created with MOLC_HOST_ONLY", who);
+  if (prec != MOLC_FP64 && prec != MOLC_FP32) return fail(MOLC_ERR_INVALID_ARG, "%s: bad precision", who);
+  if (prec == MOLC_FP32 && p->n_polar > kMaxPolarFP32)
+    return fail(MOLC_ERR_INVALID_ARG, "%s: the FP32 sweep supports at most %d polar cosines per azimuth", who,
+                kMaxPolarFP32);
+  return MOLC_OK;
+}
+
+molc_status molc_intensity_init(molc_plan *p, molc_precision prec, void *I, const double *B, molc_stream stream) {
+  if (!p || !I || !B) return fail(MOLC_ERR_INVALID_ARG, "intensity_init: NULL argument");
+  molc_status s = check_prec(p, prec, "intensity_init");
+  if (s) return s;
+  DeviceGuard dg(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = (size_t)p->G * p->view.ncell * sizeof(double);
+  cudaError_t e = cudaMemsetAsync(I, 0, bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bref_of(p, prec, I), B, nb, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "intensity_init");
+}
+
+molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, const double *B, double c,
+                       double dt, void *I, const double *bnd, const molc_moments *out, molc_stream stream) {
+  if (!p || !kappa || !B || !I || !bnd || !out) return fail(MOLC_ERR_INVALID_ARG, "sweep: NULL argument");
+  if (!out->E || !out->Fx || !out->Fy || !out->Nxx || !out->Nxy || !out->Nyy)
+    return fail(MOLC_ERR_INVALID_ARG, "sweep: NULL moment array");
+  if (!finite_pos(c) || !finite_pos(dt)) return fail(MOLC_ERR_INVALID_ARG, "sweep: need c > 0 and dt > 0");
+  molc_status s = check_prec(p, prec, "sweep");
+  if (s) return s;
+  DeviceGuard dg(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  SweepArgs a{};
+  a.kappa = kappa;
+  a.B = B;
+  a.bnd = bnd;
+  a.c = c;
+  a.dt = dt;
+  a.I = I;
+  a.Bref = bref_of(p, prec, I);
+  a.out = *out;
+  a.cdat = p->d_cdat;
+  a.cdB = p->d_cdB;
+  a.acc = p->d_acc;
+  a.items = p->d_items32;
+  a.n_items = p->n_items32;
+  const Layout L = layout_for(p->view, prec);
+  cudaError_t e =
+      cudaMemsetAsync(p->d_acc, 0, (size_t)L.n_chunks * L.gc * p->view.ncell * kOutputs * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
+  e = launch_prep(p->view, prec, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep: prep");
+  const bool timed = p->timing && p->n_timed < kMaxTimed;
+  if (timed) cudaEventRecord(p->ev[2 * p->n_timed], st);
+  e = prec == MOLC_FP64 ? launch_sweep_fp64(p->view, a, st) : launch_sweep_fp32(p->view, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep: sweep kernel");
+  if (timed) cudaEventRecord(p->ev[2 * p->n_timed++ + 1], st);
+  e = launch_finalize(p->view, prec, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep: finalize");
+  return MOLC_OK;
+}
+
+molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, double *fxx, double *fxy,
+                         double *fyy, double *f_grey, molc_stream stream) {
+  if (!p || !m || !m->E || !m->Nxx || !m->Nxy || !m->Nyy || !fxx || !fxy || !fyy)
+    return fail(MOLC_ERR_INVALID_ARG, "closure: NULL argument");
+  if (!finite_pos(c)) return fail(MOLC_ERR_INVALID_ARG, "closure: need c > 0");
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "closure: the plan was created with MOLC_HOST_ONLY");
+  DeviceGuard dg(p->device);
+  cudaError_t e = launch_closure(p->view, *m, c, fxx, fxy, fyy, f_grey, (cudaStream_t)stream);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "closure");
+}
+
+static molc_status intensity_copy(const molc_plan *p, molc_precision prec, void *I, int g_begin, int g_count,
+                                  double *canon, const double *B, bool to_canon, molc_stream stream,
+                                  const char *who) {
+  if (!p || !I || !canon || (!to_canon && !B)) return fail(MOLC_ERR_INVALID_ARG, "%s: NULL argument", who);
+  molc_status s = check_prec(p, prec, who);
+  if (s) return s;
+  if (g_begin < 0 || g_count < 1 || g_begin + g_count > p->G)
+    return fail(MOLC_ERR_INVALID_ARG, "%s: group range [%d, %d) outside [0, %d)", who, g_begin, g_begin + g_count,
+                p->G);
+  DeviceGuard dg(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double *bref = bref_of(p, prec, I);
+  cudaError_t e = cudaSuccess;
+  if (!to_canon) {  // the imported groups refer to the given B from now on
+    const size_t off = (size_t)g_begin * p->view.ncell;
+    e = cudaMemcpyAsync(bref + off, B + off, (size_t)g_count * p->view.ncell * sizeof(double),
+                        cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = launch_intensity_copy(p->view, prec, I, bref, g_begin, g_count, canon, to_canon, st);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, who);
+}
+
+molc_status molc_intensity_export(const molc_plan *p, molc_precision prec, const void *I, int g_begin, int g_count,
+                                  double *canon, molc_stream stream) {
+  return intensity_copy(p, prec, const_cast<void *>(I), g_begin, g_count, canon, nullptr, true, stream,
+                        "intensity_export");
+}
+
+molc_status molc_intensity_import(molc_plan *p, molc_precision prec, void *I, int g_begin, int g_count,
+                                  const double *canon, const double *B, molc_stream stream) {
+  return intensity_copy(p, prec, I, g_begin, g_count, const_cast<double *>(canon), B, false, stream,
+                        "intensity_import");
+}
+
+molc_status molc_tracks_export(const molc_plan *p, int64_t *dir_ray_off, int64_t *ray_seg_off, double *width,
+                               int *entry, int *cell, double *len, double *area) {
+  if (!p || !dir_ray_off || !ray_seg_off || !width || !entry || !cell || !len || !area)
+    return fail(MOLC_ERR_INVALID_ARG, "tracks_export: NULL argument");
+  int64_t ri = 0, si = 0;
+  dir_ray_off[0] = 0;
+  ray_seg_off[0] = 0;
+  for (int m = 0; m < p->n_dir; ++m) {
+    const int j = p->dir_pair[m], sense = p->dir_sense[m];
+    const int64_t k0 = p->pair_track_off[j], k1 = p->pair_track_off[j + 1];
+    for (int64_t kk = 0; kk < k1 - k0; ++kk) {
+      const HostTrack &h = p->tracks[sense == 0 ? k0 + kk : k1 - 1 - kk];
+      width[ri] = h.width;
+      entry[ri] = sense == 0 ? h.entry_plus : h.entry_minus;
+      for (int q = 0; q < h.nseg; ++q, ++si) {
+        const int64_t sg = sense == 0 ? h.seg_off + q : h.seg_off + h.nseg - 1 - q;
+        cell[si] = p->seg_cell[sg];
+        len[si] = p->seg_len[sg];
+        area[si] = p->seg_afrac[sg] * p->V;
+      }
+      ray_seg_off[++ri] = si;
+    }
+    dir_ray_off[m + 1] = ri;
+  }
+  return MOLC_OK;
+}
+
+molc_status molc_kernel_timing(molc_plan *p, int enable) {
+  if (!p) return fail(MOLC_ERR_INVALID_ARG, "kernel_timing: NULL plan");
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "kernel_timing: the plan was created with MOLC_HOST_ONLY");
+  DeviceGuard dg(p->device);
+  if (enable && p->ev.empty()) {
+    p->ev.resize(2 * kMaxTimed);
+    for (auto &e : p->ev) {
+      cudaError_t r = cudaEventCreate(&e);
+      if (r != cudaSuccess) {
+        e = nullptr;
+        return cuda_fail(r, "kernel_timing");
+      }
+    }
+  }
+  p->timing = enable != 0;
+  p->n_timed = 0;
+  return MOLC_OK;
+}
+
+molc_status molc_kernel_time(molc_plan *p, double *total_ms, int *launches) {
+  if (!p || !total_ms || !launches) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: NULL argument");
+  DeviceGuard dg(p->device);
+  double tot = 0;
+  if (p->n_timed > 0) {
+    cudaError_t r = cudaEventSynchronize(p->ev[2 * p->n_timed - 1]);
+    if (r != cudaSuccess) return cuda_fail(r, "kernel_time");
+    for (int i = 0; i < p->n_timed; ++i) {
+      float ms = 0;
+      r = cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]);
+      if (r != cudaSuccess) return cuda_fail(r, "kernel_time");
+      tot += ms;
+    }
+  }
+  *total_ms = tot;
+  *launches = p->n_timed;
+  p->n_timed = 0;
+  return MOLC_OK;
+}
+
+molc_status molc_device_status(molc_plan *p, int *code) {
+  if (!p || !code) return fail(MOLC_ERR_INVALID_ARG, "device_status: NULL argument");
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "device_status: the plan was created with MOLC_HOST_ONLY");
+  DeviceGuard dg(p->device);
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "device_status");
+  e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "device_status");
+  *code = (h & kStatusNonfinite) ? MOLC_ERR_NONFINITE_INPUT : MOLC_OK;
+  return MOLC_OK;
+}
+
+void molc_destroy(molc_plan *p) {
+  if (!p) return;
+  if (p->host_only) {
+    delete p;
+    return;
+  }
+  DeviceGuard dg(p->device);
+  free_device(p);
+  delete p;
+}
+
+}  // extern "C"

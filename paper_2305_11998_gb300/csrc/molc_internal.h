@@ -1,0 +1,101 @@
+// Internal declarations shared by the host planner (molc_host.cpp) and the CUDA kernels (molc_kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "molc.h"
+
+namespace molc {
+
+constexpr int kMaxPolarFP32 = 8;     // FP32 sweep: polar cosines per azimuth handled by one half-warp
+constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators per (cell, group)
+
+// Device status bits (the first one set wins in molc_device_status).
+constexpr int kStatusNonfinite = 1;
+
+// One characteristic (track) of an azimuth pair; the + sense walks its segments forward, the - sense backward.
+struct TrackDev {
+  int64_t seg_off;      // first segment in the track-segment arrays
+  int nseg;
+  int pair;             // azimuth pair
+  int entry_plus;       // edge the + sense enters through (0 L, 1 R, 2 B, 3 T)
+  int entry_minus;      // edge the - sense enters through (= exit edge of the + sense)
+  int64_t canon_plus;   // offset of this track's segments within the + sense direction's canonical block
+  int64_t canon_minus;  // same for the - sense (tracks are in reverse order there)
+};
+
+struct PairDev {
+  double c, s;          // + sense in-plane direction (unit)
+  float cf, sf;
+};
+
+struct PolarDev {       // per (pair, polar cosine)
+  double w;             // omega of each of the two directions (+ and - sense)
+  double sinz, inv_sinz;
+  float wf, sinzf, inv_sinzf;
+  int dir_plus, dir_minus;  // quadrature indices of the two directions
+};
+
+// Everything a kernel needs, by value.
+struct PlanView {
+  int nx, ny, ncell, G, n_pairs, n_polar;
+  int64_t n_tracks, n_track_segments;
+  const TrackDev *tracks;
+  const int4 *seg32;            // {cell, len (f32 bits), a/V (f32 bits), 0}
+  const int *seg_cell;          // FP64 path
+  const double *seg_len;
+  const double *seg_afrac;      // A / V (area fraction of the cell, after renormalisation)
+  const PairDev *pairs;
+  const PolarDev *polar;        // [pair][p]
+  const double *geo;            // [4][cell]: sum_m omega sum_{C(i,m)} a times 1, Ox^2, OxOy, Oy^2
+  const int64_t *dir_seg_off;   // canonical segment offset of each direction
+  int *status;
+  int gc32;                     // FP32 sweep: groups per chunk (keeps a chunk's atomics L2-resident)
+};
+
+// Layout of the opaque intensity state: groups are tiled in chunks of `gc` groups; within a chunk, rows of
+// width gcount*n_polar are ordered (track, sense, step); element (chunk, row, g_local, p).
+struct Layout {
+  int gc;                  // groups per chunk (FP64: G, FP32: PlanView::gc32)
+  int n_chunks;
+  int64_t rows;            // 2 * n_track_segments
+};
+
+inline Layout layout_for(const PlanView &v, molc_precision prec) {
+  Layout L;
+  L.gc = prec == MOLC_FP64 ? v.G : v.gc32;
+  if (L.gc > v.G) L.gc = v.G;
+  L.n_chunks = (v.G + L.gc - 1) / L.gc;
+  L.rows = 2 * v.n_track_segments;
+  return L;
+}
+
+// Byte offset of the reference Planck block inside an intensity state of `count` elements of `esize` bytes.
+inline size_t bref_offset(int64_t count, int esize) { return ((size_t)count * esize + 255) / 256 * 256; }
+
+struct SweepArgs {
+  const double *kappa, *B, *bnd;
+  double c, dt;
+  void *I;            // deviations delta = Ibar - B_ref, [chunk][row][g_local][p]
+  double *Bref;       // [G][cell] Planck intensity the deviations refer to (inside the state)
+  molc_moments out;
+  float4 *cdat;       // FP32: [chunk][cell][gc] {kappa~, 1/(c dt kappa~), B_hi, B_lo}
+  float *cdB;         // FP32: [chunk][cell][gc] (B_ref - B) / (c dt kappa~)
+  double *acc;        // [chunk][cell][6][gc] FP64 accumulators
+  const int2 *items;  // FP32: one per thread, {track, sense | g_local << 1 | chunk << 16}; chunk-major,
+                      // longest track first, then sense, then group
+  int64_t n_items;
+};
+
+// Kernel launchers (molc_kernels.cu).  Return cudaSuccess or the launch error.
+cudaError_t launch_prep(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st);
+cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
+                           double *fyy, double *f_grey, cudaStream_t st);
+cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
+                                  int g_begin, int g_count, double *canon, bool to_canon, cudaStream_t st);
+
+}  // namespace molc

@@ -1,0 +1,436 @@
+// CUDA kernels of libmolc (sm_103a): the MOLC high-order sweep of Sec. 3 in two precisions, the cell
+// assembly of the moments, the Eddington closure and the intensity-state utilities.
+//
+// Both sweeps walk each characteristic in the deviation form psi = I - B_i (B_i the Planck intensity of
+// the current cell).  With S = Q / kappa~ (Eq. 11) and E1(tau) = (1 - e^-tau) / tau, Eqs. (12)-(13) become
+//     psi_out  = d + (psi_in - d) e^-tau,     psibar = d + (psi_in - d) E1(tau),
+//     d = S - B_i = (I^{n-1} - B_i) / (c dt kappa~),
+// (alpha I_s + (1 - alpha) I_{s+1} = S + (I_s - S) E1 exactly), and at a cell crossing
+// psi_in(next) = psi_out + (B_prev - B_next).  The stored state is the deviation delta = Ibar - B_ref of each
+// segment average from the Planck intensity B_ref its cell had when it was written, so
+// d = (delta + B_ref - B) / (c dt kappa~) keeps the precision of the deviation (exactly 0 after
+// molc_intensity_init, in any precision).  The cell moments then carry the deviations, and the B_i part
+// is added analytically from per-cell geometric moments (it cancels exactly in F: the two senses of a track
+// have opposite Omega and equal areas).  This keeps the cancelling sums F and N_xy accurate in optically
+// thick cells, where |F| can be ~1e-8 c E.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "molc_internal.h"
+
+namespace molc {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ bool bad_input(double x) { return !(x >= 0.0) || !isfinite(x); }
+
+// Track holding row r of the intensity layout (rows are (track, sense, step); a track owns 2 nseg rows).
+__device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int64_t row) {
+  int64_t lo = 0, hi = T - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (2 * tr[mid].seg_off <= row)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// prep: input checks; FP32 path also tabulates per (chunk, cell, group) {kappa~, 1/(c dt kappa~), B_hi, B_lo}
+// with B = B_hi + B_lo split so that B differences between neighbouring cells keep ~48 bits.
+// ---------------------------------------------------------------------------------------------------------
+__global__ void prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
+  const int64_t n = (int64_t)v.G * v.ncell;
+  const double inv_cdt = 1.0 / (a.c * a.dt);
+  bool bad = false;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(idx / v.ncell);
+    const int cell = (int)(idx - (int64_t)g * v.ncell);
+    const double kap = a.kappa[idx], B = a.B[idx];
+    bad |= bad_input(kap) | bad_input(B);
+    if (fp32) {
+      const double kt = kap + inv_cdt;
+      const double r = inv_cdt / kt;
+      const float bhi = (float)B;
+      const float blo = (float)(B - (double)bhi);
+      const int ch = g / L.gc, gl = g - ch * L.gc;
+      const int64_t o = ((int64_t)ch * v.ncell + cell) * L.gc + gl;
+      a.cdat[o] = make_float4((float)kt, (float)r, bhi, blo);
+      a.cdB[o] = (float)((a.Bref[idx] - B) * r);
+    }
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * (int64_t)v.G;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= bad_input(a.bnd[i]);
+  if (bad) atomicOr(v.status, kStatusNonfinite);
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// FP64 plain sweep: one thread per (track, sense, group, polar cosine), all arithmetic in FP64, one FP64
+// atomic per output and update into the [cell][6][G] accumulators.
+// ---------------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a) {
+  const int NP = v.n_polar, Q = v.G * NP;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= v.n_tracks * 2 * Q) return;
+  const int q = (int)(idx % Q);
+  const int64_t rest = idx / Q;
+  const int sense = (int)(rest & 1);
+  const int64_t t = rest >> 1;
+  const int g = q / NP, p = q - g * NP;
+  const TrackDev tr = v.tracks[t];
+  const PolarDev pd = v.polar[tr.pair * NP + p];
+  const PairDev pr = v.pairs[tr.pair];
+  const double sg = sense ? -1.0 : 1.0;
+  const double Ox = sg * pd.sinz * pr.c, Oy = sg * pd.sinz * pr.s;
+  const double inv_cdt = 1.0 / (a.c * a.dt);
+  const double *kap = a.kappa + (int64_t)g * v.ncell;
+  const double *Bg = a.B + (int64_t)g * v.ncell;
+  const double *Bref = a.Bref + (int64_t)g * v.ncell;
+  double *I = (double *)a.I + (2 * tr.seg_off + (int64_t)sense * tr.nseg) * Q + q;
+  const int nseg = tr.nseg;
+  const double Iin = a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g];
+  double psi = 0.0, Bprev = 0.0;
+  for (int s = 0; s < nseg; ++s) {
+    const int64_t sgi = sense ? tr.seg_off + nseg - 1 - s : tr.seg_off + s;
+    const int cell = v.seg_cell[sgi];
+    const double len = v.seg_len[sgi], af = v.seg_afrac[sgi];
+    const double Bc = Bg[cell];
+    const double kt = kap[cell] + inv_cdt;
+    psi = s == 0 ? Iin - Bc : psi + (Bprev - Bc);
+    const double d = (I[(int64_t)s * Q] + (Bref[cell] - Bc)) * (inv_cdt / kt);
+    const double tau = kt * len * pd.inv_sinz;
+    const double one_m_e = -expm1(-tau);
+    const double ex = exp(-tau);
+    const double E1 = one_m_e / tau;
+    const double x = psi - d;
+    const double pb = fma(x, E1, d);
+    psi = fma(x, ex, d);
+    I[(int64_t)s * Q] = pb;
+    const double wv = pd.w * af * pb;
+    double *acc = a.acc + (int64_t)cell * kOutputs * v.G + g;
+    atomicAdd(acc + 0 * v.G, wv);
+    atomicAdd(acc + 1 * v.G, wv * Ox);
+    atomicAdd(acc + 2 * v.G, wv * Oy);
+    atomicAdd(acc + 3 * v.G, wv * Ox * Ox);
+    atomicAdd(acc + 4 * v.G, wv * Ox * Oy);
+    atomicAdd(acc + 5 * v.G, wv * Oy * Oy);
+    Bprev = Bc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// FP32 production sweep.  One thread per (track, sense, group): the thread walks its track in its sense and
+// carries all NP polar cosines of the azimuth in registers (the in-plane track is shared by them).  Threads of
+// a warp hold consecutive groups of the same track-sense, so the cell table gathers, the previous-step
+// deviations (NP contiguous values per thread, vector loads) and the atomics are coalesced.  Groups are
+// processed in chunks (chunk-major item order) so that a chunk's cell table and FP64 accumulators stay
+// resident in L2 while the deviations stream through HBM.
+// ---------------------------------------------------------------------------------------------------------
+constexpr int kSweepBlock = 128;
+
+// (1 - e^-tau)/tau and e^-tau in FP32: a degree-8 Taylor polynomial below tau = 1/2 (truncation < 6e-10
+// relative), ex2.approx above (no cancellation there: 1 - e^-tau > 0.39).  inv_tau is 1/tau.
+__device__ __forceinline__ void attenuation(float tau, float inv_tau, float &E1, float &ex) {
+  float p = 1.f / 362880.f;
+  p = fmaf(p, tau, -1.f / 40320.f);
+  p = fmaf(p, tau, 1.f / 5040.f);
+  p = fmaf(p, tau, -1.f / 720.f);
+  p = fmaf(p, tau, 1.f / 120.f);
+  p = fmaf(p, tau, -1.f / 24.f);
+  p = fmaf(p, tau, 1.f / 6.f);
+  p = fmaf(p, tau, -0.5f);
+  p = fmaf(p, tau, 1.f);
+  const float e = __expf(-tau);
+  const bool small = tau < 0.5f;
+  ex = small ? fmaf(-tau, p, 1.f) : e;
+  E1 = small ? p : (1.f - e) * inv_tau;
+}
+
+// FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU).  Exact for normal
+// numbers; zeros and subnormals (|x| < 2^-126) map to a value of magnitude < 2^-126 with the same sign.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+template <int NP>
+__device__ __forceinline__ void load_dev(const float *p, float (&v)[NP]) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4) {
+      const float4 t = __ldcs(reinterpret_cast<const float4 *>(p + i));
+      v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
+    }
+  } else if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2) {
+      const float2 t = __ldcs(reinterpret_cast<const float2 *>(p + i));
+      v[i] = t.x; v[i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) v[i] = __ldcs(p + i);
+  }
+}
+template <int NP>
+__device__ __forceinline__ void store_dev(float *p, const float (&v)[NP]) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4)
+      __stcs(reinterpret_cast<float4 *>(p + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+  } else if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2) __stcs(reinterpret_cast<float2 *>(p + i), make_float2(v[i], v[i + 1]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) __stcs(p + i, v[i]);
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+  const int64_t item = (int64_t)blockIdx.x * kSweepBlock + threadIdx.x;
+  const bool live = item < a.n_items;
+  const int2 it = live ? a.items[item] : make_int2(0, 0);
+  const TrackDev tr = v.tracks[it.x];
+  const int sense = it.y & 1, gi = (it.y >> 1) & 0x7fff, ch = it.y >> 16;
+  const int g0 = ch * L.gc;
+  const int gcount = min(L.gc, v.G - g0);
+  const int g = g0 + gi;
+  const int W = gcount * NP;
+  const int nseg = live ? tr.nseg : 0;
+  // warp-uniform trip count
+  int nmax = nseg;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+
+  float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W + gi * NP;
+  const int4 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
+  const int rstep = sense ? -1 : 1;
+  const int64_t cbase = (int64_t)ch * v.ncell * L.gc + gi;
+  const float4 *cd = a.cdat + cbase;
+  const float *cdB = a.cdB + cbase;
+  double *acc = a.acc + (int64_t)ch * v.ncell * kOutputs * L.gc + gi;
+
+  float inv_sinz[NP], sinz[NP], w0[NP], w1[NP], w2[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const PolarDev pd = v.polar[tr.pair * NP + p];
+    inv_sinz[p] = pd.inv_sinzf;
+    sinz[p] = pd.sinzf;
+    w0[p] = pd.wf;
+    w1[p] = pd.wf * pd.sinzf;
+    w2[p] = pd.wf * pd.sinzf * pd.sinzf;
+  }
+  const PairDev pr = v.pairs[tr.pair];
+  const float sg = sense ? -1.f : 1.f;
+  const float fx = sg * pr.cf, fy = sg * pr.sf, fxx = pr.cf * pr.cf, fxy = pr.cf * pr.sf, fyy = pr.sf * pr.sf;
+  // entering intensity, split like B so that I_in - B keeps the precision of the difference
+  const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] : 0.0;
+  const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
+
+  float psi[NP];
+  float bhi_prev = 0.f, blo_prev = 0.f;
+  int4 r = live && nseg > 0 ? __ldg(rec) : make_int4(0, 0, 0, 0);
+  for (int s = 0; s < nmax; ++s) {
+    if (s < nseg) {
+      const int cell = r.x;
+      const float len = __int_as_float(r.y), af = __int_as_float(r.z);
+      if (s + 1 < nseg) r = __ldg(rec + (s + 1) * rstep);
+      const float4 q = __ldg(cd + (int64_t)cell * L.gc);
+      const float dB = __ldg(cdB + (int64_t)cell * L.gc);
+      float dv[NP];
+      load_dev<NP>(I, dv);
+      const float jump = s == 0 ? (in_hi - q.z) + (in_lo - q.w) : (bhi_prev - q.z) + (blo_prev - q.w);
+      const float kl = q.x * len;
+      const float rkl = __frcp_rn(kl);
+      float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        psi[p] = s == 0 ? jump : psi[p] + jump;
+        float E1, ex;
+        attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
+        const float d = fmaf(dv[p], q.y, dB);
+        const float x = psi[p] - d;
+        const float pb = fmaf(x, E1, d);
+        psi[p] = fmaf(x, ex, d);
+        dv[p] = pb;
+        S0 = fmaf(w0[p], pb, S0);
+        S1 = fmaf(w1[p], pb, S1);
+        S2 = fmaf(w2[p], pb, S2);
+      }
+      store_dev<NP>(I, dv);
+      S0 *= af;
+      S1 *= af;
+      S2 *= af;
+      double *ac = acc + (int64_t)cell * (kOutputs * L.gc);
+      atomicAdd(ac, f32_to_f64(S0));
+      atomicAdd(ac + L.gc, f32_to_f64(fx * S1));
+      atomicAdd(ac + 2 * L.gc, f32_to_f64(fy * S1));
+      atomicAdd(ac + 3 * L.gc, f32_to_f64(fxx * S2));
+      atomicAdd(ac + 4 * L.gc, f32_to_f64(fxy * S2));
+      atomicAdd(ac + 5 * L.gc, f32_to_f64(fyy * S2));
+      bhi_prev = q.z;
+      blo_prev = q.w;
+      I += W;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// finalize: cell assembly.  acc holds sum_m omega_m sum_{C(i,m)} (A/V) psibar (times Omega components);
+// the B_i part uses the geometric moments geo = sum_m omega_m sum_{C(i,m)} A/V (times Omega components).
+//   E = (B geo0 + D)/c, F = acc, N_ab = B geo_ab + acc_ab.  (The B part of F is zero by symmetry.)
+// ---------------------------------------------------------------------------------------------------------
+__global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
+  const int64_t n = (int64_t)v.G * v.ncell;
+  const double inv_c = 1.0 / a.c;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(idx / v.ncell);
+    const int cell = (int)(idx - (int64_t)g * v.ncell);
+    const int ch = g / L.gc, gl = g - ch * L.gc;
+    const double *ac = a.acc + ((int64_t)ch * v.ncell + cell) * kOutputs * L.gc + gl;
+    const double B = a.B[idx];
+    a.out.E[idx] = (B * v.geo[cell] + ac[0 * L.gc]) * inv_c;
+    a.out.Fx[idx] = ac[1 * L.gc];
+    a.out.Fy[idx] = ac[2 * L.gc];
+    a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + ac[3 * L.gc];
+    a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + ac[4 * L.gc];
+    a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + ac[5 * L.gc];
+    a.Bref[idx] = B;   // the new deviations refer to this step's B
+  }
+}
+
+// f = N / (c E) per group (Eq. 7 with the cell averages of Eq. 15); <f>_E = sum_g N_g / (c sum_g E_g).
+__global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx, double *fxy, double *fyy,
+                               double *fgrey) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
+    double se = 0, sxx = 0, sxy = 0, syy = 0;
+    for (int g = 0; g < v.G; ++g) {
+      const int64_t i = (int64_t)g * v.ncell + cell;
+      const double E = m.E[i], nxx = m.Nxx[i], nxy = m.Nxy[i], nyy = m.Nyy[i];
+      const double inv = E > 0 ? 1.0 / (c * E) : 0.0;
+      fxx[i] = nxx * inv;
+      fxy[i] = nxy * inv;
+      fyy[i] = nyy * inv;
+      se += E;
+      sxx += nxx;
+      sxy += nxy;
+      syy += nyy;
+    }
+    if (fgrey) {
+      const double inv = se > 0 ? 1.0 / (c * se) : 0.0;
+      fgrey[cell] = sxx * inv;
+      fgrey[v.ncell + cell] = sxy * inv;
+      fgrey[2 * (int64_t)v.ncell + cell] = syy * inv;
+    }
+  }
+}
+
+// Canonical segment averages <-> deviation state: one thread per row (track, sense, step) of the layout,
+// looping over polar cosines and the selected groups.  Ibar = B_ref(cell) + delta.
+template <class T>
+__global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *Bref, int g_begin, int g_count,
+                                      double *canon, int to_canon) {
+  const int NP = v.n_polar;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < L.rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = find_track(v.tracks, v.n_tracks, row);
+    const TrackDev tr = v.tracks[t];
+    const int64_t local = row - 2 * tr.seg_off;
+    const int sense = local >= tr.nseg;
+    const int s = (int)(local - (int64_t)sense * tr.nseg);
+    const int cell = v.seg_cell[sense ? tr.seg_off + tr.nseg - 1 - s : tr.seg_off + s];
+    for (int p = 0; p < NP; ++p) {
+      const PolarDev pd = v.polar[tr.pair * NP + p];
+      const int dir = sense ? pd.dir_minus : pd.dir_plus;
+      const int64_t cs = v.dir_seg_off[dir] + (sense ? tr.canon_minus : tr.canon_plus) + s;
+      for (int g = g_begin; g < g_begin + g_count; ++g) {
+        const int ch = g / L.gc, gl = g - ch * L.gc, gcount = min(L.gc, v.G - ch * L.gc);
+        T *el = I + L.rows * (int64_t)NP * (ch * L.gc) + row * (int64_t)(gcount * NP) + gl * NP + p;
+        const double br = Bref[(int64_t)g * v.ncell + cell];
+        double *cv = canon + cs * g_count + (g - g_begin);
+        if (to_canon)
+          *cv = br + (double)*el;
+        else
+          *el = (T)(*cv - br);
+      }
+    }
+  }
+}
+
+int grid_for(int64_t n, int block) {
+  int64_t b = (n + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
+  const Layout L = layout_for(v, prec);
+  prep_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(v, a, L, prec == MOLC_FP32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
+  const int64_t threads = v.n_tracks * 2 * (int64_t)v.G * v.n_polar;
+  const int64_t blocks = (threads + 127) / 128;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  sweep_fp64_kernel<<<(unsigned)blocks, 128, 0, st>>>(v, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
+  const Layout L = layout_for(v, MOLC_FP32);
+  const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)blocks), block(kSweepBlock);
+  switch (v.n_polar) {
+    case 1: sweep_fp32_kernel<1><<<grid, block, 0, st>>>(v, a, L); break;
+    case 2: sweep_fp32_kernel<2><<<grid, block, 0, st>>>(v, a, L); break;
+    case 3: sweep_fp32_kernel<3><<<grid, block, 0, st>>>(v, a, L); break;
+    case 4: sweep_fp32_kernel<4><<<grid, block, 0, st>>>(v, a, L); break;
+    case 5: sweep_fp32_kernel<5><<<grid, block, 0, st>>>(v, a, L); break;
+    case 6: sweep_fp32_kernel<6><<<grid, block, 0, st>>>(v, a, L); break;
+    case 7: sweep_fp32_kernel<7><<<grid, block, 0, st>>>(v, a, L); break;
+    case 8: sweep_fp32_kernel<8><<<grid, block, 0, st>>>(v, a, L); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
+  finalize_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(v, a, layout_for(v, prec));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
+                           double *fyy, double *f_grey, cudaStream_t st) {
+  closure_kernel<<<grid_for(v.ncell, 256), 256, 0, st>>>(v, m, c, fxx, fxy, fyy, f_grey);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
+                                  int g_begin, int g_count, double *canon, bool to_canon, cudaStream_t st) {
+  const Layout L = layout_for(v, prec);
+  if (prec == MOLC_FP64)
+    intensity_copy_kernel<double><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (double *)I, Bref, g_begin,
+                                                                         g_count, canon, to_canon);
+  else
+    intensity_copy_kernel<float><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (float *)I, Bref, g_begin,
+                                                                       g_count, canon, to_canon);
+  return cudaGetLastError();
+}
+
+}  // namespace molc

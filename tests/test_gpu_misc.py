@@ -1,0 +1,189 @@
+"""GPU: full-size parity on sampled groups, closure, state export/import, symmetry, device status."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import parity
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def molc():
+    import paper_2305_11998_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def host(d):
+    return {k: v.cpu().numpy() for k, v in d.items()}
+
+
+def test_full_size_512_sampled_groups(molc):
+    """The production workload (512^2, 17 groups, 128 directions, h/2, three fronts) in the launch
+    configuration the benchmark times; groups 0, 8 and 16 checked against the double oracle."""
+    wl = synth.WORKLOADS["fc512_g17_d128"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity("fp32")
+    P.intensity_init("fp32", I, B)
+    got = host(P.sweep("fp32", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"])))
+    assert P.device_status() == 0
+    n_upd = P.info.n_updates
+    P.close()
+    del I
+    torch.cuda.empty_cache()
+    assert n_upd > 1.4e9
+    groups = [0, 8, 16]
+    geom = oracle.Geometry.from_workload(wl)
+    ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="double",
+                       want_I=False)
+    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"])
+
+
+def test_closure_and_grey_average(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(3)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity("fp64")
+    P.intensity_init("fp64", I, B)
+    m = P.sweep("fp64", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"]))
+    f = P.closure(m, d["c"], grey=True)
+    mh = host(m)
+    cE = d["c"] * mh["E"]
+    for k, n in (("fxx", "Nxx"), ("fxy", "Nxy"), ("fyy", "Nyy")):
+        assert np.allclose(f[k].cpu().numpy(), mh[n] / cE, rtol=1e-15, atol=0)
+    g = f["grey"].cpu().numpy()
+    # <f>_E = sum_g f_g E_g / sum_g E_g   (Eq. 8)
+    for i, k in enumerate(("fxx", "fxy", "fyy")):
+        ref = (f[k].cpu().numpy() * mh["E"]).sum(0) / mh["E"].sum(0)
+        assert np.allclose(g[i], ref, rtol=1e-13, atol=1e-16)
+    # trace bound of the closure
+    fx, fy = f["fxx"].cpu().numpy(), f["fyy"].cpu().numpy()
+    assert np.all((fx >= 0) & (fy >= 0) & (fx + fy <= 1 + 1e-12))
+    P.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_export_import_roundtrip(molc, prec):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity(prec)
+    rng = np.random.default_rng(0)
+    canon = rng.uniform(0.0, 1.0, (P.info.n_segments, wl.G)) * d["B"].max()
+    P.intensity_init(prec, I, B)
+    P.intensity_import(prec, I, dev(canon), B)
+    back = P.intensity_export(prec, I).cpu().numpy()
+    tol = 1e-15 if prec == "fp64" else 2e-7
+    assert np.max(np.abs(back - canon)) <= tol * np.abs(canon).max()
+    # a partial group range leaves the others alone
+    before = P.intensity_export(prec, I).cpu().numpy()
+    P.intensity_import(prec, I, dev(np.zeros((P.info.n_segments, 1))), B, g_begin=2)
+    after = P.intensity_export(prec, I).cpu().numpy()
+    assert np.array_equal(after[:, [0, 1, 3]], before[:, [0, 1, 3]]) and np.all(after[:, 2] == 0)
+    # a swept state imported into a fresh buffer gives the same next step
+    k, bnd = dev(d["kappa"]), dev(d["bnd"])
+    P.intensity_init(prec, I, B)
+    P.sweep(prec, k, B, d["c"], d["dt"], I, bnd)
+    snap = P.intensity_export(prec, I)
+    J = P.new_intensity(prec)
+    P.intensity_init(prec, J, B)
+    P.intensity_import(prec, J, snap, B)
+    a = host(P.sweep(prec, k, B, d["c"], d["dt"], I, bnd))
+    b = host(P.sweep(prec, k, B, d["c"], d["dt"], J, bnd))
+    for kk in a:
+        assert np.allclose(a[kk], b[kk], rtol=1e-12 if prec == "fp64" else 1e-5, atol=1e-30)
+    P.close()
+
+
+def _rot(a, n):
+    a = a.reshape(a.shape[:-1] + (n, n))
+    out = np.empty_like(a)
+    for iy in range(n):
+        for ix in range(n):
+            out[..., ix, n - 1 - iy] = a[..., iy, ix]
+    return out.reshape(a.shape[:-2] + (n * n,))
+
+
+def test_rotation_symmetry_on_gpu(molc):
+    wl = synth.Workload("sym", 12, 12, 6.0, 3, 0.01, 10.0, 2, 16, 2, 1)
+    d = wl.inputs(4)
+    n = wl.nx
+    P = molc.Plan.from_workload(wl)
+
+    def step(kappa, B, bnd):
+        Bd = dev(B)
+        I = P.new_intensity("fp64")
+        P.intensity_init("fp64", I, Bd)
+        return host(P.sweep("fp64", dev(kappa), Bd, d["c"], d["dt"], I, dev(bnd)))
+
+    base = step(d["kappa"], d["B"], d["bnd"])
+    bnd_r = np.zeros_like(d["bnd"])
+    bnd_r[synth.EDGE_BOTTOM] = d["bnd"][synth.EDGE_LEFT]
+    rot = step(_rot(d["kappa"], n), _rot(d["B"], n), bnd_r)
+    cE = _rot(d["c"] * base["E"], n)
+    exp = {"E": base["E"], "Fx": -base["Fy"], "Fy": base["Fx"], "Nxx": base["Nyy"], "Nyy": base["Nxx"],
+           "Nxy": -base["Nxy"]}
+    for k, v in exp.items():
+        assert np.max(np.abs(rot[k] - _rot(v, n)) / cE) < 1e-13, k
+    P.close()
+
+
+def test_device_status_flags_bad_inputs(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    bnd = dev(d["bnd"])
+    for prec in ("fp64", "fp32"):
+        I = P.new_intensity(prec)
+        P.intensity_init(prec, I, B)
+        P.sweep(prec, dev(d["kappa"]), B, d["c"], d["dt"], I, bnd)
+        assert P.device_status() == 0
+        bad = d["kappa"].copy()
+        bad[1, 17] = np.nan
+        P.sweep(prec, dev(bad), B, d["c"], d["dt"], I, bnd)
+        assert P.device_status() == 4
+        assert P.device_status() == 0          # reading clears it
+        badB = d["B"].copy()
+        badB[0, 3] = -1.0
+        P.sweep(prec, dev(d["kappa"]), dev(badB), d["c"], d["dt"], I, bnd)
+        assert P.device_status() == 4
+        badb = d["bnd"].copy()
+        badb[2, 1] = np.inf
+        P.sweep(prec, dev(d["kappa"]), B, d["c"], d["dt"], I, dev(badb))
+        assert P.device_status() == 4
+    with pytest.raises(molc.MolcError) as e:
+        P.sweep("fp32", dev(d["kappa"]), B, -1.0, d["dt"], I, bnd)
+    assert e.value.code == 1
+    P.close()
+
+
+def test_kernel_timing_hook(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity("fp32")
+    P.intensity_init("fp32", I, B)
+    P.kernel_timing(True)
+    for _ in range(3):
+        P.sweep("fp32", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"]))
+    ms, n = P.kernel_time()
+    assert n == 3 and ms > 0
+    P.kernel_timing(False)
+    P.sweep("fp32", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"]))
+    assert P.kernel_time() == (0.0, 0)
+    P.close()
