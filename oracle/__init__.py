@@ -30,7 +30,8 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", _OUT + ".tmp", _SRC]
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", _OUT + ".tmp",
+           _SRC]
     if platform.machine() in ("x86_64", "AMD64"):
         cmd.append("-lquadmath")
     subprocess.run(cmd, check=True)
@@ -56,7 +57,7 @@ def _load():
         lib.oracle_count.argtypes = [C.POINTER(_Geom), i64p]
         lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp]
         lib.oracle_sweep.argtypes = [C.POINTER(_Geom), C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
-                                     ip, C.c_int, dp, dp, dp, C.c_int]
+                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int]
         for f in (lib.oracle_count, lib.oracle_tracks, lib.oracle_sweep):
             f.restype = C.c_int
         lib.oracle_real_bits.argtypes = [C.c_int]
@@ -133,10 +134,11 @@ def tracks(geom: Geometry, precision: str = "quad") -> dict:
 
 
 def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
-          want_I=True, want_exit=False, threads=None) -> dict:
+          want_I=True, want_exit=False, threads=None, I_as_deviation=False) -> dict:
     """One backward-Euler sweep.  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
     (I^{n-1} = B of the segment's cell).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
-    plus 'I' (canonical [nseg][Gsub] segment averages) and 'I_exit' ([nrays][Gsub]) when asked."""
+    plus 'I' (canonical [nseg][Gsub] segment averages, or their deviations from the cell's B formed in the
+    oracle's precision when I_as_deviation) and 'I_exit' ([nrays][Gsub]) when asked."""
     lib = _load()
     kappa = np.ascontiguousarray(kappa, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
@@ -158,7 +160,8 @@ def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precis
     nthreads = threads or max(1, min(os.cpu_count() or 1, 64))
     rc = lib.oracle_sweep(C.byref(g), PREC[precision], G, _dp(kappa), _dp(B), float(c), float(dt), _dp(bnd),
                           _dp(I_prev), gl.ctypes.data_as(C.POINTER(C.c_int)) if gl is not None else None,
-                          0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads))
+                          0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads),
+                          int(bool(I_as_deviation)))
     if rc:
         raise RuntimeError(f"oracle_sweep failed ({rc})")
     res = {k: out[i] for i, k in enumerate(MOMENTS)}

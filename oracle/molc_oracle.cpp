@@ -23,7 +23,11 @@
 //     Eq. 4) and the Eddington-tensor numerator int Omega Omega I dOmega (Eq. 7 / Eq. 15), all cell averages.
 // Readings where the paper is silent: I^{n-1} in Q is the previous step's segment average on the same
 // segment, direction and group; the cell tensor of Eq. (15) uses the segment average Ibar; each direction
-// with mu > 0 also stands for its mirror through the x-y plane (weights sum to 4 pi).
+// with mu > 0 also stands for its mirror through the x-y plane (weights sum to 4 pi).  The characteristic grid
+// is defined by its double-precision evaluation: the unit direction (c, s) / sqrt(c^2 + s^2), the grid lines
+// x0 + i lx/nx, the characteristic offsets and widths are formed in double (this file is compiled without
+// FMA contraction), and a direction and its opposite share the same lines; the crossings, segment lengths and
+// everything after are then evaluated in R.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -100,42 +104,43 @@ template <class R> struct Dir {
 };
 
 // Offsets t (along the normal n) and widths of the characteristics of one direction.
-template <class R>
-static void characteristic_offsets(const oracle_geom &g, R dx, R dy, std::vector<R> &t, std::vector<R> &w) {
-  const R x0 = g.x0, y0 = g.y0, x1 = R(g.x0) + R(g.lx), y1 = R(g.y0) + R(g.ly);
-  auto proj = [&](R x, R y) { return -dy * x + dx * y; };
+// (evaluated in double: part of the definition of the characteristic grid)
+static void characteristic_offsets(const oracle_geom &g, double dx, double dy, std::vector<double> &t,
+                                   std::vector<double> &w) {
+  const double x0 = g.x0, y0 = g.y0, x1 = g.x0 + g.lx, y1 = g.y0 + g.ly;
+  auto proj = [&](double x, double y) { return -dy * x + dx * y; };
   t.clear();
   w.clear();
   if (g.layout == 0) {
-    R c[4] = {proj(x0, y0), proj(x1, y0), proj(x0, y1), proj(x1, y1)};
-    R tmin = c[0], tmax = c[0];
+    double c[4] = {proj(x0, y0), proj(x1, y0), proj(x0, y1), proj(x1, y1)};
+    double tmin = c[0], tmax = c[0];
     for (int i = 1; i < 4; ++i) { tmin = std::min(tmin, c[i]); tmax = std::max(tmax, c[i]); }
-    R Lp = tmax - tmin;
-    long n = (long)Fn<R>::ceil(Lp / R(g.spacing) - R(1e-9));
+    double Lp = tmax - tmin;
+    long n = (long)std::ceil(Lp / g.spacing - 1e-9);
     if (n < 1) n = 1;
-    R wk = Lp / R(n);
-    for (long k = 0; k < n; ++k) { t.push_back(tmin + (R(k) + R(0.5)) * wk); w.push_back(wk); }
+    double wk = Lp / (double)n;
+    for (long k = 0; k < n; ++k) { t.push_back(tmin + ((double)k + 0.5) * wk); w.push_back(wk); }
     return;
   }
   // Paper layout: project every vertex of the material grid onto n; each gap between consecutive distinct
   // projections is one initial characteristic (it contains no vertex).  Halve until w <= h_moc.
-  const R hx = R(g.lx) / R(g.nx), hy = R(g.ly) / R(g.ny);
-  std::vector<R> v;
+  const double hx = g.lx / g.nx, hy = g.ly / g.ny;
+  std::vector<double> v;
   v.reserve((size_t)(g.nx + 1) * (g.ny + 1));
   for (int b = 0; b <= g.ny; ++b)
-    for (int a = 0; a <= g.nx; ++a) v.push_back(proj(R(g.x0) + R(a) * hx, R(g.y0) + R(b) * hy));
+    for (int a = 0; a <= g.nx; ++a) v.push_back(proj(g.x0 + a * hx, g.y0 + b * hy));
   std::sort(v.begin(), v.end());
-  const R Lp = v.back() - v.front();
-  const R merge = R(1e-13) * Lp;
-  std::vector<R> u;
-  for (R x : v)
+  const double Lp = v.back() - v.front();
+  const double merge = 1e-13 * Lp;
+  std::vector<double> u;
+  for (double x : v)
     if (u.empty() || x - u.back() > merge) u.push_back(x);
   for (size_t i = 0; i + 1 < u.size(); ++i) {
-    R gap = u[i + 1] - u[i];
+    double gap = u[i + 1] - u[i];
     long pieces = 1;
-    while (gap / R(pieces) > R(g.spacing)) pieces *= 2;
-    R wk = gap / R(pieces);
-    for (long p = 0; p < pieces; ++p) { t.push_back(u[i] + (R(p) + R(0.5)) * wk); w.push_back(wk); }
+    while (gap / (double)pieces > g.spacing) pieces *= 2;
+    double wk = gap / (double)pieces;
+    for (long p = 0; p < pieces; ++p) { t.push_back(u[i] + ((double)p + 0.5) * wk); w.push_back(wk); }
   }
 }
 
@@ -144,8 +149,9 @@ static void characteristic_offsets(const oracle_geom &g, R dx, R dy, std::vector
 // segment is the cell holding its midpoint.
 template <class R>
 static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
-  const R hx = R(g.lx) / R(g.nx), hy = R(g.ly) / R(g.ny);
-  const R x0 = g.x0, y0 = g.y0, x1 = R(g.x0) + R(g.lx), y1 = R(g.y0) + R(g.ly);
+  const double hxd = g.lx / g.nx, hyd = g.ly / g.ny;
+  const R hx = hxd, hy = hyd;
+  const R x0 = g.x0, y0 = g.y0, x1 = g.x0 + g.lx, y1 = g.y0 + g.ly;
   const R eps = R(1e-12) * std::min(hx, hy);
   // p(u) = t n + u d with n = (-dy, dx): x(u) = -t dy + u dx, y(u) = t dx + u dy
   const R bx = -t * dy, by = t * dx;
@@ -177,12 +183,12 @@ static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
   cut.push_back(ulo);
   if (dx != R(0))
     for (int i = 1; i < g.nx; ++i) {
-      R u = (R(g.x0) + R(i) * hx - bx) / dx;
+      R u = (R(g.x0 + i * hxd) - bx) / dx;
       if (u > ulo && u < uhi) cut.push_back(u);
     }
   if (dy != R(0))
     for (int j = 1; j < g.ny; ++j) {
-      R u = (R(g.y0) + R(j) * hy - by) / dy;
+      R u = (R(g.y0 + j * hyd) - by) / dy;
       if (u > ulo && u < uhi) cut.push_back(u);
     }
   cut.push_back(uhi);
@@ -206,24 +212,41 @@ static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
   return !ray.cell.empty();
 }
 
-template <class R> static void unit_dir(const oracle_geom &g, int m, R &dx, R &dy) {
-  R c = g.cos_phi[m], s = g.sin_phi[m];
-  R n = Fn<R>::sqrt(c * c + s * s);
+// (evaluated in double: part of the definition of the characteristic grid)
+static void unit_dir(const oracle_geom &g, int m, double &dx, double &dy) {
+  const double c = g.cos_phi[m], s = g.sin_phi[m];
+  const double n = std::sqrt(c * c + s * s);
   dx = c / n;
   dy = s / n;
 }
 
 template <class R> static int build_dir(const oracle_geom &g, int m, Dir<R> &d) {
-  unit_dir<R>(g, m, d.dx, d.dy);
-  std::vector<R> t, w;
-  characteristic_offsets<R>(g, d.dx, d.dy, t, w);
+  double dxd, dyd;
+  unit_dir(g, m, dxd, dyd);
+  d.dx = dxd;
+  d.dy = dyd;
+  // A characteristic is a line: the direction and its opposite share the same lines.  The lines are built for
+  // the sense with sin > 0 (or sin = 0, cos > 0); for the opposite sense the offsets along n = (-dy, dx) are
+  // their exact negations, in reverse order (increasing offset again).
+  std::vector<double> t, w;
+  const bool minus = dyd < 0 || (dyd == 0 && dxd < 0);
+  if (!minus) {
+    characteristic_offsets(g, dxd, dyd, t, w);
+  } else {
+    std::vector<double> tp, wp;
+    characteristic_offsets(g, -dxd, -dyd, tp, wp);
+    for (size_t k = tp.size(); k-- > 0;) {
+      t.push_back(-tp[k]);
+      w.push_back(wp[k]);
+    }
+  }
   d.rays.clear();
   for (size_t k = 0; k < t.size(); ++k) {
     Ray<R> r;
-    if (trace<R>(g, d.dx, d.dy, t[k], w[k], r)) d.rays.push_back(std::move(r));
+    if (trace<R>(g, d.dx, d.dy, R(t[k]), R(w[k]), r)) d.rays.push_back(std::move(r));
   }
   if (g.renorm) {
-    const R V = (R(g.lx) / R(g.nx)) * (R(g.ly) / R(g.ny));
+    const R V = R(g.lx / g.nx) * R(g.ly / g.ny);
     std::vector<R> sum((size_t)g.nx * g.ny, R(0));
     for (auto &r : d.rays)
       for (size_t s = 0; s < r.cell.size(); ++s) sum[r.cell[s]] += r.area[s];
@@ -284,7 +307,7 @@ template <class R>
 static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
                             const double *kappa, const double *B, R inv_cdt, const double *bnd,
                             const double *I_prev, int64_t seg0, double *I_new, double *I_exit, int64_t ray0,
-                            int Gsub, std::vector<R> *acc) {
+                            int Gsub, int store_dev, std::vector<R> *acc) {
   const Dir<R> &d = geo.dirs[geo.of[m]];
   const int64_t ncell = (int64_t)g.nx * g.ny;
   const R mu = g.mu[m];
@@ -323,7 +346,7 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
       a[MOM_AFX * ncell + i] += wA * rabs(Ox) * dev;
       a[MOM_AFY * ncell + i] += wA * rabs(Oy) * dev;
       a[MOM_ANXY * ncell + i] += wA * rabs(Ox * Oy) * dev;
-      if (I_new) I_new[seg * Gsub + gi] = (double)Ibar;
+      if (I_new) I_new[seg * Gsub + gi] = store_dev ? (double)(Ibar - B_i) : (double)Ibar;
       I = Iout;
     }
     if (I_exit) I_exit[(ray0 + (int64_t)k) * Gsub + gi] = (double)I;
@@ -333,7 +356,7 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
 template <class R>
 static int run_sweep(const oracle_geom *g, int G, const double *kappa, const double *B, double c, double dt,
                      const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                     double *I_new, double *I_exit, int nthreads) {
+                     double *I_new, double *I_exit, int nthreads, int store_dev) {
   if (check_geom(g)) return -1;
   if (G < 1 || !kappa || !B || !bnd || !(c > 0) || !(dt > 0) || !out) return -1;
   Geometry<R> geo;
@@ -355,7 +378,7 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
   for (int m = 0; m < g->ndir; ++m) ray_off[m + 1] = ray_off[m] + (int64_t)geo.dirs[geo.of[m]].rays.size();
   const int64_t ncell = (int64_t)g->nx * g->ny;
   const R inv_cdt = R(1) / (R(c) * R(dt));
-  const R V = (R(g->lx) / R(g->nx)) * (R(g->ly) / R(g->ny));
+  const R V = R(g->lx / g->nx) * R(g->ly / g->ny);
   const int nblk = std::min(g->ndir, 16);
   if (nthreads < 1) nthreads = 1;
   std::vector<std::vector<R>> acc(nblk);
@@ -366,7 +389,7 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
         int m0 = (int)((int64_t)g->ndir * b / nblk), m1 = (int)((int64_t)g->ndir * (b + 1) / nblk);
         for (int m = m0; m < m1; ++m)
           sweep_direction<R>(*g, geo, m, gi, G, gl[gi], kappa, B, inv_cdt, bnd, I_prev, seg_off[m], I_new,
-                             I_exit, ray_off[m], Gsub, &acc[b]);
+                             I_exit, ray_off[m], Gsub, store_dev, &acc[b]);
       }
     };
     int nt = std::min(nthreads, nblk);
@@ -442,15 +465,16 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 //   groups     [ngroups]         subset of groups to sweep, or NULL for all (Gsub = G)
 //   out        [10][Gsub][ncell] E, Fx, Fy, Nxx, Nxy, Nyy, Nzz, then the conditioning magnitudes
 //                                (1/V) sum omega A |Omega_x| |Ibar - B|, same with |Omega_y|, |Omega_x Omega_y|
-//   I_new      [nseg][Gsub]      canonical segment averages Ibar (may be NULL)
+//   I_new      [nseg][Gsub]      canonical segment averages Ibar (may be NULL); with store_dev != 0 the
+//                                deviations Ibar - B of the segment's cell, formed in the oracle's precision
 //   I_exit     [nrays][Gsub]     intensity leaving each characteristic (may be NULL)
 int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa, const double *B, double c,
                  double dt, const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                 double *I_new, double *I_exit, int nthreads) {
+                 double *I_new, double *I_exit, int nthreads, int store_dev) {
   return precision ? run_sweep<real128>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads)
+                                       nthreads, store_dev)
                    : run_sweep<double>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads);
+                                       nthreads, store_dev);
 }
 
 int oracle_real_bits(int precision) { return precision ? (int)(sizeof(real128) * 8) : 64; }

@@ -13,6 +13,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmolc.so")
 SOURCES = ["molc_host.cpp", "molc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# the host planner defines the characteristic grid by plain double evaluation: no FMA contraction there
+PER_FILE = {"molc_host.cpp": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def nvcc() -> str:
@@ -40,7 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc(), *common, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *common, *PER_FILE.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")

@@ -164,8 +164,34 @@ void characteristic_offsets(const molc_grid &g, double c, double s, double spaci
   }
 }
 
-// Cut one characteristic into cell segments.  Crossings with vertical and horizontal grid lines are produced
-// as two increasing sequences and merged; a gap <= eps between consecutive cut points is not a segment (the
+// Double-double helpers (error-free transformations) for the crossing parameters.
+struct DD {
+  double hi, lo;
+};
+inline DD two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+inline DD fast_two_sum(double hi, double lo) {
+  const double s = hi + lo;
+  return {s, lo - (s - hi)};
+}
+inline bool dd_less(const DD &a, const DD &b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+// (X + t q) / d to ~106 bits: the parameter where the line {p : p.n = t} meets a grid line.
+inline DD crossing(double X, double t, double q, double d) {
+  const double p = t * q, pe = std::fma(t, q, -p);
+  const DD n0 = two_sum(X, p);
+  const DD n = fast_two_sum(n0.hi, n0.lo + pe);
+  const double q1 = n.hi / d;
+  const double r = std::fma(-q1, d, n.hi) + n.lo;
+  return fast_two_sum(q1, r / d);
+}
+
+// Cut one characteristic into cell segments.  The characteristic grid is defined by double-precision
+// evaluation of the direction, grid lines and offsets (this file is compiled without FMA contraction); the
+// crossing parameters are then evaluated in double-double so that every segment length is accurate relative
+// to itself, short corner segments included.  Crossings with vertical and horizontal grid lines form two
+// increasing sequences that are merged; a gap <= eps between consecutive cut points is not a segment (the
 // characteristic passes within eps of a vertex, i.e. steps diagonally).  A segment belongs to the cell that
 // contains its midpoint.  Returns false if the line misses the domain.
 bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, double s, double t,
@@ -173,67 +199,72 @@ bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, doub
   const double eps = 1e-12 * std::min(hx, hy);
   const double bx = -t * s, by = t * c;  // the point of the line at u = 0
   const double x1 = g.x0 + g.lx, y1 = g.y0 + g.ly;
-  double xlo = -1e300, xhi = 1e300, ylo = -1e300, yhi = 1e300;
+  const DD lo_inf{-1e300, 0}, hi_inf{1e300, 0};
+  DD xlo = lo_inf, xhi = hi_inf, ylo = lo_inf, yhi = hi_inf;
   if (c != 0.0) {
-    xlo = (g.x0 - bx) / c;
-    xhi = (x1 - bx) / c;
-    if (xlo > xhi) std::swap(xlo, xhi);
+    xlo = crossing(g.x0, t, s, c);   // (x0 - bx) / c
+    xhi = crossing(x1, t, s, c);
+    if (dd_less(xhi, xlo)) std::swap(xlo, xhi);
   } else if (bx < g.x0 || bx > x1) {
     return false;
   }
   if (s != 0.0) {
-    ylo = (g.y0 - by) / s;
-    yhi = (y1 - by) / s;
-    if (ylo > yhi) std::swap(ylo, yhi);
+    ylo = crossing(g.y0, t, -c, s);  // (y0 - by) / s
+    yhi = crossing(y1, t, -c, s);
+    if (dd_less(yhi, ylo)) std::swap(ylo, yhi);
   } else if (by < g.y0 || by > y1) {
     return false;
   }
-  const double uin = std::max(xlo, ylo), uout = std::min(xhi, yhi);
-  if (uout - uin <= eps) return false;
+  const DD uin = dd_less(xlo, ylo) ? ylo : xlo, uout = dd_less(xhi, yhi) ? xhi : yhi;
+  if ((uout.hi - uin.hi) + (uout.lo - uin.lo) <= eps) return false;
   // entry of the + sense: the larger lower bound (tie -> the vertical edge); exit likewise with upper bounds.
-  const bool x_in = c != 0.0 && (s == 0.0 || xlo >= ylo - eps);
+  const bool x_in = c != 0.0 && (s == 0.0 || xlo.hi >= ylo.hi - eps);
   entry_plus = x_in ? (c > 0 ? 0 : 1) : (s > 0 ? 2 : 3);
-  const bool x_out = c != 0.0 && (s == 0.0 || xhi <= yhi + eps);
+  const bool x_out = c != 0.0 && (s == 0.0 || xhi.hi <= yhi.hi + eps);
   entry_minus = x_out ? (c > 0 ? 1 : 0) : (s > 0 ? 3 : 2);
   // crossing parameters, each list increasing in u
-  std::vector<double> ux, uy;
+  std::vector<DD> ux, uy;
   if (c != 0.0) {
     for (int i = 1; i < g.nx; ++i) {
       const int ii = c > 0 ? i : g.nx - i;
-      const double u = (g.x0 + ii * hx - bx) / c;
-      if (u > uin && u < uout) ux.push_back(u);
+      const DD u = crossing(g.x0 + ii * hx, t, s, c);
+      if (dd_less(uin, u) && dd_less(u, uout)) ux.push_back(u);
     }
   }
   if (s != 0.0) {
     for (int j = 1; j < g.ny; ++j) {
       const int jj = s > 0 ? j : g.ny - j;
-      const double u = (g.y0 + jj * hy - by) / s;
-      if (u > uin && u < uout) uy.push_back(u);
+      const DD u = crossing(g.y0 + jj * hy, t, -c, s);
+      if (dd_less(uin, u) && dd_less(u, uout)) uy.push_back(u);
     }
   }
   cells.clear();
   lens.clear();
   size_t ix = 0, iy = 0;
-  double a = uin;
+  DD a = uin;
   while (true) {
-    double b;
-    if (ix < ux.size() && (iy >= uy.size() || ux[ix] <= uy[iy]))
+    DD b;
+    bool last = false;
+    if (ix < ux.size() && (iy >= uy.size() || !dd_less(uy[iy], ux[ix])))
       b = ux[ix++];
     else if (iy < uy.size())
       b = uy[iy++];
-    else
+    else {
       b = uout;
-    if (b - a > eps) {
-      const double m = 0.5 * (a + b);
+      last = true;
+    }
+    const double len = (b.hi - a.hi) + (b.lo - a.lo);
+    if (len > eps) {
+      const double m = a.hi + 0.5 * len;
       int cx = (int)std::floor((bx + m * c - g.x0) / hx);
       int cy = (int)std::floor((by + m * s - g.y0) / hy);
       cx = std::min(std::max(cx, 0), g.nx - 1);
       cy = std::min(std::max(cy, 0), g.ny - 1);
       cells.push_back(cy * g.nx + cx);
-      lens.push_back(b - a);
+      lens.push_back(len);
     }
     a = b;
-    if (b == uout) break;
+    if (last) break;
   }
   return !cells.empty();
 }
@@ -405,7 +436,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       return fail(MOLC_ERR_INVALID_ARG, "create: every azimuth must carry the same number of polar cosines");
     }
     const int j = p->n_pairs++;
-    const double nrm = std::hypot(c, s);
+    const double nrm = std::sqrt(c * c + s * s);
     PairDev pd;
     pd.c = c / nrm;
     pd.s = s / nrm;
@@ -668,11 +699,16 @@ int64_t molc_intensity_count(const molc_plan *p) {
 
 size_t molc_intensity_bytes(const molc_plan *p, molc_precision prec) {
   if (!p) return 0;
-  return bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4) + (size_t)p->G * p->view.ncell * 8;
+  return header_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell) + kHeaderBytes;
 }
 
 static double *bref_of(const molc_plan *p, molc_precision prec, void *I) {
   return (double *)((char *)I + bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4));
+}
+
+static double *header_of(const molc_plan *p, molc_precision prec, void *I) {
+  return (double *)((char *)I +
+                    header_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell));
 }
 
 static molc_status check_prec(const molc_plan *p, molc_precision prec, const char *who) {
@@ -693,6 +729,7 @@ molc_status molc_intensity_init(molc_plan *p, molc_precision prec, void *I, cons
   const size_t nb = (size_t)p->G * p->view.ncell * sizeof(double);
   cudaError_t e = cudaMemsetAsync(I, 0, bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bref_of(p, prec, I), B, nb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = launch_set_scale(p->view, prec, B, header_of(p, prec, I), st);
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "intensity_init");
 }
 
@@ -714,6 +751,7 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.dt = dt;
   a.I = I;
   a.Bref = bref_of(p, prec, I);
+  a.scale = header_of(p, prec, I);
   a.out = *out;
   a.cdat = p->d_cdat;
   a.cdB = p->d_cdB;
@@ -765,7 +803,8 @@ static molc_status intensity_copy(const molc_plan *p, molc_precision prec, void 
     e = cudaMemcpyAsync(bref + off, B + off, (size_t)g_count * p->view.ncell * sizeof(double),
                         cudaMemcpyDeviceToDevice, st);
   }
-  if (e == cudaSuccess) e = launch_intensity_copy(p->view, prec, I, bref, g_begin, g_count, canon, to_canon, st);
+  if (e == cudaSuccess)
+    e = launch_intensity_copy(p->view, prec, I, bref, header_of(p, prec, I), g_begin, g_count, canon, to_canon, st);
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, who);
 }
 
@@ -856,7 +895,7 @@ molc_status molc_device_status(molc_plan *p, int *code) {
   if (e != cudaSuccess) return cuda_fail(e, "device_status");
   e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "device_status");
-  *code = (h & kStatusNonfinite) ? MOLC_ERR_NONFINITE_INPUT : MOLC_OK;
+  *code = (h & kStatusNonfinite) ? MOLC_ERR_NONFINITE_INPUT : (h & kStatusRange) ? MOLC_ERR_RANGE : MOLC_OK;
   return MOLC_OK;
 }
 

@@ -13,6 +13,10 @@ constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators pe
 
 // Device status bits (the first one set wins in molc_device_status).
 constexpr int kStatusNonfinite = 1;
+constexpr int kStatusRange = 2;
+// FP32 states work in units scaled by 2^k with max B * 2^k in [2^99, 2^100); inputs above 2^124 are rejected.
+constexpr int kScaleTargetExp = 100;
+constexpr double kScaledMax = 21267647932558653966460912964485513216.0;  // 2^124
 
 // One characteristic (track) of an azimuth pair; the + sense walks its segments forward, the - sense backward.
 struct TrackDev {
@@ -71,14 +75,20 @@ inline Layout layout_for(const PlanView &v, molc_precision prec) {
   return L;
 }
 
-// Byte offset of the reference Planck block inside an intensity state of `count` elements of `esize` bytes.
+// Byte offset of the reference Planck block inside an intensity state of `count` elements of `esize` bytes,
+// and of the header after it: {scale, 1/scale, scratch (max B bits)}.
 inline size_t bref_offset(int64_t count, int esize) { return ((size_t)count * esize + 255) / 256 * 256; }
+inline size_t header_offset(int64_t count, int esize, int G, int ncell) {
+  return bref_offset(count, esize) + ((size_t)G * ncell * 8 + 255) / 256 * 256;
+}
+constexpr size_t kHeaderBytes = 256;
 
 struct SweepArgs {
   const double *kappa, *B, *bnd;
   double c, dt;
   void *I;            // deviations delta = Ibar - B_ref, [chunk][row][g_local][p]
   double *Bref;       // [G][cell] Planck intensity the deviations refer to (inside the state)
+  const double *scale;  // state header: [0] = scale of the stored deviations, [1] = 1/scale
   molc_moments out;
   float4 *cdat;       // FP32: [chunk][cell][gc] {kappa~, 1/(c dt kappa~), B_hi, B_lo}
   float *cdB;         // FP32: [chunk][cell][gc] (B_ref - B) / (c dt kappa~)
@@ -96,6 +106,9 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
                            double *fyy, double *f_grey, cudaStream_t st);
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
-                                  int g_begin, int g_count, double *canon, bool to_canon, cudaStream_t st);
+                                  const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
+                                  cudaStream_t st);
+cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const double *B, double *header,
+                             cudaStream_t st);
 
 }  // namespace molc

@@ -47,7 +47,8 @@ __device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int
 __global__ void prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
   const int64_t n = (int64_t)v.G * v.ncell;
   const double inv_cdt = 1.0 / (a.c * a.dt);
-  bool bad = false;
+  const double sc = a.scale[0];
+  bool bad = false, range = false;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int g = (int)(idx / v.ncell);
@@ -57,18 +58,23 @@ __global__ void prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
     if (fp32) {
       const double kt = kap + inv_cdt;
       const double r = inv_cdt / kt;
-      const float bhi = (float)B;
-      const float blo = (float)(B - (double)bhi);
+      const double Bs = B * sc;
+      range |= !(Bs < kScaledMax);
+      const float bhi = (float)Bs;
+      const float blo = (float)(Bs - (double)bhi);
       const int ch = g / L.gc, gl = g - ch * L.gc;
       const int64_t o = ((int64_t)ch * v.ncell + cell) * L.gc + gl;
       a.cdat[o] = make_float4((float)kt, (float)r, bhi, blo);
-      a.cdB[o] = (float)((a.Bref[idx] - B) * r);
+      a.cdB[o] = (float)((a.Bref[idx] - B) * sc * r);
     }
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * (int64_t)v.G;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     bad |= bad_input(a.bnd[i]);
+    range |= fp32 && !(a.bnd[i] * sc < kScaledMax);
+  }
   if (bad) atomicOr(v.status, kStatusNonfinite);
+  if (range && !bad) atomicOr(v.status, kStatusRange);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -154,11 +160,14 @@ __device__ __forceinline__ void attenuation(float tau, float inv_tau, float &E1,
 }
 
 // FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU).  Exact for normal
-// numbers; zeros and subnormals (|x| < 2^-126) map to a value of magnitude < 2^-126 with the same sign.
+// numbers (exponent rebiased by 1023 - 127, mantissa shifted into place); zeros and subnormals
+// (|x| < 2^-126) become a signed zero, an absolute error below 2^-126 per converted value.
 __device__ __forceinline__ double f32_to_f64(float x) {
   const unsigned u = __float_as_uint(x);
-  const unsigned hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
-  return __hiloint2double((int)hi, (int)(u << 29));
+  const unsigned mag = u & 0x7fffffffu;
+  const bool normal = mag >= 0x00800000u;
+  const unsigned hi = (u & 0x80000000u) | (normal ? (mag >> 3) + 0x38000000u : 0u);
+  return __hiloint2double((int)hi, normal ? (int)(u << 29) : 0);
 }
 
 template <int NP>
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   const float sg = sense ? -1.f : 1.f;
   const float fx = sg * pr.cf, fy = sg * pr.sf, fxx = pr.cf * pr.cf, fxy = pr.cf * pr.sf, fyy = pr.sf * pr.sf;
   // entering intensity, split like B so that I_in - B keeps the precision of the difference
-  const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] : 0.0;
+  const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
 
   float psi[NP];
@@ -293,6 +302,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
 __global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
   const int64_t n = (int64_t)v.G * v.ncell;
   const double inv_c = 1.0 / a.c;
+  const double is = a.scale[1];   // accumulators are in the state's scaled units (exact power of two)
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int g = (int)(idx / v.ncell);
@@ -300,12 +310,12 @@ __global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
     const int ch = g / L.gc, gl = g - ch * L.gc;
     const double *ac = a.acc + ((int64_t)ch * v.ncell + cell) * kOutputs * L.gc + gl;
     const double B = a.B[idx];
-    a.out.E[idx] = (B * v.geo[cell] + ac[0 * L.gc]) * inv_c;
-    a.out.Fx[idx] = ac[1 * L.gc];
-    a.out.Fy[idx] = ac[2 * L.gc];
-    a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + ac[3 * L.gc];
-    a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + ac[4 * L.gc];
-    a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + ac[5 * L.gc];
+    a.out.E[idx] = (B * v.geo[cell] + ac[0 * L.gc] * is) * inv_c;
+    a.out.Fx[idx] = ac[1 * L.gc] * is;
+    a.out.Fy[idx] = ac[2 * L.gc] * is;
+    a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + ac[3 * L.gc] * is;
+    a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + ac[4 * L.gc] * is;
+    a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + ac[5 * L.gc] * is;
     a.Bref[idx] = B;   // the new deviations refer to this step's B
   }
 }
@@ -339,9 +349,10 @@ __global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx
 // Canonical segment averages <-> deviation state: one thread per row (track, sense, step) of the layout,
 // looping over polar cosines and the selected groups.  Ibar = B_ref(cell) + delta.
 template <class T>
-__global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *Bref, int g_begin, int g_count,
-                                      double *canon, int to_canon) {
+__global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *Bref, const double *scale,
+                                      int g_begin, int g_count, double *canon, int to_canon) {
   const int NP = v.n_polar;
+  const double sc = scale[0], is = scale[1];
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < L.rows;
        row += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = find_track(v.tracks, v.n_tracks, row);
@@ -360,12 +371,37 @@ __global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *
         const double br = Bref[(int64_t)g * v.ncell + cell];
         double *cv = canon + cs * g_count + (g - g_begin);
         if (to_canon)
-          *cv = br + (double)*el;
+          *cv = br + (double)*el * is;
         else
-          *el = (T)(*cv - br);
+          *el = (T)((*cv - br) * sc);
       }
     }
   }
+}
+
+// max over finite non-negative B of the IEEE bits (ordered like the values for x >= 0)
+__global__ void max_bits_kernel(const double *B, int64_t n, unsigned long long *mx) {
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double b = B[i];
+    if (b >= 0.0 && isfinite(b)) m = max(m, (unsigned long long)__double_as_longlong(b));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
+// scale = 2^(100 - e) with max B = f 2^e, f in [1/2, 1) (2^100 if max B = 0); 1 for FP64 states.
+__global__ void set_scale_kernel(const unsigned long long *mx, double *header, int fp32) {
+  double s = 1.0;
+  if (fp32) {
+    const double m = __longlong_as_double((long long)*mx);
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);
+    s = ldexp(1.0, kScaleTargetExp - e);
+  }
+  header[0] = s;
+  header[1] = 1.0 / s;
 }
 
 int grid_for(int64_t n, int block) {
@@ -422,14 +458,25 @@ cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, d
 }
 
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
-                                  int g_begin, int g_count, double *canon, bool to_canon, cudaStream_t st) {
+                                  const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
+                                  cudaStream_t st) {
   const Layout L = layout_for(v, prec);
   if (prec == MOLC_FP64)
-    intensity_copy_kernel<double><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (double *)I, Bref, g_begin,
+    intensity_copy_kernel<double><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (double *)I, Bref, scale, g_begin,
                                                                          g_count, canon, to_canon);
   else
-    intensity_copy_kernel<float><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (float *)I, Bref, g_begin,
+    intensity_copy_kernel<float><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (float *)I, Bref, scale, g_begin,
                                                                        g_count, canon, to_canon);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const double *B, double *header,
+                             cudaStream_t st) {
+  unsigned long long *mx = reinterpret_cast<unsigned long long *>(header + 2);
+  cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  max_bits_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(B, (int64_t)v.G * v.ncell, mx);
+  set_scale_kernel<<<1, 1, 0, st>>>(mx, header, prec == MOLC_FP32);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,7 @@ HOST_ONLY = 2
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 LAYOUT = {"uniform": RAYS_UNIFORM, "paper": RAYS_PAPER, RAYS_UNIFORM: RAYS_UNIFORM, RAYS_PAPER: RAYS_PAPER}
 STATUS = {0: "MOLC_OK", 1: "MOLC_ERR_INVALID_ARG", 2: "MOLC_ERR_OUT_OF_MEMORY", 3: "MOLC_ERR_CUDA",
-          4: "MOLC_ERR_NONFINITE_INPUT", 5: "MOLC_ERR_TIMEOUT", 6: "MOLC_ERR_INTERNAL"}
+          4: "MOLC_ERR_NONFINITE_INPUT", 5: "MOLC_ERR_TIMEOUT", 6: "MOLC_ERR_INTERNAL", 7: "MOLC_ERR_RANGE"}
 MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")
 
 # every symbol include/molc.h declares

@@ -29,7 +29,8 @@ def host(d):
 
 def test_full_size_512_sampled_groups(molc):
     """The production workload (512^2, 17 groups, 128 directions, h/2, three fronts) in the launch
-    configuration the benchmark times; groups 0, 8 and 16 checked against the double oracle."""
+    configuration the benchmark times; four groups checked against the double oracle (the floor of the
+    relative metric is taken over all groups of the GPU output)."""
     wl = synth.WORKLOADS["fc512_g17_d128"]
     d = wl.inputs(0)
     P = molc.Plan.from_workload(wl)
@@ -43,11 +44,13 @@ def test_full_size_512_sampled_groups(molc):
     del I
     torch.cuda.empty_cache()
     assert n_upd > 1.4e9
-    groups = [0, 8, 16]
+    groups = [0, 8, 11, 16]     # 11 holds the Planck peak of the hot region
     geom = oracle.Geometry.from_workload(wl)
     ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="double",
                        want_I=False)
-    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"])
+    fm = {k: float(np.abs(v).max()) for k, v in got.items()}
+    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"], ref_precision="double",
+                   floor_max=fm)
 
 
 def test_closure_and_grey_average(molc):
@@ -92,7 +95,10 @@ def test_export_import_roundtrip(molc, prec):
     before = P.intensity_export(prec, I).cpu().numpy()
     P.intensity_import(prec, I, dev(np.zeros((P.info.n_segments, 1))), B, g_begin=2)
     after = P.intensity_export(prec, I).cpu().numpy()
-    assert np.array_equal(after[:, [0, 1, 3]], before[:, [0, 1, 3]]) and np.all(after[:, 2] == 0)
+    assert np.array_equal(after[:, [0, 1, 3]], before[:, [0, 1, 3]])
+    # zero is stored as the deviation -B of the segment's cell: exact in FP64, within FP32 rounding of B
+    Bseg = d["B"][2][P.tracks()["cell"]]
+    assert np.all(np.abs(after[:, 2]) <= (0.0 if prec == "fp64" else 6e-8) * Bseg)
     # a swept state imported into a fresh buffer gives the same next step
     k, bnd = dev(d["kappa"]), dev(d["bnd"])
     P.intensity_init(prec, I, B)
@@ -103,8 +109,37 @@ def test_export_import_roundtrip(molc, prec):
     P.intensity_import(prec, J, snap, B)
     a = host(P.sweep(prec, k, B, d["c"], d["dt"], I, bnd))
     b = host(P.sweep(prec, k, B, d["c"], d["dt"], J, bnd))
-    for kk in a:
-        assert np.allclose(a[kk], b[kk], rtol=1e-12 if prec == "fp64" else 1e-5, atol=1e-30)
+    # the canonical format holds segment averages, not deviations: the round trip is exact to rounding of
+    # the averages, so the next step agrees to that on E and to it times c E on the signed moments
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    cE = d["c"] * a["E"]
+    for kk in ("E", "Nxx", "Nyy"):
+        assert np.all(np.abs(a[kk] - b[kk]) <= tol * np.abs(a[kk]) + 1e-300), kk
+    for kk in ("Fx", "Fy", "Nxy"):
+        assert np.all(np.abs(a[kk] - b[kk]) <= tol * cE), kk
+    P.close()
+
+
+def test_fp32_state_range_is_checked(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity("fp32")
+    P.intensity_init("fp32", I, B)
+    P.sweep("fp32", dev(d["kappa"]), dev(d["B"] * 2.0 ** 20), d["c"], d["dt"], I, dev(d["bnd"]))
+    assert P.device_status() == 0              # within the 2^24 headroom
+    P.sweep("fp32", dev(d["kappa"]), dev(d["B"] * 2.0 ** 30), d["c"], d["dt"], I, dev(d["bnd"]))
+    assert P.device_status() == 7              # MOLC_ERR_RANGE
+    # tiny intensities far below FP32's normal range in absolute units are fine after scaling
+    small = d["B"] * 1e-60
+    Bs = dev(small)
+    P.intensity_init("fp32", I, Bs)
+    m = host(P.sweep("fp32", dev(d["kappa"]), Bs, d["c"], d["dt"], I, dev(d["bnd"] * 1e-60)))
+    P.intensity_init("fp32", I, B)
+    m0 = host(P.sweep("fp32", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"])))
+    assert P.device_status() == 0
+    assert np.allclose(m["E"] * 1e60, m0["E"], rtol=1e-6, atol=1e-30 * np.abs(m0["E"]).max())
     P.close()
 
 

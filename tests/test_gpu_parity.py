@@ -93,18 +93,19 @@ def test_fp32_ten_steps_64x64(molc):
     got, _ = run_gpu(molc, wl, d, "fp32", steps=wl.steps)
     ref, _ = run_oracle(wl, d, "double", steps=wl.steps)
     for g_, r_ in zip(got, ref):
-        parity.compare(g_, r_, "fp32", d["c"])
+        parity.compare(g_, r_, "fp32", d["c"], ref_precision="double")
 
 
 def test_fp64_64x64_sampled_groups_vs_binary128(molc):
     wl = synth.WORKLOADS["fc64_g17_d128"]
     d = wl.inputs(1)
     got, _ = run_gpu(molc, wl, d, "fp64")
-    groups = [0, 8, 16]
+    groups = [0, 8, 11, 16]
     geom = oracle.Geometry.from_workload(wl)
     ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="quad",
                        want_I=False)
-    parity.compare({k: v[groups] for k, v in got[0].items()}, ref, "fp64", d["c"])
+    fm = {k: float(np.abs(v).max()) for k, v in got[0].items()}
+    parity.compare({k: v[groups] for k, v in got[0].items()}, ref, "fp64", d["c"], floor_max=fm)
 
 
 # Varied shapes: rectangular cells, G = 1, odd polar counts (every FP32 template), the paper's layout,

