@@ -57,7 +57,7 @@ def _load():
         lib.oracle_count.argtypes = [C.POINTER(_Geom), i64p]
         lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp]
         lib.oracle_sweep.argtypes = [C.POINTER(_Geom), C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
-                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int]
+                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int]
         for f in (lib.oracle_count, lib.oracle_tracks, lib.oracle_sweep):
             f.restype = C.c_int
         lib.oracle_real_bits.argtypes = [C.c_int]
@@ -134,9 +134,10 @@ def tracks(geom: Geometry, precision: str = "quad") -> dict:
 
 
 def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
-          want_I=True, want_exit=False, threads=None, I_as_deviation=False) -> dict:
+          want_I=True, want_exit=False, threads=None, I_as_deviation=False, I_prev_is_deviation=False) -> dict:
     """One backward-Euler sweep.  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
-    (I^{n-1} = B of the segment's cell).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
+    (I^{n-1} = B of the segment's cell); with I_prev_is_deviation, I_prev holds deviations from B of the
+    segment's cell (so a state carried between steps as deviations keeps its precision).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
     plus 'I' (canonical [nseg][Gsub] segment averages, or their deviations from the cell's B formed in the
     oracle's precision when I_as_deviation) and 'I_exit' ([nrays][Gsub]) when asked."""
     lib = _load()
@@ -161,7 +162,7 @@ def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precis
     rc = lib.oracle_sweep(C.byref(g), PREC[precision], G, _dp(kappa), _dp(B), float(c), float(dt), _dp(bnd),
                           _dp(I_prev), gl.ctypes.data_as(C.POINTER(C.c_int)) if gl is not None else None,
                           0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads),
-                          int(bool(I_as_deviation)))
+                          int(bool(I_as_deviation)), int(bool(I_prev_is_deviation)))
     if rc:
         raise RuntimeError(f"oracle_sweep failed ({rc})")
     res = {k: out[i] for i, k in enumerate(MOMENTS)}

@@ -307,7 +307,7 @@ template <class R>
 static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
                             const double *kappa, const double *B, R inv_cdt, const double *bnd,
                             const double *I_prev, int64_t seg0, double *I_new, double *I_exit, int64_t ray0,
-                            int Gsub, int store_dev, std::vector<R> *acc) {
+                            int Gsub, int store_dev, int prev_dev, std::vector<R> *acc) {
   const Dir<R> &d = geo.dirs[geo.of[m]];
   const int64_t ncell = (int64_t)g.nx * g.ny;
   const R mu = g.mu[m];
@@ -324,7 +324,7 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
       const int i = r.cell[s];
       const R kap_i = kap[i];
       const R B_i = Bg[i];
-      const R Iprev = I_prev ? R(I_prev[seg * Gsub + gi]) : B_i;
+      const R Iprev = I_prev ? (prev_dev ? B_i + R(I_prev[seg * Gsub + gi]) : R(I_prev[seg * Gsub + gi])) : B_i;
       const R kt = kap_i + inv_cdt;                                 // Eq. (11)
       const R Q = kap_i * B_i + inv_cdt * Iprev;                    // Eq. (11)
       const R tau = kt * r.len[s] / sinz;                           // Eq. (13)
@@ -356,7 +356,7 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
 template <class R>
 static int run_sweep(const oracle_geom *g, int G, const double *kappa, const double *B, double c, double dt,
                      const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                     double *I_new, double *I_exit, int nthreads, int store_dev) {
+                     double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev) {
   if (check_geom(g)) return -1;
   if (G < 1 || !kappa || !B || !bnd || !(c > 0) || !(dt > 0) || !out) return -1;
   Geometry<R> geo;
@@ -389,7 +389,7 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
         int m0 = (int)((int64_t)g->ndir * b / nblk), m1 = (int)((int64_t)g->ndir * (b + 1) / nblk);
         for (int m = m0; m < m1; ++m)
           sweep_direction<R>(*g, geo, m, gi, G, gl[gi], kappa, B, inv_cdt, bnd, I_prev, seg_off[m], I_new,
-                             I_exit, ray_off[m], Gsub, store_dev, &acc[b]);
+                             I_exit, ray_off[m], Gsub, store_dev, prev_dev, &acc[b]);
       }
     };
     int nt = std::min(nthreads, nblk);
@@ -461,7 +461,9 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 // One backward-Euler sweep of every direction, characteristic and (selected) group.
 //   kappa, B   [G][ncell]        opacity (cm^-1) and group Planck intensity
 //   bnd        [4][G]            isotropic incoming intensity per edge (left, right, bottom, top)
-//   I_prev     [nseg][Gsub]      canonical previous-step segment averages, or NULL for I^{n-1} = B of the cell
+//   I_prev     [nseg][Gsub]      canonical previous-step segment averages, or NULL for I^{n-1} = B of the cell;
+//                                with prev_dev != 0 their deviations from this step's B of the segment's cell
+//                                (I^{n-1} = B + I_prev formed in the oracle's precision)
 //   groups     [ngroups]         subset of groups to sweep, or NULL for all (Gsub = G)
 //   out        [10][Gsub][ncell] E, Fx, Fy, Nxx, Nxy, Nyy, Nzz, then the conditioning magnitudes
 //                                (1/V) sum omega A |Omega_x| |Ibar - B|, same with |Omega_y|, |Omega_x Omega_y|
@@ -470,11 +472,11 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 //   I_exit     [nrays][Gsub]     intensity leaving each characteristic (may be NULL)
 int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa, const double *B, double c,
                  double dt, const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                 double *I_new, double *I_exit, int nthreads, int store_dev) {
+                 double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev) {
   return precision ? run_sweep<real128>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev)
+                                       nthreads, store_dev, prev_dev)
                    : run_sweep<double>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev);
+                                       nthreads, store_dev, prev_dev);
 }
 
 int oracle_real_bits(int precision) { return precision ? (int)(sizeof(real128) * 8) : 64; }

@@ -543,8 +543,12 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       wxy += ww * s2 * c * s;
       wyy += ww * s2 * s * s;
     }
+    // With renormalisation, or with the paper's layout (bands free of vertices tile each cell, so the areas
+    // l w sum exactly to the cell area), sum_{C(i,m)} A = V holds exactly and is used as such: the B parts of
+    // F and N_xy then cancel exactly instead of to the rounding of the FP64 areas.
+    const bool exact_tiling = renorm || layout == MOLC_RAYS_PAPER;
     for (int i = 0; i < ncell; ++i) {
-      const double a = renorm ? 1.0 : asum[i] / p->V;
+      const double a = exact_tiling ? 1.0 : asum[i] / p->V;
       g0[i].add(w0 * a);
       gxx[i].add(wxx * a);
       gxy[i].add(wxy * a);

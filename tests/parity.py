@@ -8,15 +8,20 @@ relative error is bounded by the unit roundoff u times the sum's condition numbe
 which is unbounded where the output crosses zero, so no arithmetic meets a fixed relative bound there.  For
 these outputs the denominator also contains eta * x_abs, where x_abs = (1/V) sum omega |Omega..| A |Ibar - B|
 is the magnitude of the deviation terms the GPU paths sum (computed by the oracle) and eta = C u / tol with
-C = 32 for FP32 and C = 192 for FP64 (besides rounding, the FP64 planner's segment lengths differ from the
-binary128 oracle's by O(1e-16 L), which enters the deviation terms of short segments): cells whose output is
-at least eta x_abs are held to the literal relative bound, the others to an absolute error of C u x_abs.
+C = 64 for FP32 and C = 32 for FP64: cells whose output is at least eta x_abs are held to the literal relative
+bound, the others to an absolute error of C u x_abs.  For FP32 the per-term error is not just a few u: tau is
+formed from kappa~, l and 1/sin(zeta), each rounded to FP32, so e^-tau carries a relative error ~tau u, which
+accumulates along a beam like a random walk over its segments (measured up to ~40 u of the deviation
+magnitude on the 64^2 and 512^2 workloads).
 
 When the reference is the double-precision oracle, which sums the literal intensities, its own error on a
 signed moment is ~u_64 c E; the denominator then also contains 64 u_64 c E / tol.
 
 The floor 1e-30 max|x| is taken over the whole output array (all groups); `floor_max` passes it when only some
 groups are compared.  The literal pass fraction is reported alongside.
+
+The Eddington factors f = N / (c E) are compared in the cells whose E is above that floor; below it E and N
+are both unresolved and their ratio carries no information.
 """
 import numpy as np
 
@@ -26,7 +31,7 @@ TOL_F_ABS_FP32 = 1e-6          # absolute bound on the Eddington factors for the
 SIGNED = {"Fx": "absFx", "Fy": "absFy", "Nxy": "absNxy"}
 
 
-ETA_C = {"fp64": 192.0, "fp32": 32.0}
+ETA_C = {"fp64": 32.0, "fp32": 64.0}
 
 
 def eta(prec: str) -> float:
@@ -44,6 +49,12 @@ def rel_error(got, ref, absmag=None, eta_=0.0, floor_max=None, extra=None):
         den = np.maximum(den, extra)
     den = np.where(den > 0, den, 1e-300)
     return np.abs(got - ref) / den
+
+
+def _worst(err, got, ref, k, ak):
+    g, i = np.unravel_index(np.argmax(err), np.shape(err))
+    return dict(group=int(g), cell=int(i), got=float(got[k][g, i]), ref=float(ref[k][g, i]),
+                abs=float(ref[ak][g, i]), E=float(ref["E"][g, i]))
 
 
 def closure(m, c):
@@ -72,22 +83,24 @@ def compare(got: dict, ref: dict, prec: str, c: float, report=None, ref_precisio
         gated = rel_error(got[k], ref[k], ref[ak], e, floor_max=fm.get(k), extra=ref_err)
         out[k] = float(gated.max())
         out[k + "_literal_pass"] = float(np.mean(lit <= tol))
-        assert out[k] <= tol, (k, out[k])
+        assert out[k] <= tol, (k, out[k], _worst(gated, got, ref, k, ak))
     fg = closure(got, c)
     fr = closure(ref, c)
     cE = c * np.asarray(ref["E"])
     safe = np.where(cE > 0, cE, 1.0)
+    resolved = np.asarray(ref["E"]) >= 1e-30 * (fm.get("E") or np.max(np.abs(ref["E"])))
     if prec == "fp32":
         for k in ("fxx", "fxy", "fyy"):
-            out[k] = float(np.max(np.abs(fg[k] - fr[k])))
+            err = np.where(resolved, np.abs(fg[k] - fr[k]), 0.0)
+            out[k] = float(np.max(err))
             assert out[k] <= TOL_F_ABS_FP32, (k, out[k])
     else:
         for k in ("fxx", "fyy"):
-            out[k] = float(rel_error(fg[k], fr[k]).max())
+            out[k] = float(np.where(resolved, rel_error(fg[k], fr[k]), 0.0).max())
             assert out[k] <= tol, (k, out[k])
         r = rel_error(fg["fxy"], fr["fxy"], np.where(cE > 0, ref["absNxy"] / safe, 0.0), e,
                       extra=None if ref_err is None else np.where(cE > 0, ref_err / safe, 0.0))
-        out["fxy"] = float(r.max())
+        out["fxy"] = float(np.where(resolved, r, 0.0).max())
         assert out["fxy"] <= tol, ("fxy", out["fxy"])
     if report is not None:
         report.append(out)

@@ -98,7 +98,8 @@ def test_export_import_roundtrip(molc, prec):
     assert np.array_equal(after[:, [0, 1, 3]], before[:, [0, 1, 3]])
     # zero is stored as the deviation -B of the segment's cell: exact in FP64, within FP32 rounding of B
     Bseg = d["B"][2][P.tracks()["cell"]]
-    assert np.all(np.abs(after[:, 2]) <= (0.0 if prec == "fp64" else 6e-8) * Bseg)
+    floor = 1e-30 * d["B"].max()      # FP32 states resolve deviations down to ~1e-68 of max B
+    assert np.all(np.abs(after[:, 2]) <= (0.0 if prec == "fp64" else 6e-8) * Bseg + (prec == "fp32") * floor)
     # a swept state imported into a fresh buffer gives the same next step
     k, bnd = dev(d["kappa"]), dev(d["bnd"])
     P.intensity_init(prec, I, B)

@@ -48,15 +48,18 @@ def run_gpu(molc, wl, d, prec, steps=1, quad=None, layout="uniform", renorm=True
 
 
 def run_oracle(wl, d, precision, steps=1, quad=None, layout=0, renorm=1, spacing=None, want_I=False):
+    """The oracle over `steps` steps; between steps it carries its state as deviations from B (fixed B here),
+    so the carried state keeps the oracle's precision.  Returns the moments and the segment averages."""
     geom = oracle.Geometry.from_workload(wl, quad=quad, layout=layout, renorm=renorm, spacing=spacing)
     outs, Is = [], []
-    I = None
+    dev = None
+    cells = oracle.tracks(geom, "double")["cell"] if (steps > 1 or want_I) else None
     for _ in range(steps):
-        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=I, precision=precision,
-                         want_I=(steps > 1 or want_I))
-        I = r.get("I")
+        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=dev, precision=precision,
+                         want_I=(steps > 1 or want_I), I_as_deviation=True, I_prev_is_deviation=True)
+        dev = r.get("I")
         outs.append(r)
-        Is.append(I)
+        Is.append(None if dev is None else dev + d["B"][:, cells].T)
     return outs, Is
 
 
@@ -70,8 +73,8 @@ def test_small_one_step_vs_binary128(molc, prec, seed):
     got, gI = run_gpu(molc, C0, d, prec, export=True)
     ref, rI = run_oracle(C0, d, "quad", want_I=True)
     parity.compare(got[0], ref[0], prec, d["c"])
-    # carried state: segment averages (lengths are FP64 differences of O(L) coordinates: 1e-11 relative)
-    tol_I = 1e-11 if prec == "fp64" else 5e-6
+    # carried state, per segment, against its deviation from B (FP32: the tau u error accumulated along beams)
+    tol_I = 1e-12 if prec == "fp64" else 2e-5
     Bseg = d["B"][:, oracle.tracks(oracle.Geometry.from_workload(C0), "double")["cell"]].T
     scale = np.maximum(np.abs(rI[0] - Bseg), 1e-30 * np.abs(rI[0]).max())
     scale = np.maximum(scale, np.abs(rI[0]) * (1e-3 if prec == "fp64" else 1.0))
@@ -162,7 +165,8 @@ def test_variants_vs_binary128(molc, prec, vi):
                            0 if layout == "uniform" else 1, int(renorm))
     Iq = None
     for step in range(2):
-        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=Iq, precision="quad")
+        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=Iq, precision="quad",
+                         I_as_deviation=True, I_prev_is_deviation=True)
         Iq = r["I"]
         parity.compare(res[step], r, prec, d["c"])
 
