@@ -91,7 +91,9 @@ struct molc_plan {
   float *d_cdB = nullptr;
   double *d_acc = nullptr;
   int2 *d_items32 = nullptr;
-  int64_t n_items32 = 0;
+  int2 *d_tiles32 = nullptr;
+  int64_t n_items32 = 0, n_tiles32 = 0;
+  int fp32_kernel = kKernelTile;
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
@@ -293,7 +295,8 @@ void free_events(molc_plan *p) {
 void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
-                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32};
+                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
+                  p->d_tiles32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -603,7 +606,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   if (!p->host_only) cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device);
   if (l2_bytes <= 0) l2_bytes = 128 << 20;
   const double per_group = 68.0 * ncell;
-  const int gc32 = std::max(1, std::min(p->G, (int)std::floor(0.5 * l2_bytes / per_group)));
+  const int gc_l2 = std::max(1, (int)std::floor(0.5 * l2_bytes / per_group));
+  const int gc32 = std::max(1, std::min({p->G, gc_l2, 16 / std::max(p->n_polar, 1)}));
   const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
   std::vector<int64_t> order(T);
   for (int64_t k = 0; k < T; ++k) order[k] = k;
@@ -620,7 +624,12 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       for (int sense = 0; sense < 2; ++sense)
         for (int gi = 0; gi < gcount; ++gi) items.push_back(make_int2((int)k, sense | (gi << 1) | (ch << 16)));
   }
+  std::vector<int2> tiles;
+  tiles.reserve((size_t)T * nch32);
+  for (int ch = 0; ch < nch32; ++ch)
+    for (int64_t k : order) tiles.push_back(make_int2((int)k, ch));
   p->n_items32 = (int64_t)items.size();
+  p->n_tiles32 = (int64_t)tiles.size();
   p->acc_elems = (size_t)ncell * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
 
   PlanView &v = p->view;
@@ -656,6 +665,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
   UP(d_items32, items.data(), items.size(), "items")
+  UP(d_tiles32, tiles.data(), tiles.size(), "tiles")
 #undef UP
   if (st == MOLC_OK) {
     cudaError_t e = cudaMemset(p->d_status, 0, sizeof(int));
@@ -762,6 +772,9 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.acc = p->d_acc;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
+  a.tiles = p->d_tiles32;
+  a.n_tiles = p->n_tiles32;
+  a.kernel = p->fp32_kernel;
   const Layout L = layout_for(p->view, prec);
   cudaError_t e =
       cudaMemsetAsync(p->d_acc, 0, (size_t)L.n_chunks * L.gc * p->view.ncell * kOutputs * sizeof(double), st);
@@ -850,6 +863,16 @@ molc_status molc_tracks_export(const molc_plan *p, int64_t *dir_ray_off, int64_t
   }
   return MOLC_OK;
 }
+
+molc_status molc_set_fp32_variant(molc_plan *p, int variant) {
+  if (!p) return fail(MOLC_ERR_INVALID_ARG, "set_fp32_variant: NULL plan");
+  if (variant != kKernelTile && variant != kKernelTrack)
+    return fail(MOLC_ERR_INVALID_ARG, "set_fp32_variant: unknown variant %d", variant);
+  p->fp32_kernel = variant;
+  return MOLC_OK;
+}
+
+int molc_get_fp32_variant(const molc_plan *p) { return p ? p->fp32_kernel : -1; }
 
 molc_status molc_kernel_timing(molc_plan *p, int enable) {
   if (!p) return fail(MOLC_ERR_INVALID_ARG, "kernel_timing: NULL plan");

@@ -170,37 +170,86 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double((int)hi, normal ? (int)(u << 29) : 0);
 }
 
-template <int NP>
-__device__ __forceinline__ void load_dev(const float *p, float (&v)[NP]) {
-  if constexpr (NP % 4 == 0) {
-#pragma unroll
-    for (int i = 0; i < NP; i += 4) {
-      const float4 t = __ldcs(reinterpret_cast<const float4 *>(p + i));
-      v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
-    }
-  } else if constexpr (NP % 2 == 0) {
-#pragma unroll
-    for (int i = 0; i < NP; i += 2) {
-      const float2 t = __ldcs(reinterpret_cast<const float2 *>(p + i));
-      v[i] = t.x; v[i + 1] = t.y;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) v[i] = __ldcs(p + i);
-  }
+// L2 eviction policies (sm_80+ createpolicy) and loads/stores/reductions carrying them: the streamed state is
+// evict-first (used once per sweep), the cell table and the FP64 accumulators of the current group chunk are
+// evict-last (reused by every characteristic crossing the cell).
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_table4(const float4 *p, unsigned long long pol) {
+  float4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_table1(const float *p, unsigned long long pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int4 ld_record(const int4 *p) {
+  int4 v;
+  asm("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void red_f64(double *p, double v, unsigned long long pol) {
+  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// NP consecutive FP32 deviations of one thread: vector accesses where the alignment allows (the row offset is
+// a multiple of NP elements and the state is 256-byte aligned), evict-first in L2, no L1 allocation.
 template <int NP>
-__device__ __forceinline__ void store_dev(float *p, const float (&v)[NP]) {
+__device__ __forceinline__ void load_dev(const float *p, float (&v)[NP], unsigned long long pol) {
   if constexpr (NP % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 4)
-      __stcs(reinterpret_cast<float4 *>(p + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+      asm("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+          : "=f"(v[i]), "=f"(v[i + 1]), "=f"(v[i + 2]), "=f"(v[i + 3])
+          : "l"(p + i), "l"(pol));
   } else if constexpr (NP % 2 == 0) {
 #pragma unroll
-    for (int i = 0; i < NP; i += 2) __stcs(reinterpret_cast<float2 *>(p + i), make_float2(v[i], v[i + 1]));
+    for (int i = 0; i < NP; i += 2)
+      asm("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+          : "=f"(v[i]), "=f"(v[i + 1])
+          : "l"(p + i), "l"(pol));
   } else {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) __stcs(p + i, v[i]);
+    for (int i = 0; i < NP; ++i)
+      asm("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v[i]) : "l"(p + i), "l"(pol));
+  }
+}
+template <int NP>
+__device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsigned long long pol) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4)
+      asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p + i),
+                   "f"(v[i]), "f"(v[i + 1]), "f"(v[i + 2]), "f"(v[i + 3]), "l"(pol)
+                   : "memory");
+  } else if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2)
+      asm volatile("st.global.L1::no_allocate.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p + i), "f"(v[i]),
+                   "f"(v[i + 1]), "l"(pol)
+                   : "memory");
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+      asm volatile("st.global.L1::no_allocate.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p + i), "f"(v[i]), "l"(pol)
+                   : "memory");
   }
 }
 
@@ -220,7 +269,9 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   int nmax = nseg;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
+  if (nmax == 0) return;
 
+  const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W + gi * NP;
   const int4 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
   const int rstep = sense ? -1 : 1;
@@ -229,42 +280,63 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   const float *cdB = a.cdB + cbase;
   double *acc = a.acc + (int64_t)ch * v.ncell * kOutputs * L.gc + gi;
 
-  float inv_sinz[NP], sinz[NP], w0[NP], w1[NP], w2[NP];
+  float inv_sinz[NP], sinz[NP], w0[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const PolarDev pd = v.polar[tr.pair * NP + p];
     inv_sinz[p] = pd.inv_sinzf;
     sinz[p] = pd.sinzf;
     w0[p] = pd.wf;
-    w1[p] = pd.wf * pd.sinzf;
-    w2[p] = pd.wf * pd.sinzf * pd.sinzf;
   }
   const PairDev pr = v.pairs[tr.pair];
   const float sg = sense ? -1.f : 1.f;
   const float fx = sg * pr.cf, fy = sg * pr.sf, fxx = pr.cf * pr.cf, fxy = pr.cf * pr.sf, fyy = pr.sf * pr.sf;
-  // entering intensity, split like B so that I_in - B keeps the precision of the difference
+  // entering intensity (scaled), split like B so that I_in - B keeps the precision of the difference
   const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
 
+  // software pipeline: the record of step s+1 and the cell data and deviations of step s are in flight
+  // while step s-1 is computed
+  int4 r_cur = make_int4(0, 0, 0, 0), r_next = make_int4(0, 0, 0, 0);
+  float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+  float dB = 0.f;
+  float dv[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) dv[p] = 0.f;
+  if (nseg > 0) {
+    r_cur = ld_record(rec);
+    q = ld_table4(cd + (int64_t)r_cur.x * L.gc, pol_keep);
+    dB = ld_table1(cdB + (int64_t)r_cur.x * L.gc, pol_keep);
+    load_dev<NP>(I, dv, pol_stream);
+    if (nseg > 1) r_next = ld_record(rec + rstep);
+  }
   float psi[NP];
-  float bhi_prev = 0.f, blo_prev = 0.f;
-  int4 r = live && nseg > 0 ? __ldg(rec) : make_int4(0, 0, 0, 0);
+  float bhi_prev = in_hi, blo_prev = in_lo;   // the boundary acts as the "previous cell" of step 0
+#pragma unroll
+  for (int p = 0; p < NP; ++p) psi[p] = 0.f;
   for (int s = 0; s < nmax; ++s) {
     if (s < nseg) {
-      const int cell = r.x;
-      const float len = __int_as_float(r.y), af = __int_as_float(r.z);
-      if (s + 1 < nseg) r = __ldg(rec + (s + 1) * rstep);
-      const float4 q = __ldg(cd + (int64_t)cell * L.gc);
-      const float dB = __ldg(cdB + (int64_t)cell * L.gc);
-      float dv[NP];
-      load_dev<NP>(I, dv);
-      const float jump = s == 0 ? (in_hi - q.z) + (in_lo - q.w) : (bhi_prev - q.z) + (blo_prev - q.w);
+      // prefetch step s+1
+      float4 qn = q;
+      float dBn = dB;
+      float dvn[NP];
+      int4 rnn = r_next;
+      if (s + 1 < nseg) {
+        qn = ld_table4(cd + (int64_t)r_next.x * L.gc, pol_keep);
+        dBn = ld_table1(cdB + (int64_t)r_next.x * L.gc, pol_keep);
+        load_dev<NP>(I + W, dvn, pol_stream);
+        if (s + 2 < nseg) rnn = ld_record(rec + (s + 2) * rstep);
+      }
+      // step s
+      const int cell = r_cur.x;
+      const float len = __int_as_float(r_cur.y), af = __int_as_float(r_cur.z);
+      const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
       const float kl = q.x * len;
-      const float rkl = __frcp_rn(kl);
+      const float rkl = rcp_approx(kl);
       float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        psi[p] = s == 0 ? jump : psi[p] + jump;
+        psi[p] += jump;
         float E1, ex;
         attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
         const float d = fmaf(dv[p], q.y, dB);
@@ -272,25 +344,164 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
         const float pb = fmaf(x, E1, d);
         psi[p] = fmaf(x, ex, d);
         dv[p] = pb;
-        S0 = fmaf(w0[p], pb, S0);
-        S1 = fmaf(w1[p], pb, S1);
-        S2 = fmaf(w2[p], pb, S2);
+        const float t0 = w0[p] * pb;
+        S0 += t0;
+        const float t1 = t0 * sinz[p];
+        S1 += t1;
+        S2 = fmaf(t1, sinz[p], S2);
       }
-      store_dev<NP>(I, dv);
+      store_dev<NP>(I, dv, pol_stream);
       S0 *= af;
       S1 *= af;
       S2 *= af;
       double *ac = acc + (int64_t)cell * (kOutputs * L.gc);
-      atomicAdd(ac, f32_to_f64(S0));
-      atomicAdd(ac + L.gc, f32_to_f64(fx * S1));
-      atomicAdd(ac + 2 * L.gc, f32_to_f64(fy * S1));
-      atomicAdd(ac + 3 * L.gc, f32_to_f64(fxx * S2));
-      atomicAdd(ac + 4 * L.gc, f32_to_f64(fxy * S2));
-      atomicAdd(ac + 5 * L.gc, f32_to_f64(fyy * S2));
+      red_f64(ac, f32_to_f64(S0), pol_keep);
+      red_f64(ac + L.gc, f32_to_f64(fx * S1), pol_keep);
+      red_f64(ac + 2 * L.gc, f32_to_f64(fy * S1), pol_keep);
+      red_f64(ac + 3 * L.gc, f32_to_f64(fxx * S2), pol_keep);
+      red_f64(ac + 4 * L.gc, f32_to_f64(fxy * S2), pol_keep);
+      red_f64(ac + 5 * L.gc, f32_to_f64(fyy * S2), pol_keep);
       bhi_prev = q.z;
       blo_prev = q.w;
       I += W;
+      r_cur = r_next;
+      r_next = rnn;
+      q = qn;
+      dB = dBn;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) dv[p] = dvn[p];
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// FP32 production sweep, tile form.  One warp per (track, group chunk): lanes 0-15 walk the + sense and
+// lanes 16-31 the - sense of the same track; within a half-warp, lane = g_local * NP + p holds one group and
+// one polar cosine.  The polar cosines are folded by shuffles, then the NP lanes of a group issue its six FP64
+// reductions, which for a half-warp hit consecutive addresses of one cell (one or two L2 requests per
+// instruction).  State rows of a full chunk are 64 bytes (two sectors) per half-warp and step.
+// ---------------------------------------------------------------------------------------------------------
+constexpr int kTileWarps = 4;
+
+template <int NP>
+__device__ __forceinline__ float polar_sum(float x) {
+  if constexpr ((NP & (NP - 1)) == 0) {
+#pragma unroll
+    for (int o = 1; o < NP; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
+    return x;
+  } else {
+    const int lane = threadIdx.x & 31;
+    const int leader = (lane & 16) + ((lane & 15) / NP) * NP;
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) s += __shfl_sync(kFull, x, leader + q);
+    return s;
+  }
+}
+
+__device__ __forceinline__ float ld_dev1(const float *p, unsigned long long pol) {
+  float v;
+  asm("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_dev1(float *p, float v, unsigned long long pol) {
+  asm volatile("st.global.L1::no_allocate.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTileWarps * 32) sweep_fp32_tile_kernel(PlanView v, SweepArgs a, Layout L) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int64_t item = (int64_t)blockIdx.x * kTileWarps + wi;
+  if (item >= a.n_tiles) return;  // warp-uniform
+  const int2 it = a.tiles[item];
+  const TrackDev tr = v.tracks[it.x];
+  const int ch = it.y;
+  const int sense = lane >> 4, l = lane & 15;
+  const int gi = l / NP, p = l - gi * NP;
+  const int g0 = ch * L.gc;
+  const int gcount = min(L.gc, v.G - g0);
+  const bool valid = gi < gcount;
+  const int g = g0 + (valid ? gi : 0);
+  const int nseg = tr.nseg;
+  const int W = gcount * NP;
+  const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
+  float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W +
+             (valid ? gi * NP + p : 0);
+  const int4 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
+  const int rstep = sense ? -1 : 1;
+  const int64_t cbase = (int64_t)ch * v.ncell * L.gc + (valid ? gi : 0);
+  const float4 *cd = a.cdat + cbase;
+  const float *cdB = a.cdB + cbase;
+  double *acc = a.acc + (int64_t)ch * v.ncell * kOutputs * L.gc + (valid ? gi : 0);
+  const PolarDev pd = v.polar[tr.pair * NP + p];
+  const float inv_sinz = pd.inv_sinzf, sinz = pd.sinzf, w0 = valid ? pd.wf : 0.f;
+  const PairDev pr = v.pairs[tr.pair];
+  const float sg = sense ? -1.f : 1.f;
+  // the outputs this lane issues: o = p, p + NP, ... < 6, with their angular factors
+  constexpr int kPer = (kOutputs + NP - 1) / NP;
+  float fac[kPer];
+  int which[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int o = p + j * NP;
+    const float f[6] = {1.f, sg * pr.cf, sg * pr.sf, pr.cf * pr.cf, pr.cf * pr.sf, pr.sf * pr.sf};
+    fac[j] = o < kOutputs ? f[o] : 0.f;
+    which[j] = o == 0 ? 0 : (o <= 2 ? 1 : 2);
+  }
+  const double bin = valid ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
+  const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
+
+  // software pipeline: record of step s+1 and cell data / deviation of step s in flight during step s-1
+  int4 r_cur = ld_record(rec);
+  int4 r_next = nseg > 1 ? ld_record(rec + rstep) : r_cur;
+  float4 q = valid ? ld_table4(cd + (int64_t)r_cur.x * L.gc, pol_keep) : make_float4(1.f, 0.f, 0.f, 0.f);
+  float dB = valid ? ld_table1(cdB + (int64_t)r_cur.x * L.gc, pol_keep) : 0.f;
+  float dv = valid ? ld_dev1(I, pol_stream) : 0.f;
+  float psi = 0.f, bhi_prev = in_hi, blo_prev = in_lo;
+  for (int s = 0; s < nseg; ++s) {
+    float4 qn = q;
+    float dBn = dB, dvn = 0.f;
+    int4 rnn = r_next;
+    if (s + 1 < nseg) {
+      if (valid) {
+        qn = ld_table4(cd + (int64_t)r_next.x * L.gc, pol_keep);
+        dBn = ld_table1(cdB + (int64_t)r_next.x * L.gc, pol_keep);
+        dvn = ld_dev1(I + W, pol_stream);
+      }
+      if (s + 2 < nseg) rnn = ld_record(rec + (s + 2) * rstep);
+    }
+    const int cell = r_cur.x;
+    const float len = __int_as_float(r_cur.y), af = __int_as_float(r_cur.z);
+    psi += (bhi_prev - q.z) + (blo_prev - q.w);
+    const float kl = q.x * len;
+    float E1, ex;
+    attenuation(kl * inv_sinz, sinz * rcp_approx(kl), E1, ex);
+    const float d = fmaf(dv, q.y, dB);
+    const float x = psi - d;
+    const float pb = fmaf(x, E1, d);
+    psi = fmaf(x, ex, d);
+    if (valid) st_dev1(I, pb, pol_stream);
+    const float t0 = w0 * pb, t1 = t0 * sinz;
+    float S[3];
+    S[0] = polar_sum<NP>(t0) * af;
+    S[1] = polar_sum<NP>(t1) * af;
+    S[2] = polar_sum<NP>(t1 * sinz) * af;
+    if (valid) {
+      double *ac = acc + (int64_t)cell * (kOutputs * L.gc);
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int o = p + j * NP;
+        if (o < kOutputs) red_f64(ac + o * L.gc, f32_to_f64(fac[j] * S[which[j]]), pol_keep);
+      }
+    }
+    bhi_prev = q.z;
+    blo_prev = q.w;
+    I += W;
+    r_cur = r_next;
+    r_next = rnn;
+    q = qn;
+    dB = dBn;
+    dv = dvn;
   }
 }
 
@@ -429,6 +640,23 @@ cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_
 
 cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
   const Layout L = layout_for(v, MOLC_FP32);
+  if (a.kernel == kKernelTile) {
+    const int64_t blocks = (a.n_tiles + kTileWarps - 1) / kTileWarps;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)blocks), block(kTileWarps * 32);
+    switch (v.n_polar) {
+      case 1: sweep_fp32_tile_kernel<1><<<grid, block, 0, st>>>(v, a, L); break;
+      case 2: sweep_fp32_tile_kernel<2><<<grid, block, 0, st>>>(v, a, L); break;
+      case 3: sweep_fp32_tile_kernel<3><<<grid, block, 0, st>>>(v, a, L); break;
+      case 4: sweep_fp32_tile_kernel<4><<<grid, block, 0, st>>>(v, a, L); break;
+      case 5: sweep_fp32_tile_kernel<5><<<grid, block, 0, st>>>(v, a, L); break;
+      case 6: sweep_fp32_tile_kernel<6><<<grid, block, 0, st>>>(v, a, L); break;
+      case 7: sweep_fp32_tile_kernel<7><<<grid, block, 0, st>>>(v, a, L); break;
+      case 8: sweep_fp32_tile_kernel<8><<<grid, block, 0, st>>>(v, a, L); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)blocks), block(kSweepBlock);
