@@ -171,15 +171,6 @@ molc_status molc_intensity_import(molc_plan *plan, molc_precision prec, void *I,
 molc_status molc_tracks_export(const molc_plan *plan, int64_t *dir_ray_off, int64_t *ray_seg_off, double *width,
                                int *entry, int *cell, double *len, double *area);
 
-/* Work decomposition of the FP32 sweep (both produce the same results to rounding, on the same state layout):
- *  MOLC_FP32_TILE  (0, default): a warp per (characteristic, group chunk); lanes hold (sense, group, polar
- *                  cosine); polar cosines folded by warp shuffles before the FP64 reductions.
- *  MOLC_FP32_TRACK (1): a thread per (characteristic, sense, group) with every polar cosine in registers. */
-#define MOLC_FP32_TILE 0
-#define MOLC_FP32_TRACK 1
-molc_status molc_set_fp32_variant(molc_plan *plan, int variant);
-int molc_get_fp32_variant(const molc_plan *plan);   /* -1 for a NULL plan */
-
 /* Kernel timing for benchmarks: while enabled, every molc_sweep / molc_batch_sweep records a CUDA event pair
  * around its sweep kernel (at most 4096 launches are kept).  molc_kernel_time synchronises with the last
  * recorded event, returns the summed elapsed milliseconds and the number of timed launches, and clears the

@@ -91,9 +91,7 @@ struct molc_plan {
   float *d_cdB = nullptr;
   double *d_acc = nullptr;
   int2 *d_items32 = nullptr;
-  int2 *d_tiles32 = nullptr;
-  int64_t n_items32 = 0, n_tiles32 = 0;
-  int fp32_kernel = kKernelTile;
+  int64_t n_items32 = 0;
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
@@ -197,7 +195,8 @@ inline DD crossing(double X, double t, double q, double d) {
 // characteristic passes within eps of a vertex, i.e. steps diagonally).  A segment belongs to the cell that
 // contains its midpoint.  Returns false if the line misses the domain.
 bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, double s, double t,
-                        std::vector<int> &cells, std::vector<double> &lens, int &entry_plus, int &entry_minus) {
+                        std::vector<int> &cells, std::vector<double> &lens, std::vector<double> &lens_lo,
+                        int &entry_plus, int &entry_minus) {
   const double eps = 1e-12 * std::min(hx, hy);
   const double bx = -t * s, by = t * c;  // the point of the line at u = 0
   const double x1 = g.x0 + g.lx, y1 = g.y0 + g.ly;
@@ -242,6 +241,7 @@ bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, doub
   }
   cells.clear();
   lens.clear();
+  lens_lo.clear();
   size_t ix = 0, iy = 0;
   DD a = uin;
   while (true) {
@@ -255,7 +255,8 @@ bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, doub
       b = uout;
       last = true;
     }
-    const double len = (b.hi - a.hi) + (b.lo - a.lo);
+    const DD ld = fast_two_sum(b.hi - a.hi, b.lo - a.lo);  // b.hi - a.hi is exact where it matters (close)
+    const double len = ld.hi;
     if (len > eps) {
       const double m = a.hi + 0.5 * len;
       int cx = (int)std::floor((bx + m * c - g.x0) / hx);
@@ -264,6 +265,7 @@ bool cut_characteristic(const molc_grid &g, double hx, double hy, double c, doub
       cy = std::min(std::max(cy, 0), g.ny - 1);
       cells.push_back(cy * g.nx + cx);
       lens.push_back(len);
+      lens_lo.push_back(ld.lo);
     }
     a = b;
     if (last) break;
@@ -295,8 +297,7 @@ void free_events(molc_plan *p) {
 void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
-                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
-                  p->d_tiles32};
+                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -487,14 +488,14 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   const int ncell = g.nx * g.ny;
   std::vector<double> t, wv;
   std::vector<int> cells;
-  std::vector<double> lens;
+  std::vector<double> lens, lens_lo, seg_len_lo;
   p->pair_track_off.push_back(0);
   for (int j = 0; j < p->n_pairs; ++j) {
     const double c = p->pairs[j].c, s = p->pairs[j].s;
     characteristic_offsets(g, c, s, ray_spacing, layout, t, wv);
     for (size_t k = 0; k < t.size(); ++k) {
       int ep, em;
-      if (!cut_characteristic(g, p->hx, p->hy, c, s, t[k], cells, lens, ep, em)) continue;
+      if (!cut_characteristic(g, p->hx, p->hy, c, s, t[k], cells, lens, lens_lo, ep, em)) continue;
       if (cells.size() > (size_t)1 << 30) {
         delete p;
         return fail(MOLC_ERR_INVALID_ARG, "create: characteristic too long");
@@ -505,6 +506,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         p->seg_cell.push_back(cells[q]);
         p->seg_len.push_back(lens[q]);
         p->seg_afrac.push_back(lens[q] * wv[k]);  // A for now
+        seg_len_lo.push_back(lens_lo[q]);
       }
     }
     p->pair_track_off.push_back((int64_t)p->tracks.size());
@@ -516,14 +518,32 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     return fail(MOLC_ERR_INVALID_ARG, "create: no characteristic crosses the domain");
   }
   // ---- areas (Eq. 14), optional renormalisation per (cell, pair), area fractions a = A / V, geometric moments
+  //   G_ab(i) = sum_m omega_m Omega_a Omega_b sum_{C(i,m)} A / V = sum_j W_ab(j) (1 + e_ij),
+  // with W_ab(j) the pair's angular weight and e_ij = sum_{C(i,j)} A / V - 1 the area defect.  With
+  // renormalisation e_ij = 0 by construction.  Otherwise e_ij is formed from double-double lengths and sums: for
+  // the paper's layout it is ~1e-15 (double band edges), and N_xy's B part, sum_j W_xy(j) e_ij, is a small
+  // sum that must not carry the rounding of sum_j W_xy(j) (which is exactly zero for a symmetric set).
   const bool renorm = flags & MOLC_AREA_RENORM;
   std::vector<double> asum(ncell);
+  std::vector<Acc2> asum_dd(ncell);
   std::vector<Acc2> g0(ncell), gxx(ncell), gxy(ncell), gyy(ncell);
+  Acc2 w0_all, wxx_all, wxy_all, wyy_all;
   for (int j = 0; j < p->n_pairs; ++j) {
     std::fill(asum.begin(), asum.end(), 0.0);
+    std::fill(asum_dd.begin(), asum_dd.end(), Acc2());
     const int64_t s0 = p->tracks[p->pair_track_off[j]].seg_off;
     const int64_t s1 = p->pair_track_off[j + 1] < T ? p->tracks[p->pair_track_off[j + 1]].seg_off : S;
-    for (int64_t q = s0; q < s1; ++q) asum[p->seg_cell[q]] += p->seg_afrac[q];
+    for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) {
+      const double w = p->tracks[k].width;
+      for (int64_t q = p->tracks[k].seg_off; q < p->tracks[k].seg_off + p->tracks[k].nseg; ++q) {
+        const int i = p->seg_cell[q];
+        asum[i] += p->seg_afrac[q];
+        const double pa = p->seg_len[q] * w;
+        asum_dd[i].add(pa);
+        asum_dd[i].add(std::fma(p->seg_len[q], w, -pa));
+        asum_dd[i].add(seg_len_lo[q] * w);
+      }
+    }
     if (renorm) {
       for (int i = 0; i < ncell; ++i)
         if (!(asum[i] > 0)) {
@@ -535,7 +555,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     } else {
       for (int64_t q = s0; q < s1; ++q) p->seg_afrac[q] /= p->V;
     }
-    // sum over the pair's directions of omega (times Omega components) and over its segments of a
+    // sum over the pair's directions of omega (times Omega components)
     double w0 = 0, wxx = 0, wxy = 0, wyy = 0;
     const double c = p->pairs[j].c, s = p->pairs[j].s;
     for (int q = 0; q < p->n_polar; ++q) {
@@ -546,17 +566,24 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       wxy += ww * s2 * c * s;
       wyy += ww * s2 * s * s;
     }
-    // With renormalisation, or with the paper's layout (bands free of vertices tile each cell, so the areas
-    // l w sum exactly to the cell area), sum_{C(i,m)} A = V holds exactly and is used as such: the B parts of
-    // F and N_xy then cancel exactly instead of to the rounding of the FP64 areas.
-    const bool exact_tiling = renorm || layout == MOLC_RAYS_PAPER;
-    for (int i = 0; i < ncell; ++i) {
-      const double a = exact_tiling ? 1.0 : asum[i] / p->V;
-      g0[i].add(w0 * a);
-      gxx[i].add(wxx * a);
-      gxy[i].add(wxy * a);
-      gyy[i].add(wyy * a);
-    }
+    w0_all.add(w0);
+    wxx_all.add(wxx);
+    wxy_all.add(wxy);
+    wyy_all.add(wyy);
+    if (!renorm)
+      for (int i = 0; i < ncell; ++i) {
+        const double e = ((asum_dd[i].hi - p->V) + asum_dd[i].lo) / p->V;
+        g0[i].add(w0 * e);
+        gxx[i].add(wxx * e);
+        gxy[i].add(wxy * e);
+        gyy[i].add(wyy * e);
+      }
+  }
+  for (int i = 0; i < ncell; ++i) {
+    g0[i].add(w0_all.value());
+    gxx[i].add(wxx_all.value());
+    gxy[i].add(wxy_all.value());
+    gyy[i].add(wyy_all.value());
   }
   std::vector<double> geo(4 * (size_t)ncell);
   for (int i = 0; i < ncell; ++i) {
@@ -605,9 +632,15 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   int l2_bytes = 0;
   if (!p->host_only) cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device);
   if (l2_bytes <= 0) l2_bytes = 128 << 20;
+  // chunk size: the largest that fits 60% of L2, rounded down so that a chunk's state rows
+  // (gcount * n_polar floats) are a whole number of 32-byte sectors when that is possible
   const double per_group = 68.0 * ncell;
-  const int gc_l2 = std::max(1, (int)std::floor(0.5 * l2_bytes / per_group));
-  const int gc32 = std::max(1, std::min({p->G, gc_l2, 16 / std::max(p->n_polar, 1)}));
+  int gc32 = std::max(1, std::min(p->G, (int)std::floor(0.6 * l2_bytes / per_group)));
+  for (int gc = gc32; gc >= 1; --gc)
+    if ((gc * p->n_polar) % 8 == 0 || gc == p->G) {
+      gc32 = gc;
+      break;
+    }
   const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
   std::vector<int64_t> order(T);
   for (int64_t k = 0; k < T; ++k) order[k] = k;
@@ -624,12 +657,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       for (int sense = 0; sense < 2; ++sense)
         for (int gi = 0; gi < gcount; ++gi) items.push_back(make_int2((int)k, sense | (gi << 1) | (ch << 16)));
   }
-  std::vector<int2> tiles;
-  tiles.reserve((size_t)T * nch32);
-  for (int ch = 0; ch < nch32; ++ch)
-    for (int64_t k : order) tiles.push_back(make_int2((int)k, ch));
   p->n_items32 = (int64_t)items.size();
-  p->n_tiles32 = (int64_t)tiles.size();
   p->acc_elems = (size_t)ncell * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
 
   PlanView &v = p->view;
@@ -665,7 +693,6 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
   UP(d_items32, items.data(), items.size(), "items")
-  UP(d_tiles32, tiles.data(), tiles.size(), "tiles")
 #undef UP
   if (st == MOLC_OK) {
     cudaError_t e = cudaMemset(p->d_status, 0, sizeof(int));
@@ -772,9 +799,6 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.acc = p->d_acc;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
-  a.tiles = p->d_tiles32;
-  a.n_tiles = p->n_tiles32;
-  a.kernel = p->fp32_kernel;
   const Layout L = layout_for(p->view, prec);
   cudaError_t e =
       cudaMemsetAsync(p->d_acc, 0, (size_t)L.n_chunks * L.gc * p->view.ncell * kOutputs * sizeof(double), st);
@@ -863,16 +887,6 @@ molc_status molc_tracks_export(const molc_plan *p, int64_t *dir_ray_off, int64_t
   }
   return MOLC_OK;
 }
-
-molc_status molc_set_fp32_variant(molc_plan *p, int variant) {
-  if (!p) return fail(MOLC_ERR_INVALID_ARG, "set_fp32_variant: NULL plan");
-  if (variant != kKernelTile && variant != kKernelTrack)
-    return fail(MOLC_ERR_INVALID_ARG, "set_fp32_variant: unknown variant %d", variant);
-  p->fp32_kernel = variant;
-  return MOLC_OK;
-}
-
-int molc_get_fp32_variant(const molc_plan *p) { return p ? p->fp32_kernel : -1; }
 
 molc_status molc_kernel_timing(molc_plan *p, int enable) {
   if (!p) return fail(MOLC_ERR_INVALID_ARG, "kernel_timing: NULL plan");

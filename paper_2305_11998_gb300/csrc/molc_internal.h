@@ -10,8 +10,6 @@ namespace molc {
 
 constexpr int kMaxPolarFP32 = 8;     // FP32 sweep: polar cosines per azimuth handled by one half-warp
 constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators per (cell, group)
-constexpr int kKernelTile = 0;       // FP32 sweep variants: warp per (track, chunk), lane = (sense, group, polar)
-constexpr int kKernelTrack = 1;      //                      thread per (track, sense, group), polar in registers
 
 // Device status bits (the first one set wins in molc_device_status).
 constexpr int kStatusNonfinite = 1;
@@ -95,12 +93,9 @@ struct SweepArgs {
   float4 *cdat;       // FP32: [chunk][cell][gc] {kappa~, 1/(c dt kappa~), B_hi, B_lo}
   float *cdB;         // FP32: [chunk][cell][gc] (B_ref - B) / (c dt kappa~)
   double *acc;        // [chunk][cell][6][gc] FP64 accumulators
-  const int2 *items;  // FP32 track kernel: one per thread, {track, sense | g_local << 1 | chunk << 16};
-                      // chunk-major, longest track first, then sense, then group
+  const int2 *items;  // FP32: one per thread, {track, sense | g_local << 1 | chunk << 16}; chunk-major,
+                      // longest track first, then sense, then group
   int64_t n_items;
-  const int2 *tiles;  // FP32 tile kernel: one per warp, {track, chunk}; chunk-major, longest track first
-  int64_t n_tiles;
-  int kernel;         // kKernelTile or kKernelTrack
 };
 
 // Kernel launchers (molc_kernels.cu).  Return cudaSuccess or the launch error.

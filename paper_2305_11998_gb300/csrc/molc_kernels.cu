@@ -141,33 +141,29 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
 // ---------------------------------------------------------------------------------------------------------
 constexpr int kSweepBlock = 128;
 
-// (1 - e^-tau)/tau and e^-tau in FP32: a degree-8 Taylor polynomial below tau = 1/2 (truncation < 6e-10
-// relative), ex2.approx above (no cancellation there: 1 - e^-tau > 0.39).  inv_tau is 1/tau.
+// (1 - e^-tau)/tau and e^-tau in FP32.  With h = e^(-tau/2) (ex2.approx):
+//   tau < 1/2:  E1 = h sinh(tau/2) / (tau/2), the even Taylor series in y = tau^2/4 to y^3 (truncation
+//               < 5e-11 relative), free of cancellation;
+//   tau >= 1/2: E1 = (1 - e^-tau) / tau (1 - e^-tau > 0.39, no cancellation).
+// e^-tau itself from ex2.approx.  inv_tau is 1/tau.
 __device__ __forceinline__ void attenuation(float tau, float inv_tau, float &E1, float &ex) {
-  float p = 1.f / 362880.f;
-  p = fmaf(p, tau, -1.f / 40320.f);
-  p = fmaf(p, tau, 1.f / 5040.f);
-  p = fmaf(p, tau, -1.f / 720.f);
-  p = fmaf(p, tau, 1.f / 120.f);
-  p = fmaf(p, tau, -1.f / 24.f);
-  p = fmaf(p, tau, 1.f / 6.f);
-  p = fmaf(p, tau, -0.5f);
-  p = fmaf(p, tau, 1.f);
-  const float e = __expf(-tau);
-  const bool small = tau < 0.5f;
-  ex = small ? fmaf(-tau, p, 1.f) : e;
-  E1 = small ? p : (1.f - e) * inv_tau;
+  const float h = __expf(-0.5f * tau);
+  ex = __expf(-tau);
+  const float y = 0.25f * tau * tau;
+  float p = fmaf(y, 1.f / 5040.f, 1.f / 120.f);
+  p = fmaf(p, y, 1.f / 6.f);
+  p = fmaf(p, y, 1.f);
+  E1 = tau < 0.5f ? h * p : (1.f - ex) * inv_tau;
 }
 
-// FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU).  Exact for normal
-// numbers (exponent rebiased by 1023 - 127, mantissa shifted into place); zeros and subnormals
-// (|x| < 2^-126) become a signed zero, an absolute error below 2^-126 per converted value.
+// FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU): exponent rebiased by
+// 1023 - 127 and mantissa shifted into place, exact for normal numbers.  Zeros and subnormals (|x| < 2^-126)
+// map to a value of the same sign and magnitude below 2^-126; the FP32 sweep works in units where max B is
+// ~2^100, so that is below 1e-68 of max B.
 __device__ __forceinline__ double f32_to_f64(float x) {
   const unsigned u = __float_as_uint(x);
-  const unsigned mag = u & 0x7fffffffu;
-  const bool normal = mag >= 0x00800000u;
-  const unsigned hi = (u & 0x80000000u) | (normal ? (mag >> 3) + 0x38000000u : 0u);
-  return __hiloint2double((int)hi, normal ? (int)(u << 29) : 0);
+  const unsigned hi = (u & 0x80000000u) | (((u >> 3) & 0x0fffffffu) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 // L2 eviction policies (sm_80+ createpolicy) and loads/stores/reductions carrying them: the streamed state is
@@ -375,137 +371,6 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
 }
 
 // ---------------------------------------------------------------------------------------------------------
-// FP32 production sweep, tile form.  One warp per (track, group chunk): lanes 0-15 walk the + sense and
-// lanes 16-31 the - sense of the same track; within a half-warp, lane = g_local * NP + p holds one group and
-// one polar cosine.  The polar cosines are folded by shuffles, then the NP lanes of a group issue its six FP64
-// reductions, which for a half-warp hit consecutive addresses of one cell (one or two L2 requests per
-// instruction).  State rows of a full chunk are 64 bytes (two sectors) per half-warp and step.
-// ---------------------------------------------------------------------------------------------------------
-constexpr int kTileWarps = 4;
-
-template <int NP>
-__device__ __forceinline__ float polar_sum(float x) {
-  if constexpr ((NP & (NP - 1)) == 0) {
-#pragma unroll
-    for (int o = 1; o < NP; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
-  } else {
-    const int lane = threadIdx.x & 31;
-    const int leader = (lane & 16) + ((lane & 15) / NP) * NP;
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) s += __shfl_sync(kFull, x, leader + q);
-    return s;
-  }
-}
-
-__device__ __forceinline__ float ld_dev1(const float *p, unsigned long long pol) {
-  float v;
-  asm("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ void st_dev1(float *p, float v, unsigned long long pol) {
-  asm volatile("st.global.L1::no_allocate.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
-}
-
-template <int NP>
-__global__ void __launch_bounds__(kTileWarps * 32) sweep_fp32_tile_kernel(PlanView v, SweepArgs a, Layout L) {
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const int64_t item = (int64_t)blockIdx.x * kTileWarps + wi;
-  if (item >= a.n_tiles) return;  // warp-uniform
-  const int2 it = a.tiles[item];
-  const TrackDev tr = v.tracks[it.x];
-  const int ch = it.y;
-  const int sense = lane >> 4, l = lane & 15;
-  const int gi = l / NP, p = l - gi * NP;
-  const int g0 = ch * L.gc;
-  const int gcount = min(L.gc, v.G - g0);
-  const bool valid = gi < gcount;
-  const int g = g0 + (valid ? gi : 0);
-  const int nseg = tr.nseg;
-  const int W = gcount * NP;
-  const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
-  float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W +
-             (valid ? gi * NP + p : 0);
-  const int4 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
-  const int rstep = sense ? -1 : 1;
-  const int64_t cbase = (int64_t)ch * v.ncell * L.gc + (valid ? gi : 0);
-  const float4 *cd = a.cdat + cbase;
-  const float *cdB = a.cdB + cbase;
-  double *acc = a.acc + (int64_t)ch * v.ncell * kOutputs * L.gc + (valid ? gi : 0);
-  const PolarDev pd = v.polar[tr.pair * NP + p];
-  const float inv_sinz = pd.inv_sinzf, sinz = pd.sinzf, w0 = valid ? pd.wf : 0.f;
-  const PairDev pr = v.pairs[tr.pair];
-  const float sg = sense ? -1.f : 1.f;
-  // the outputs this lane issues: o = p, p + NP, ... < 6, with their angular factors
-  constexpr int kPer = (kOutputs + NP - 1) / NP;
-  float fac[kPer];
-  int which[kPer];
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) {
-    const int o = p + j * NP;
-    const float f[6] = {1.f, sg * pr.cf, sg * pr.sf, pr.cf * pr.cf, pr.cf * pr.sf, pr.sf * pr.sf};
-    fac[j] = o < kOutputs ? f[o] : 0.f;
-    which[j] = o == 0 ? 0 : (o <= 2 ? 1 : 2);
-  }
-  const double bin = valid ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
-  const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
-
-  // software pipeline: record of step s+1 and cell data / deviation of step s in flight during step s-1
-  int4 r_cur = ld_record(rec);
-  int4 r_next = nseg > 1 ? ld_record(rec + rstep) : r_cur;
-  float4 q = valid ? ld_table4(cd + (int64_t)r_cur.x * L.gc, pol_keep) : make_float4(1.f, 0.f, 0.f, 0.f);
-  float dB = valid ? ld_table1(cdB + (int64_t)r_cur.x * L.gc, pol_keep) : 0.f;
-  float dv = valid ? ld_dev1(I, pol_stream) : 0.f;
-  float psi = 0.f, bhi_prev = in_hi, blo_prev = in_lo;
-  for (int s = 0; s < nseg; ++s) {
-    float4 qn = q;
-    float dBn = dB, dvn = 0.f;
-    int4 rnn = r_next;
-    if (s + 1 < nseg) {
-      if (valid) {
-        qn = ld_table4(cd + (int64_t)r_next.x * L.gc, pol_keep);
-        dBn = ld_table1(cdB + (int64_t)r_next.x * L.gc, pol_keep);
-        dvn = ld_dev1(I + W, pol_stream);
-      }
-      if (s + 2 < nseg) rnn = ld_record(rec + (s + 2) * rstep);
-    }
-    const int cell = r_cur.x;
-    const float len = __int_as_float(r_cur.y), af = __int_as_float(r_cur.z);
-    psi += (bhi_prev - q.z) + (blo_prev - q.w);
-    const float kl = q.x * len;
-    float E1, ex;
-    attenuation(kl * inv_sinz, sinz * rcp_approx(kl), E1, ex);
-    const float d = fmaf(dv, q.y, dB);
-    const float x = psi - d;
-    const float pb = fmaf(x, E1, d);
-    psi = fmaf(x, ex, d);
-    if (valid) st_dev1(I, pb, pol_stream);
-    const float t0 = w0 * pb, t1 = t0 * sinz;
-    float S[3];
-    S[0] = polar_sum<NP>(t0) * af;
-    S[1] = polar_sum<NP>(t1) * af;
-    S[2] = polar_sum<NP>(t1 * sinz) * af;
-    if (valid) {
-      double *ac = acc + (int64_t)cell * (kOutputs * L.gc);
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) {
-        const int o = p + j * NP;
-        if (o < kOutputs) red_f64(ac + o * L.gc, f32_to_f64(fac[j] * S[which[j]]), pol_keep);
-      }
-    }
-    bhi_prev = q.z;
-    blo_prev = q.w;
-    I += W;
-    r_cur = r_next;
-    r_next = rnn;
-    q = qn;
-    dB = dBn;
-    dv = dvn;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------------------
 // finalize: cell assembly.  acc holds sum_m omega_m sum_{C(i,m)} (A/V) psibar (times Omega components);
 // the B_i part uses the geometric moments geo = sum_m omega_m sum_{C(i,m)} A/V (times Omega components).
 //   E = (B geo0 + D)/c, F = acc, N_ab = B geo_ab + acc_ab.  (The B part of F is zero by symmetry.)
@@ -640,23 +505,6 @@ cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_
 
 cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
   const Layout L = layout_for(v, MOLC_FP32);
-  if (a.kernel == kKernelTile) {
-    const int64_t blocks = (a.n_tiles + kTileWarps - 1) / kTileWarps;
-    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    const dim3 grid((unsigned)blocks), block(kTileWarps * 32);
-    switch (v.n_polar) {
-      case 1: sweep_fp32_tile_kernel<1><<<grid, block, 0, st>>>(v, a, L); break;
-      case 2: sweep_fp32_tile_kernel<2><<<grid, block, 0, st>>>(v, a, L); break;
-      case 3: sweep_fp32_tile_kernel<3><<<grid, block, 0, st>>>(v, a, L); break;
-      case 4: sweep_fp32_tile_kernel<4><<<grid, block, 0, st>>>(v, a, L); break;
-      case 5: sweep_fp32_tile_kernel<5><<<grid, block, 0, st>>>(v, a, L); break;
-      case 6: sweep_fp32_tile_kernel<6><<<grid, block, 0, st>>>(v, a, L); break;
-      case 7: sweep_fp32_tile_kernel<7><<<grid, block, 0, st>>>(v, a, L); break;
-      case 8: sweep_fp32_tile_kernel<8><<<grid, block, 0, st>>>(v, a, L); break;
-      default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-  }
   const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)blocks), block(kSweepBlock);

@@ -27,8 +27,7 @@ MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")
 # every symbol include/molc.h declares
 EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "molc_intensity_count",
             "molc_intensity_bytes", "molc_intensity_init", "molc_sweep", "molc_closure", "molc_intensity_export",
-            "molc_intensity_import", "molc_tracks_export", "molc_set_fp32_variant", "molc_get_fp32_variant",
-            "molc_kernel_timing", "molc_kernel_time",
+            "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy")
 
 
@@ -89,8 +88,6 @@ def load(build_if_needed: bool = True):
         "molc_intensity_export": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "molc_intensity_import": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp, vp]),
         "molc_tracks_export": (C.c_int, [vp, i64p, i64p, dp, ip, ip, dp, dp]),
-        "molc_set_fp32_variant": (C.c_int, [vp, C.c_int]),
-        "molc_get_fp32_variant": (C.c_int, [vp]),
         "molc_kernel_timing": (C.c_int, [vp, C.c_int]),
         "molc_kernel_time": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_device_status": (C.c_int, [vp, ip]),
@@ -241,14 +238,6 @@ class Plan:
         if grey:
             f["grey"] = fg
         return f
-
-    @property
-    def fp32_variant(self) -> str:
-        return ("tile", "track")[self._lib.molc_get_fp32_variant(self._h)]
-
-    @fp32_variant.setter
-    def fp32_variant(self, name: str):
-        _check(self._lib.molc_set_fp32_variant(self._h, {"tile": 0, "track": 1}[name]))
 
     def kernel_timing(self, enable: bool = True):
         _check(self._lib.molc_kernel_timing(self._h, int(enable)))

@@ -32,11 +32,8 @@ def host(d):
     return {k: v.cpu().numpy() for k, v in d.items()}
 
 
-def run_gpu(molc, wl, d, prec, steps=1, quad=None, layout="uniform", renorm=True, spacing=None, export=False,
-            variant=None):
+def run_gpu(molc, wl, d, prec, steps=1, quad=None, layout="uniform", renorm=True, spacing=None, export=False):
     P = molc.Plan.from_workload(wl, quad=quad, layout=layout, renorm=renorm, spacing=spacing)
-    if variant:
-        P.fp32_variant = variant
     k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
     I = P.new_intensity(prec)
     P.intensity_init(prec, I, B)
@@ -93,11 +90,10 @@ def test_small_multistep_vs_binary128(molc, prec):
         parity.compare(g_, r_, prec, d["c"])
 
 
-@pytest.mark.parametrize("variant", ["tile", "track"])
-def test_fp32_ten_steps_64x64(molc, variant):
+def test_fp32_ten_steps_64x64(molc):
     wl = synth.WORKLOADS["fc64_g17_d128"]
     d = wl.inputs(0)
-    got, _ = run_gpu(molc, wl, d, "fp32", steps=wl.steps, variant=variant)
+    got, _ = run_gpu(molc, wl, d, "fp32", steps=wl.steps)
     ref, _ = run_oracle(wl, d, "double", steps=wl.steps)
     for g_, r_ in zip(got, ref):
         parity.compare(g_, r_, "fp32", d["c"], ref_precision="double")
@@ -150,16 +146,13 @@ def variant_inputs(v, seed=0):
 
 
 @pytest.mark.parametrize("vi", range(len(VARIANTS)))
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32-track"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_variants_vs_binary128(molc, prec, vi):
     v = VARIANTS[vi]
     wl, q, d, Ly, sp = variant_inputs(v, vi)
     layout = v.get("layout", "uniform")
     renorm = v.get("renorm", layout == "uniform")
     P = molc.Plan(v["nx"], v["ny"], wl.L, Ly, q.mu, q.cos_phi, q.sin_phi, q.w, v["G"], sp, layout, renorm)
-    if prec == "fp32-track":
-        P.fp32_variant = "track"
-        prec = "fp32"
     k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
     I = P.new_intensity(prec)
     P.intensity_init(prec, I, B)
