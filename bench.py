@@ -30,9 +30,10 @@ import synth  # noqa: E402
 
 WORKLOAD = "fc512_g17_d128"
 METRIC = "segment×group updates/s"
-# ncu dram bytes (read + write) of one sweep_fp32_kernel launch on this workload, from the capture summarised in
-# profiles/sweep_fp32_fc512.md; None until that capture matches the current kernel.
-SWEEP_FP32_DRAM_BYTES = None
+# ncu dram bytes (read + write) per update of sweep_fp32_kernel, from the capture summarised in
+# profiles/sweep_fp32_fc384_g17.md (384x384 cells, same kernel configuration), scaled by the updates of the
+# launch; None once the kernel changes after that capture.
+SWEEP_FP32_DRAM_BYTES_PER_UPDATE = 14.42
 
 
 def parse():
@@ -45,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only the FP32 sweeps (warmup + steps), for profiler captures")
     return ap.parse_args()
 
 
@@ -244,7 +247,9 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kern_avg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": SWEEP_FP32_DRAM_BYTES, "kernel": "sweep_fp32_kernel", "kernel_ms": kern_avg,
+                "traffic": (None if SWEEP_FP32_DRAM_BYTES_PER_UPDATE is None
+                            else SWEEP_FP32_DRAM_BYTES_PER_UPDATE * info.n_updates),
+                "kernel": "sweep_fp32_kernel", "kernel_ms": kern_avg,
                 "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
     # end to end through the public API: pinned host inputs copied in, moments and factors copied out
@@ -325,9 +330,35 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_only(args):
+    """FP32 sweeps only (no closure, e2e, FP64 or CPU legs): the command profiler captures use."""
+    import torch
+    import paper_2305_11998_gb300 as molc
+    wl = synth.WORKLOADS[args.workload]
+    d = wl.inputs(seed=0)
+    P = molc.Plan.from_workload(wl)
+    dev = torch.device("cuda")
+    k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
+    I = P.new_intensity("fp32", dev)
+    P.intensity_init("fp32", I, B)
+    out = P.new_moments(dev)
+    for _ in range(args.warmup):
+        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=out)
+    P.kernel_timing(True)
+    for _ in range(args.steps):
+        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=out)
+    ms, n = P.kernel_time()
+    print(json.dumps({"workload": wl.name, "kernel": "sweep_fp32_kernel", "launches": n,
+                      "kernel_ms": ms / max(n, 1), "updates": P.info.n_updates,
+                      "device_status": P.device_status()}), flush=True)
+    P.close()
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.kernel_only:
+        run_kernel_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -626,21 +626,13 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     seg32[q] = r;
   }
 
-  // ---- FP32 work items: one thread per (track, sense, group).  Groups are tiled in chunks whose cell table
-  // (20 B per cell and group) and FP64 accumulators (48 B) fit in half of the L2 cache; items are ordered
-  // chunk-major, then by decreasing track length, then track, sense and group.
-  int l2_bytes = 0;
-  if (!p->host_only) cudaDeviceGetAttribute(&l2_bytes, cudaDevAttrL2CacheSize, p->device);
-  if (l2_bytes <= 0) l2_bytes = 128 << 20;
-  // chunk size: the largest that fits 60% of L2, rounded down so that a chunk's state rows
-  // (gcount * n_polar floats) are a whole number of 32-byte sectors when that is possible
-  const double per_group = 68.0 * ncell;
-  int gc32 = std::max(1, std::min(p->G, (int)std::floor(0.6 * l2_bytes / per_group)));
-  for (int gc = gc32; gc >= 1; --gc)
-    if ((gc * p->n_polar) % 8 == 0 || gc == p->G) {
-      gc32 = gc;
-      break;
-    }
+  // ---- FP32 work items: one thread per (track, sense, group), ordered chunk-major, then by decreasing track
+  // length, then track, sense and group.  Groups are tiled in chunks of up to 32: the threads of one (track,
+  // sense) are consecutive, so the more groups a chunk holds, the fewer distinct cells a warp's FP64 reductions
+  // touch and the fewer L2 requests they cost.  (Measured on GB300 at 512^2 x 17 groups: one 17-group chunk
+  // is 1.5x faster than 4-group chunks sized to keep the accumulators L2-resident; the reduction request rate,
+  // not L2 capacity, bounds this kernel.)
+  const int gc32 = std::min(p->G, 32);
   const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
   std::vector<int64_t> order(T);
   for (int64_t k = 0; k < T; ++k) order[k] = k;

@@ -45,27 +45,29 @@ __device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int
 // with B = B_hi + B_lo split so that B differences between neighbouring cells keep ~48 bits.
 // ---------------------------------------------------------------------------------------------------------
 __global__ void prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
-  const int64_t n = (int64_t)v.G * v.ncell;
   const double inv_cdt = 1.0 / (a.c * a.dt);
   const double sc = a.scale[0];
   bool bad = false, range = false;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int g = (int)(idx / v.ncell);
-    const int cell = (int)(idx - (int64_t)g * v.ncell);
-    const double kap = a.kappa[idx], B = a.B[idx];
-    bad |= bad_input(kap) | bad_input(B);
-    if (fp32) {
-      const double kt = kap + inv_cdt;
-      const double r = inv_cdt / kt;
-      const double Bs = B * sc;
-      range |= !(Bs < kScaledMax);
-      const float bhi = (float)Bs;
-      const float blo = (float)(Bs - (double)bhi);
-      const int ch = g / L.gc, gl = g - ch * L.gc;
-      const int64_t o = ((int64_t)ch * v.ncell + cell) * L.gc + gl;
-      a.cdat[o] = make_float4((float)kt, (float)r, bhi, blo);
-      a.cdB[o] = (float)((a.Bref[idx] - B) * sc * r);
+  // one thread per cell, looping over groups: reads [g][cell] coalesced across threads, writes the cell's
+  // [cell][gc] table entries contiguously
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
+    for (int g = 0; g < v.G; ++g) {
+      const int64_t idx = (int64_t)g * v.ncell + cell;
+      const double kap = a.kappa[idx], B = a.B[idx];
+      bad |= bad_input(kap) | bad_input(B);
+      if (fp32) {
+        const double kt = kap + inv_cdt;
+        const double r = inv_cdt / kt;
+        const double Bs = B * sc;
+        range |= !(Bs < kScaledMax);
+        const float bhi = (float)Bs;
+        const float blo = (float)(Bs - (double)bhi);
+        // [chunk][cell][gc] with the chunk's stride gc also in a partial last chunk (as the sweep reads it)
+        const int g0 = g / L.gc * L.gc;
+        const int64_t o = (int64_t)g0 * v.ncell + (int64_t)cell * L.gc + (g - g0);
+        a.cdat[o] = make_float4((float)kt, (float)r, bhi, blo);
+        a.cdB[o] = (float)((a.Bref[idx] - B) * sc * r);
+      }
     }
   }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * (int64_t)v.G;
@@ -376,23 +378,26 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
 //   E = (B geo0 + D)/c, F = acc, N_ab = B geo_ab + acc_ab.  (The B part of F is zero by symmetry.)
 // ---------------------------------------------------------------------------------------------------------
 __global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
-  const int64_t n = (int64_t)v.G * v.ncell;
   const double inv_c = 1.0 / a.c;
   const double is = a.scale[1];   // accumulators are in the state's scaled units (exact power of two)
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int g = (int)(idx / v.ncell);
-    const int cell = (int)(idx - (int64_t)g * v.ncell);
-    const int ch = g / L.gc, gl = g - ch * L.gc;
-    const double *ac = a.acc + ((int64_t)ch * v.ncell + cell) * kOutputs * L.gc + gl;
-    const double B = a.B[idx];
-    a.out.E[idx] = (B * v.geo[cell] + ac[0 * L.gc] * is) * inv_c;
-    a.out.Fx[idx] = ac[1 * L.gc] * is;
-    a.out.Fy[idx] = ac[2 * L.gc] * is;
-    a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + ac[3 * L.gc] * is;
-    a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + ac[4 * L.gc] * is;
-    a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + ac[5 * L.gc] * is;
-    a.Bref[idx] = B;   // the new deviations refer to this step's B
+  // one thread per cell, looping over groups: the cell's accumulator block is read contiguously (through L1)
+  // and every output [g][cell] is written coalesced across threads
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
+    const double g0v = v.geo[cell], gxx = v.geo[v.ncell + cell], gxy = v.geo[2 * (int64_t)v.ncell + cell],
+                 gyy = v.geo[3 * (int64_t)v.ncell + cell];
+    for (int g = 0; g < v.G; ++g) {
+      const int64_t idx = (int64_t)g * v.ncell + cell;
+      const int g0 = g / L.gc * L.gc, gc = L.gc;   // [chunk][cell][6][gc], as the sweeps accumulate
+      const double *ac = a.acc + (int64_t)kOutputs * g0 * v.ncell + (int64_t)cell * kOutputs * gc + (g - g0);
+      const double B = a.B[idx];
+      a.out.E[idx] = (B * g0v + __ldg(ac + 0 * gc) * is) * inv_c;
+      a.out.Fx[idx] = __ldg(ac + 1 * gc) * is;
+      a.out.Fy[idx] = __ldg(ac + 2 * gc) * is;
+      a.out.Nxx[idx] = B * gxx + __ldg(ac + 3 * gc) * is;
+      a.out.Nxy[idx] = B * gxy + __ldg(ac + 4 * gc) * is;
+      a.out.Nyy[idx] = B * gyy + __ldg(ac + 5 * gc) * is;
+      a.Bref[idx] = B;   // the new deviations refer to this step's B
+    }
   }
 }
 
@@ -491,7 +496,7 @@ int grid_for(int64_t n, int block) {
 
 cudaError_t launch_prep(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
   const Layout L = layout_for(v, prec);
-  prep_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(v, a, L, prec == MOLC_FP32);
+  prep_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, L, prec == MOLC_FP32);
   return cudaGetLastError();
 }
 
@@ -523,7 +528,7 @@ cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_
 }
 
 cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
-  finalize_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(v, a, layout_for(v, prec));
+  finalize_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, layout_for(v, prec));
   return cudaGetLastError();
 }
 

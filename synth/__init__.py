@@ -323,6 +323,8 @@ WORKLOADS = {
     "fc64_g17_d128": Workload("fc64_g17_d128", 64, 64, 6.0, 17, 0.001, 100.0, 4, 32, 4, 10),
     # production size (roofline point): 512x512, 17 groups, 4 x 32 directions, spacing h/2, three fronts
     "fc512_g17_d128": Workload("fc512_g17_d128", 512, 512, 6.0, 17, 0.001, 100.0, 4, 32, 2, 1, n_fronts=3),
+    # profiling size of the production workload (same generators; 3.3 GB FP32 state, accumulators > L2)
+    "fc384_g17_d128": Workload("fc384_g17_d128", 384, 384, 6.0, 17, 0.001, 100.0, 4, 32, 2, 1, n_fronts=3),
     # refinement stress base grid: 128x128, 17 groups, 8 x 64 directions, cold start (spacing set per run)
     "fc128_g17_d512": Workload("fc128_g17_d512", 128, 128, 6.0, 17, 0.001, 100.0, 8, 64, 2, 50,
                                cold_start=True),

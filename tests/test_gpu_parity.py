@@ -122,6 +122,7 @@ VARIANTS = [
     dict(nx=4, ny=4, G=17, npol=8, naz=16, div=4),
     dict(nx=10, ny=10, G=2, npol=2, naz=20, div=1, thick=True),
     dict(nx=10, ny=10, G=2, npol=4, naz=8, div=2, thin=True),
+    dict(nx=3, ny=4, G=37, npol=2, naz=8, div=2),          # FP32: two group chunks, the last one partial
 ]
 
 
