@@ -149,6 +149,31 @@ molc_status molc_intensity_init(molc_plan *plan, molc_precision prec, void *I, c
 molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa, const double *B, double c,
                        double dt, void *I, const double *bnd, const molc_moments *out, molc_stream stream);
 
+/* Allocation-free variant of molc_sweep (the paper has no counterpart: it is an engineering entry point).
+ * Same arguments, semantics and results as molc_sweep, but the per-sweep workspace (the FP64 moment
+ * accumulators and, for MOLC_FP32, the cell tables) comes from one fixed 16 MiB array compiled into the
+ * library instead of from the plan.  It is meant for callers that must not allocate device memory, or must
+ * know all of it in advance, once they are running: an embedding whose device memory is fully handed to
+ * another allocator, or a time-stepping loop run under a fixed memory budget.  Neither this call nor its
+ * set-up calls cudaMalloc, cudaFree or any other allocating routine.
+ *  - Limit: the workspace is 48 bytes per (cell, group) for MOLC_FP64 and 68 bytes per (cell, group) for
+ *    MOLC_FP32 (groups padded to the plan's group chunk), each part rounded up to 256 bytes; a plan that needs
+ *    more than 16 MiB (e.g. more than ~350k cell-groups in FP64) is rejected with MOLC_ERR_INVALID_ARG and
+ *    nothing is launched.  molc_sweep has no such limit.
+ *  - Set-up: the first call on each device (with the plan's device current) looks up the array's device
+ *    address with cudaGetSymbolAddress, which also loads the library's kernels on that device if that has
+ *    not happened yet; later calls reuse the cached address.  Make that first call before any stream
+ *    capture.
+ *  - The accumulators must start at zero; every call clears them itself (cudaMemsetAsync on `stream`) before
+ *    its kernels run, so nothing needs to be zeroed by the caller.
+ *  - There is ONE array per device, shared by every plan and stream in the process: calls that can overlap in
+ *    time on the same device (different streams, or different host threads) race on it and give wrong
+ *    results.  Serialise them, e.g. issue them all on one stream.
+ *  - Sweep-kernel timing (molc_kernel_timing) does not record this call. */
+molc_status molc_sweep_static_scratch(molc_plan *plan, molc_precision prec, const double *kappa,
+                                      const double *B, double c, double dt, void *I, const double *bnd,
+                                      const molc_moments *out, molc_stream stream);
+
 /* Eddington factors of each cell and group, f = N / (c E) (Eq. 7 with the cell averages of Eq. 15):
  * fxx, fxy, fyy device [G][cell]; f_zz = 1 - f_xx - f_yy.  f_grey: device [3][cell] or NULL, the
  * E-weighted spectral average <f>_E = sum_g f_g E_g / sum_g E_g (Sec. 2, Eq. 8) of xx, xy, yy.

@@ -807,6 +807,63 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   return MOLC_OK;
 }
 
+molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const double *kappa, const double *B,
+                                      double c, double dt, void *I, const double *bnd, const molc_moments *out,
+                                      molc_stream stream) {
+  if (!p || !kappa || !B || !I || !bnd || !out)
+    return fail(MOLC_ERR_INVALID_ARG, "sweep_static_scratch: NULL argument");
+  if (!out->E || !out->Fx || !out->Fy || !out->Nxx || !out->Nxy || !out->Nyy)
+    return fail(MOLC_ERR_INVALID_ARG, "sweep_static_scratch: NULL moment array");
+  if (!finite_pos(c) || !finite_pos(dt))
+    return fail(MOLC_ERR_INVALID_ARG, "sweep_static_scratch: need c > 0 and dt > 0");
+  molc_status s = check_prec(p, prec, "sweep_static_scratch");
+  if (s) return s;
+  // workspace carved from the static array: accumulators [chunk][cell][6][gc] FP64 (must start at zero, cleared
+  // below on every call), then for FP32 the cell tables [chunk][cell][gc] (fully written by prep_kernel)
+  const Layout L = layout_for(p->view, prec);
+  const size_t rows = (size_t)L.n_chunks * L.gc * p->view.ncell;
+  auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t acc_bytes = up256(rows * kOutputs * sizeof(double));
+  const size_t cdat_bytes = prec == MOLC_FP32 ? up256(rows * sizeof(float4)) : 0;
+  const size_t cdB_bytes = prec == MOLC_FP32 ? up256(rows * sizeof(float)) : 0;
+  const size_t need = acc_bytes + cdat_bytes + cdB_bytes;
+  if (need > kStaticScratchBytes)
+    return fail(MOLC_ERR_INVALID_ARG,
+                "sweep_static_scratch: this plan needs %zu bytes of workspace (%d cells x %d groups), more than "
+                "the %zu-byte static scratch; use molc_sweep",
+                need, p->view.ncell, p->G, kStaticScratchBytes);
+  DeviceGuard dg(p->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  void *base = nullptr;
+  cudaError_t e = static_scratch_address(&base);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: scratch address");
+  char *b = (char *)base;
+  SweepArgs a{};
+  a.kappa = kappa;
+  a.B = B;
+  a.bnd = bnd;
+  a.c = c;
+  a.dt = dt;
+  a.I = I;
+  a.Bref = bref_of(p, prec, I);
+  a.scale = header_of(p, prec, I);
+  a.out = *out;
+  a.acc = (double *)b;
+  a.cdat = prec == MOLC_FP32 ? (float4 *)(b + acc_bytes) : nullptr;
+  a.cdB = prec == MOLC_FP32 ? (float *)(b + acc_bytes + cdat_bytes) : nullptr;
+  a.items = p->d_items32;
+  a.n_items = p->n_items32;
+  e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
+  e = launch_prep(p->view, prec, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: prep");
+  e = prec == MOLC_FP64 ? launch_sweep_fp64(p->view, a, st) : launch_sweep_fp32(p->view, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: sweep kernel");
+  e = launch_finalize(p->view, prec, a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: finalize");
+  return MOLC_OK;
+}
+
 molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, double *fxx, double *fxy,
                          double *fyy, double *f_grey, molc_stream stream) {
   if (!p || !m || !m->E || !m->Nxx || !m->Nxy || !m->Nyy || !fxx || !fxy || !fyy)

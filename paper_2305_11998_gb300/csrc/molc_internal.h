@@ -111,4 +111,10 @@ cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *
 cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const double *B, double *header,
                              cudaStream_t st);
 
+// Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+// Device address of that array on the current device.  The first call per device looks the symbol up (which
+// also loads the library's kernels on that device if nothing has yet); later calls return the cached address.
+cudaError_t static_scratch_address(void **ptr);
+
 }  // namespace molc

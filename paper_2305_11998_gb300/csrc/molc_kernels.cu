@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "molc_internal.h"
 
@@ -559,6 +560,34 @@ cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const doubl
   max_bits_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(B, (int64_t)v.G * v.ncell, mx);
   set_scale_kernel<<<1, 1, 0, st>>>(mx, header, prec == MOLC_FP32);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------------------
+// Static scratch of molc_sweep_static_scratch: the per-sweep workspace (moment accumulators, FP32 cell table)
+// in an array fixed at build time, reserved when the module is loaded on a device, so that entry point
+// allocates nothing.  The host name g_static_scratch is not a device address: its address on a device comes
+// from cudaGetSymbolAddress with that device current, looked up once per device and cached.
+// ---------------------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+cudaError_t static_scratch_address(void **ptr) {
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static void *cached[kMaxDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < kMaxDevices && cached[dev]) {
+    *ptr = cached[dev];
+    return cudaSuccess;
+  }
+  void *addr = nullptr;
+  e = cudaGetSymbolAddress(&addr, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDevices) cached[dev] = addr;
+  *ptr = addr;
+  return cudaSuccess;
 }
 
 }  // namespace molc

@@ -28,7 +28,7 @@ MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")
 EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "molc_intensity_count",
             "molc_intensity_bytes", "molc_intensity_init", "molc_sweep", "molc_closure", "molc_intensity_export",
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
-            "molc_device_status", "molc_last_error", "molc_destroy")
+            "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch")
 
 
 class MolcError(RuntimeError):
@@ -84,6 +84,8 @@ def load(build_if_needed: bool = True):
         "molc_intensity_bytes": (C.c_size_t, [vp, C.c_int]),
         "molc_intensity_init": (C.c_int, [vp, C.c_int, vp, vp, vp]),
         "molc_sweep": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp, C.POINTER(_Moments), vp]),
+        "molc_sweep_static_scratch": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp,
+                                                C.POINTER(_Moments), vp]),
         "molc_closure": (C.c_int, [vp, C.POINTER(_Moments), C.c_double, vp, vp, vp, vp, vp]),
         "molc_intensity_export": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "molc_intensity_import": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp, vp]),
@@ -226,6 +228,17 @@ class Plan:
         m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
         _check(self._lib.molc_sweep(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt), _ptr(I),
                                     _ptr(bnd), C.byref(m), _stream(stream)))
+        return out
+
+    def sweep_static_scratch(self, prec, kappa, B, c, dt, I, bnd, out=None, stream=None):
+        """molc_sweep_static_scratch: as sweep(), with the workspace taken from the library's fixed device array
+        (no device allocation by the library; plans up to its size limit only; calls that overlap in time on
+        one device race).  `out` is allocated here by torch when not given: pass it for a call that allocates
+        nothing at all."""
+        out = out if out is not None else self.new_moments(kappa.device)
+        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        _check(self._lib.molc_sweep_static_scratch(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt),
+                                                   _ptr(I), _ptr(bnd), C.byref(m), _stream(stream)))
         return out
 
     def closure(self, moments, c, grey=False, stream=None):
