@@ -224,7 +224,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    kern_ms, kern_n = P.kernel_time()
+    parts, kern_n = P.kernel_time_parts()
+    kern_ms = parts["sweep"]
     P.kernel_timing(False)
     clocks = sampler.stop() if sampler else None
     status = P.device_status()
@@ -236,14 +237,15 @@ def run_ours(args):
     value = ws * info.n_updates * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (the FP32 sweep): algorithmic bytes per launch / average launch time
-    per_update = 8.0   # the FP32 deviation state: 4 B read + 4 B written per update
     gc = info.fp32_groups_per_warp
     n_chunks = -(-G // gc)
-    extras = (16.0 * info.n_track_segments * n_chunks      # segment records, once per group chunk
-              + 20.0 * ncell * G                            # cell table {kappa~, r, B_hi, B_lo, dB}
-              + 48.0 * ncell * G)                           # FP64 accumulators written back
-    alg_bytes = per_update * info.n_updates + extras
-    kern_avg = kern_ms / max(kern_n, 1)
+    alg_bytes = (8.0 * info.n_updates                       # deviation state: 4 B read + 4 B written per update
+                 + 16.0 * info.n_track_segments * n_chunks  # segment records, once per group chunk
+                 + 20.0 * ncell * G)                        # cell table {kappa~, r, B_hi, B_lo, dB}, read once
+    # the cell-moment gather: the swept state read once more, the cell entry lists, B in, 6 moments + B_ref out
+    mom_bytes = (4.0 * info.n_updates + 16.0 * 2 * info.n_track_segments * n_chunks + (8.0 + 56.0) * ncell * G)
+    nk = max(kern_n, 1)
+    kern_avg = kern_ms / nk
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kern_avg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -251,6 +253,9 @@ def run_ours(args):
                             else SWEEP_FP32_DRAM_BYTES_PER_UPDATE * info.n_updates),
                 "kernel": "sweep_fp32_kernel", "kernel_ms": kern_avg,
                 "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    kernels = {"prep_ms": parts["prep"] / nk, "sweep_ms": kern_avg, "moments_ms": parts["moments"] / nk,
+               "moments_gbs": mom_bytes / (parts["moments"] / nk / 1e3) / 1e9 if parts["moments"] > 0 else None,
+               "moments_alg_bytes": mom_bytes}
 
     # end to end through the public API: pinned host inputs copied in, moments and factors copied out
     e2e = None
@@ -322,7 +327,7 @@ def run_ours(args):
                            "updates_per_step_per_gpu": info.n_updates,
                            "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
                            "step": "molc_sweep (FP32) + molc_closure"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 4 * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
         print(json.dumps(line), flush=True)
     P.close()

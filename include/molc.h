@@ -156,16 +156,17 @@ molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa
  * know all of it in advance, once they are running: an embedding whose device memory is fully handed to
  * another allocator, or a time-stepping loop run under a fixed memory budget.  Neither this call nor its
  * set-up calls cudaMalloc, cudaFree or any other allocating routine.
- *  - Limit: the workspace is 48 bytes per (cell, group) for MOLC_FP64 and 68 bytes per (cell, group) for
- *    MOLC_FP32 (groups padded to the plan's group chunk), each part rounded up to 256 bytes; a plan that needs
- *    more than 16 MiB (e.g. more than ~350k cell-groups in FP64) is rejected with MOLC_ERR_INVALID_ARG and
- *    nothing is launched.  molc_sweep has no such limit.
+ *  - Limit: the workspace is 48 bytes per (cell, group) for MOLC_FP64 (the accumulators) and 20 bytes per
+ *    (cell, group) for MOLC_FP32 (the cell tables; groups padded to the plan's group chunk), each part rounded
+ *    up to 256 bytes; a plan that needs more than 16 MiB (e.g. more than ~350k cell-groups in FP64, ~840k in
+ *    FP32) is rejected with MOLC_ERR_INVALID_ARG and nothing is launched.  molc_sweep has no such limit.
  *  - Set-up: the first call on each device (with the plan's device current) looks up the array's device
  *    address with cudaGetSymbolAddress, which also loads the library's kernels on that device if that has
  *    not happened yet; later calls reuse the cached address.  Make that first call before any stream
  *    capture.
- *  - The accumulators must start at zero; every call clears them itself (cudaMemsetAsync on `stream`) before
- *    its kernels run, so nothing needs to be zeroed by the caller.
+ *  - The FP64 accumulators must start at zero; every FP64 call clears them itself (cudaMemsetAsync on
+ *    `stream`) before its kernels run, so nothing needs to be zeroed by the caller.  The FP32 cell tables are
+ *    fully rewritten by every call.
  *  - There is ONE array per device, shared by every plan and stream in the process: calls that can overlap in
  *    time on the same device (different streams, or different host threads) race on it and give wrong
  *    results.  Serialise them, e.g. issue them all on one stream.
@@ -196,12 +197,15 @@ molc_status molc_intensity_import(molc_plan *plan, molc_precision prec, void *I,
 molc_status molc_tracks_export(const molc_plan *plan, int64_t *dir_ray_off, int64_t *ray_seg_off, double *width,
                                int *entry, int *cell, double *len, double *area);
 
-/* Kernel timing for benchmarks: while enabled, every molc_sweep / molc_batch_sweep records a CUDA event pair
- * around its sweep kernel (at most 4096 launches are kept).  molc_kernel_time synchronises with the last
- * recorded event, returns the summed elapsed milliseconds and the number of timed launches, and clears the
- * record.  Disabled by default; enabling creates the events (no device memory allocation). */
+/* Kernel timing for benchmarks: while enabled, every molc_sweep records CUDA events around its three kernels
+ * (input preparation, the sweep itself, the cell moments; at most 4096 calls are kept).  molc_kernel_time
+ * synchronises with the last recorded event, returns the summed elapsed milliseconds of the sweep kernel and
+ * the number of timed calls, and clears the record; molc_kernel_time_parts does the same with
+ * parts_ms[3] = {preparation, sweep, moments}.  Disabled by default; enabling creates the events (no device
+ * memory allocation). */
 molc_status molc_kernel_timing(molc_plan *plan, int enable);
 molc_status molc_kernel_time(molc_plan *plan, double *total_ms, int *launches);
+molc_status molc_kernel_time_parts(molc_plan *plan, double *parts_ms, int *launches);
 
 /* Read and clear the plan's device status word (synchronises with the device).  *code = MOLC_OK or the first
  * error the kernels recorded. */

@@ -79,7 +79,7 @@ struct molc_plan {
   std::vector<int64_t> dir_seg_off;
   // device
   TrackDev *d_tracks = nullptr;
-  int4 *d_seg32 = nullptr;
+  int2 *d_seg32 = nullptr;
   int *d_seg_cell = nullptr;
   double *d_seg_len = nullptr, *d_seg_afrac = nullptr;
   PairDev *d_pairs = nullptr;
@@ -92,6 +92,8 @@ struct molc_plan {
   double *d_acc = nullptr;
   int2 *d_items32 = nullptr;
   int64_t n_items32 = 0;
+  int64_t *d_cell_off = nullptr;
+  int4 *d_gent = nullptr;
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
@@ -297,7 +299,8 @@ void free_events(molc_plan *p) {
 void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
-                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32};
+                  p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
+                  p->d_cell_off, p->d_gent};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -615,23 +618,18 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   p->dir_seg_off.assign(n + 1, 0);
   for (int m = 0; m < n; ++m) p->dir_seg_off[m + 1] = p->dir_seg_off[m] + pair_nseg[p->dir_pair[m]];
 
-  std::vector<int4> seg32(S);
+  std::vector<int2> seg32(S);   // FP32 sweep records {cell, l (f32 bits)}
   for (int64_t q = 0; q < S; ++q) {
-    float lf = (float)p->seg_len[q], af = (float)p->seg_afrac[q];
-    int4 r;
+    float lf = (float)p->seg_len[q];
+    int2 r;
     r.x = p->seg_cell[q];
     std::memcpy(&r.y, &lf, 4);
-    std::memcpy(&r.z, &af, 4);
-    r.w = 0;
     seg32[q] = r;
   }
 
   // ---- FP32 work items: one thread per (track, sense, group), ordered chunk-major, then by decreasing track
-  // length, then track, sense and group.  Groups are tiled in chunks of up to 32: the threads of one (track,
-  // sense) are consecutive, so the more groups a chunk holds, the fewer distinct cells a warp's FP64 reductions
-  // touch and the fewer L2 requests they cost.  (Measured on GB300 at 512^2 x 17 groups: one 17-group chunk
-  // is 1.5x faster than 4-group chunks sized to keep the accumulators L2-resident; the reduction request rate,
-  // not L2 capacity, bounds this kernel.)
+  // length, then track, sense and group.  Groups are tiled in chunks of up to 32; the threads of one (track,
+  // sense) are consecutive, so a warp's record and cell-table loads are shared by up to 32 lanes.
   const int gc32 = std::min(p->G, 32);
   const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
   std::vector<int64_t> order(T);
@@ -650,7 +648,47 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         for (int gi = 0; gi < gcount; ++gi) items.push_back(make_int2((int)k, sense | (gi << 1) | (ch << 16)));
   }
   p->n_items32 = (int64_t)items.size();
-  p->acc_elems = (size_t)ncell * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
+  p->acc_elems = (size_t)ncell * kOutputs * p->G;   // FP64 sweep accumulators
+
+  // ---- FP32 cell moments are gathered per cell from the swept state: for every cell, one entry per (track,
+  // sense) segment crossing it, {state row, A/V (f32 bits), 2 pair + sense, 0}, rows as the sweep writes them
+  // (track t, sense +: row 2 seg_off + j for its j-th segment; sense -: row 2 seg_off + nseg + (nseg - 1 - j)).
+  // Entries of a cell are in track order, so the gathered sums are deterministic.
+  if (2 * S > (int64_t)0x7fffffff) {
+    delete p;
+    return fail(MOLC_ERR_INVALID_ARG, "create: too many segments for the FP32 state rows");
+  }
+  // Each cell's list is padded to a multiple of kGatherPad entries with zero-area copies of its last entry.
+  if ((size_t)p->n_pairs * (3 * p->n_polar + 2) * sizeof(float) > kMaxGatherSmem) {
+    delete p;
+    return fail(MOLC_ERR_INVALID_ARG, "create: too many azimuth pairs for the FP32 moment kernel");
+  }
+  std::vector<int64_t> cell_off(nch32 ? (size_t)ncell + 1 : 0, 0);
+  std::vector<int4> gent;
+  if (nch32) {
+    std::vector<int64_t> cnt(ncell, 0);
+    for (int64_t q = 0; q < S; ++q) cnt[p->seg_cell[q]] += 2;
+    for (int i = 0; i < ncell; ++i) cell_off[i + 1] = cell_off[i] + (cnt[i] + kGatherPad - 1) / kGatherPad * kGatherPad;
+    gent.assign((size_t)cell_off[ncell], make_int4(0, 0, 0, 0));
+    std::vector<int64_t> pos(cell_off.begin(), cell_off.end() - 1);
+    for (int64_t k = 0; k < T; ++k) {
+      const TrackDev &t = td[k];
+      for (int j = 0; j < t.nseg; ++j) {
+        const int64_t q = t.seg_off + j;
+        const float af = (float)p->seg_afrac[q];
+        int afb;
+        std::memcpy(&afb, &af, 4);
+        const int c = p->seg_cell[q];
+        gent[pos[c]++] = make_int4((int)(2 * t.seg_off + j), afb, 2 * t.pair, 0);
+        gent[pos[c]++] = make_int4((int)(2 * t.seg_off + t.nseg + (t.nseg - 1 - j)), afb, 2 * t.pair + 1, 0);
+      }
+    }
+    for (int i = 0; i < ncell; ++i)
+      for (int64_t e = pos[i]; e < cell_off[i + 1]; ++e) {
+        gent[e] = gent[pos[i] - 1];
+        gent[e].y = 0;   // zero area
+      }
+  }
 
   PlanView &v = p->view;
   v.nx = g.nx;
@@ -681,6 +719,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_geo, geo.data(), geo.size(), "geometric moments")
   UP(d_dir_seg_off, p->dir_seg_off.data(), p->dir_seg_off.size(), "direction offsets")
   UP(d_status, (const int *)nullptr, 1, "status")
+  UP(d_cell_off, cell_off.data(), cell_off.size(), "cell entry offsets")
+  UP(d_gent, gent.data(), gent.size(), "cell entries")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
@@ -705,6 +745,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.geo = p->d_geo;
   v.dir_seg_off = p->d_dir_seg_off;
   v.status = p->d_status;
+  v.cell_off = p->d_cell_off;
+  v.gent = p->d_gent;
   *out = p;
   return MOLC_OK;
 }
@@ -782,6 +824,8 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.bnd = bnd;
   a.c = c;
   a.dt = dt;
+  a.inv_c = 1.0 / c;
+  a.inv_cdt = 1.0 / (c * dt);
   a.I = I;
   a.Bref = bref_of(p, prec, I);
   a.scale = header_of(p, prec, I);
@@ -791,19 +835,26 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.acc = p->d_acc;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
-  const Layout L = layout_for(p->view, prec);
-  cudaError_t e =
-      cudaMemsetAsync(p->d_acc, 0, (size_t)L.n_chunks * L.gc * p->view.ncell * kOutputs * sizeof(double), st);
-  if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
+  cudaError_t e = cudaSuccess;
+  if (prec == MOLC_FP64) {   // the FP32 path gathers its moments and has no accumulators
+    e = cudaMemsetAsync(p->d_acc, 0, (size_t)p->G * p->view.ncell * kOutputs * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
+  }
+  const bool timed = p->timing && p->n_timed < kMaxTimed;
+  cudaEvent_t *ev = timed ? &p->ev[4 * (size_t)p->n_timed] : nullptr;
+  if (timed) cudaEventRecord(ev[0], st);
   e = launch_prep(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep: prep");
-  const bool timed = p->timing && p->n_timed < kMaxTimed;
-  if (timed) cudaEventRecord(p->ev[2 * p->n_timed], st);
+  if (timed) cudaEventRecord(ev[1], st);
   e = prec == MOLC_FP64 ? launch_sweep_fp64(p->view, a, st) : launch_sweep_fp32(p->view, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep: sweep kernel");
-  if (timed) cudaEventRecord(p->ev[2 * p->n_timed++ + 1], st);
+  if (timed) cudaEventRecord(ev[2], st);
   e = launch_finalize(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep: finalize");
+  if (timed) {
+    cudaEventRecord(ev[3], st);
+    ++p->n_timed;
+  }
   return MOLC_OK;
 }
 
@@ -818,12 +869,12 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
     return fail(MOLC_ERR_INVALID_ARG, "sweep_static_scratch: need c > 0 and dt > 0");
   molc_status s = check_prec(p, prec, "sweep_static_scratch");
   if (s) return s;
-  // workspace carved from the static array: accumulators [chunk][cell][6][gc] FP64 (must start at zero, cleared
-  // below on every call), then for FP32 the cell tables [chunk][cell][gc] (fully written by prep_kernel)
+  // workspace carved from the static array: FP64, the accumulators [cell][6][G] (must start at zero, cleared
+  // below on every call); FP32, the cell tables [chunk][cell][gc] (fully written by prep_kernel)
   const Layout L = layout_for(p->view, prec);
   const size_t rows = (size_t)L.n_chunks * L.gc * p->view.ncell;
   auto up256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t acc_bytes = up256(rows * kOutputs * sizeof(double));
+  const size_t acc_bytes = prec == MOLC_FP64 ? up256(rows * kOutputs * sizeof(double)) : 0;
   const size_t cdat_bytes = prec == MOLC_FP32 ? up256(rows * sizeof(float4)) : 0;
   const size_t cdB_bytes = prec == MOLC_FP32 ? up256(rows * sizeof(float)) : 0;
   const size_t need = acc_bytes + cdat_bytes + cdB_bytes;
@@ -844,17 +895,21 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
   a.bnd = bnd;
   a.c = c;
   a.dt = dt;
+  a.inv_c = 1.0 / c;
+  a.inv_cdt = 1.0 / (c * dt);
   a.I = I;
   a.Bref = bref_of(p, prec, I);
   a.scale = header_of(p, prec, I);
   a.out = *out;
-  a.acc = (double *)b;
-  a.cdat = prec == MOLC_FP32 ? (float4 *)(b + acc_bytes) : nullptr;
-  a.cdB = prec == MOLC_FP32 ? (float *)(b + acc_bytes + cdat_bytes) : nullptr;
+  a.acc = prec == MOLC_FP64 ? (double *)b : nullptr;
+  a.cdat = prec == MOLC_FP32 ? (float4 *)b : nullptr;
+  a.cdB = prec == MOLC_FP32 ? (float *)(b + cdat_bytes) : nullptr;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
-  e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
-  if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
+  if (prec == MOLC_FP64) {
+    e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
+  }
   e = launch_prep(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: prep");
   e = prec == MOLC_FP64 ? launch_sweep_fp64(p->view, a, st) : launch_sweep_fp32(p->view, a, st);
@@ -942,7 +997,7 @@ molc_status molc_kernel_timing(molc_plan *p, int enable) {
   if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "kernel_timing: the plan was created with MOLC_HOST_ONLY");
   DeviceGuard dg(p->device);
   if (enable && p->ev.empty()) {
-    p->ev.resize(2 * kMaxTimed);
+    p->ev.resize(4 * (size_t)kMaxTimed);
     for (auto &e : p->ev) {
       cudaError_t r = cudaEventCreate(&e);
       if (r != cudaSuccess) {
@@ -956,24 +1011,33 @@ molc_status molc_kernel_timing(molc_plan *p, int enable) {
   return MOLC_OK;
 }
 
-molc_status molc_kernel_time(molc_plan *p, double *total_ms, int *launches) {
-  if (!p || !total_ms || !launches) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: NULL argument");
+molc_status molc_kernel_time_parts(molc_plan *p, double *parts_ms, int *launches) {
+  if (!p || !parts_ms || !launches) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: NULL argument");
   DeviceGuard dg(p->device);
-  double tot = 0;
+  double tot[3] = {0, 0, 0};
   if (p->n_timed > 0) {
-    cudaError_t r = cudaEventSynchronize(p->ev[2 * p->n_timed - 1]);
+    cudaError_t r = cudaEventSynchronize(p->ev[4 * (size_t)p->n_timed - 1]);
     if (r != cudaSuccess) return cuda_fail(r, "kernel_time");
-    for (int i = 0; i < p->n_timed; ++i) {
-      float ms = 0;
-      r = cudaEventElapsedTime(&ms, p->ev[2 * i], p->ev[2 * i + 1]);
-      if (r != cudaSuccess) return cuda_fail(r, "kernel_time");
-      tot += ms;
-    }
+    for (int i = 0; i < p->n_timed; ++i)
+      for (int k = 0; k < 3; ++k) {
+        float ms = 0;
+        r = cudaEventElapsedTime(&ms, p->ev[4 * (size_t)i + k], p->ev[4 * (size_t)i + k + 1]);
+        if (r != cudaSuccess) return cuda_fail(r, "kernel_time");
+        tot[k] += ms;
+      }
   }
-  *total_ms = tot;
+  for (int k = 0; k < 3; ++k) parts_ms[k] = tot[k];
   *launches = p->n_timed;
   p->n_timed = 0;
   return MOLC_OK;
+}
+
+molc_status molc_kernel_time(molc_plan *p, double *total_ms, int *launches) {
+  if (!total_ms) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: NULL argument");
+  double parts[3];
+  molc_status s = molc_kernel_time_parts(p, parts, launches);
+  if (s == MOLC_OK) *total_ms = parts[1];
+  return s;
 }
 
 molc_status molc_device_status(molc_plan *p, int *code) {

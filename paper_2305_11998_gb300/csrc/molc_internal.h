@@ -10,6 +10,8 @@ namespace molc {
 
 constexpr int kMaxPolarFP32 = 8;     // FP32 sweep: polar cosines per azimuth handled by one half-warp
 constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators per (cell, group)
+constexpr int kGatherPad = 4;        // FP32 moments: each cell's entry list is padded to a multiple of this
+constexpr size_t kMaxGatherSmem = 200 * 1024;  // FP32 moments: per-pair coefficient table in shared memory
 
 // Device status bits (the first one set wins in molc_device_status).
 constexpr int kStatusNonfinite = 1;
@@ -46,7 +48,7 @@ struct PlanView {
   int nx, ny, ncell, G, n_pairs, n_polar;
   int64_t n_tracks, n_track_segments;
   const TrackDev *tracks;
-  const int4 *seg32;            // {cell, len (f32 bits), a/V (f32 bits), 0}
+  const int2 *seg32;            // FP32 sweep: {cell, len (f32 bits)} per track segment
   const int *seg_cell;          // FP64 path
   const double *seg_len;
   const double *seg_afrac;      // A / V (area fraction of the cell, after renormalisation)
@@ -55,7 +57,9 @@ struct PlanView {
   const double *geo;            // [4][cell]: sum_m omega sum_{C(i,m)} a times 1, Ox^2, OxOy, Oy^2
   const int64_t *dir_seg_off;   // canonical segment offset of each direction
   int *status;
-  int gc32;                     // FP32 sweep: groups per chunk (keeps a chunk's atomics L2-resident)
+  int gc32;                     // FP32 sweep: groups per chunk
+  const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into gent
+  const int4 *gent;             // FP32 moments: per cell, {state row, A/V f32 bits, 2 pair + sense, 0}
 };
 
 // Layout of the opaque intensity state: groups are tiled in chunks of `gc` groups; within a chunk, rows of
@@ -86,13 +90,14 @@ constexpr size_t kHeaderBytes = 256;
 struct SweepArgs {
   const double *kappa, *B, *bnd;
   double c, dt;
+  double inv_c, inv_cdt;  // 1/c and 1/(c dt), formed on the host
   void *I;            // deviations delta = Ibar - B_ref, [chunk][row][g_local][p]
   double *Bref;       // [G][cell] Planck intensity the deviations refer to (inside the state)
   const double *scale;  // state header: [0] = scale of the stored deviations, [1] = 1/scale
   molc_moments out;
   float4 *cdat;       // FP32: [chunk][cell][gc] {kappa~, 1/(c dt kappa~), B_hi, B_lo}
   float *cdB;         // FP32: [chunk][cell][gc] (B_ref - B) / (c dt kappa~)
-  double *acc;        // [chunk][cell][6][gc] FP64 accumulators
+  double *acc;        // FP64 path: [cell][6][G] FP64 accumulators
   const int2 *items;  // FP32: one per thread, {track, sense | g_local << 1 | chunk << 16}; chunk-major,
                       // longest track first, then sense, then group
   int64_t n_items;

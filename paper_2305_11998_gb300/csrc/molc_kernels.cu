@@ -15,6 +15,7 @@
 // thick cells, where |F| can be ~1e-8 c E.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -45,37 +46,58 @@ __device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int
 // prep: input checks; FP32 path also tabulates per (chunk, cell, group) {kappa~, 1/(c dt kappa~), B_hi, B_lo}
 // with B = B_hi + B_lo split so that B differences between neighbouring cells keep ~48 bits.
 // ---------------------------------------------------------------------------------------------------------
-__global__ void prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
-  const double inv_cdt = 1.0 / (a.c * a.dt);
+constexpr int kPrepCells = 32;   // cells per tile of prep_kernel
+
+// Tiles of kPrepCells cells x the groups of one chunk (blockIdx.y): [g][cell] inputs are read along cells, the
+// [chunk][cell][gc] tables are staged in shared memory and written out contiguously.
+__global__ void __launch_bounds__(128) prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
+  __shared__ float4 t4[kPrepCells * 32];
+  __shared__ float t1[kPrepCells * 32];
+  const float inv_cdt_f = (float)a.inv_cdt;
   const double sc = a.scale[0];
+  const int g0 = blockIdx.y * L.gc;
+  const int gcount = min(L.gc, v.G - g0);
   bool bad = false, range = false;
-  // one thread per cell, looping over groups: reads [g][cell] coalesced across threads, writes the cell's
-  // [cell][gc] table entries contiguously
-  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
-    for (int g = 0; g < v.G; ++g) {
-      const int64_t idx = (int64_t)g * v.ncell + cell;
+  const int n_tiles = (v.ncell + kPrepCells - 1) / kPrepCells;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int c0 = tile * kPrepCells;
+    const int nc = min(kPrepCells, v.ncell - c0);
+    for (int k = threadIdx.x; k < kPrepCells * gcount; k += blockDim.x) {
+      const int gl = k / kPrepCells, c = k - gl * kPrepCells;
+      if (c >= nc) continue;
+      const int64_t idx = (int64_t)(g0 + gl) * v.ncell + c0 + c;
       const double kap = a.kappa[idx], B = a.B[idx];
       bad |= bad_input(kap) | bad_input(B);
       if (fp32) {
-        const double kt = kap + inv_cdt;
-        const double r = inv_cdt / kt;
+        // FP64 only where a difference or a split needs it (the FP64 pipe is narrow): kappa~ and
+        // 1/(c dt kappa~) are rounded to FP32 anyway and are formed in FP32
+        const float kt = (float)(kap + a.inv_cdt);
+        const float r = __fdiv_rn(inv_cdt_f, kt);
         const double Bs = B * sc;
         range |= !(Bs < kScaledMax);
         const float bhi = (float)Bs;
         const float blo = (float)(Bs - (double)bhi);
-        // [chunk][cell][gc] with the chunk's stride gc also in a partial last chunk (as the sweep reads it)
-        const int g0 = g / L.gc * L.gc;
-        const int64_t o = (int64_t)g0 * v.ncell + (int64_t)cell * L.gc + (g - g0);
-        a.cdat[o] = make_float4((float)kt, (float)r, bhi, blo);
-        a.cdB[o] = (float)((a.Bref[idx] - B) * sc * r);
+        t4[c * gcount + gl] = make_float4(kt, r, bhi, blo);
+        t1[c * gcount + gl] = (float)((a.Bref[idx] - B) * sc) * r;
       }
     }
+    if (fp32) {
+      __syncthreads();
+      // [chunk][cell][gc]: the chunk's stride is gc also in a partial last chunk (as the sweep reads it)
+      const int64_t o = (int64_t)g0 * v.ncell + (int64_t)c0 * L.gc;
+      for (int k = threadIdx.x; k < nc * gcount; k += blockDim.x) {
+        const int c = k / gcount, gl = k - c * gcount;
+        a.cdat[o + (int64_t)c * L.gc + gl] = t4[k];
+        a.cdB[o + (int64_t)c * L.gc + gl] = t1[k];
+      }
+      __syncthreads();
+    }
   }
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 4 * (int64_t)v.G;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    bad |= bad_input(a.bnd[i]);
-    range |= fp32 && !(a.bnd[i] * sc < kScaledMax);
-  }
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int i = threadIdx.x; i < 4 * v.G; i += blockDim.x) {
+      bad |= bad_input(a.bnd[i]);
+      range |= fp32 && !(a.bnd[i] * sc < kScaledMax);
+    }
   if (bad) atomicOr(v.status, kStatusNonfinite);
   if (range && !bad) atomicOr(v.status, kStatusRange);
 }
@@ -148,10 +170,10 @@ constexpr int kSweepBlock = 128;
 //   tau < 1/2:  E1 = h sinh(tau/2) / (tau/2), the even Taylor series in y = tau^2/4 to y^3 (truncation
 //               < 5e-11 relative), free of cancellation;
 //   tau >= 1/2: E1 = (1 - e^-tau) / tau (1 - e^-tau > 0.39, no cancellation).
-// e^-tau itself from ex2.approx.  inv_tau is 1/tau.
+// e^-tau = h^2.  inv_tau is 1/tau.
 __device__ __forceinline__ void attenuation(float tau, float inv_tau, float &E1, float &ex) {
   const float h = __expf(-0.5f * tau);
-  ex = __expf(-tau);
+  ex = h * h;
   const float y = 0.25f * tau * tau;
   float p = fmaf(y, 1.f / 5040.f, 1.f / 120.f);
   p = fmaf(p, y, 1.f / 6.f);
@@ -192,11 +214,6 @@ __device__ __forceinline__ float4 ld_table4(const float4 *p, unsigned long long 
 __device__ __forceinline__ float ld_table1(const float *p, unsigned long long pol) {
   float v;
   asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ int4 ld_record(const int4 *p) {
-  int4 v;
-  asm("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
   return v;
 }
 __device__ __forceinline__ void red_f64(double *p, double v, unsigned long long pol) {
@@ -252,9 +269,70 @@ __device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsign
   }
 }
 
+// Asynchronous copies (cp.async, sm_80+) of NP consecutive FP32 deviations from global to shared memory:
+// 16-byte pieces where NP * 4 bytes allow, else 8- or 4-byte pieces (the thread's deviations start at a multiple
+// of NP * 4 bytes of a 256-byte aligned state).
+template <int NP>
+__device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src, unsigned long long pol) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4)
+      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
+  } else if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2)
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void copy16_async(void *dst_smem, const void *src, unsigned long long pol) {
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst_smem)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ void copy4_async(void *dst_smem, const void *src, unsigned long long pol) {
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(dst_smem)),
+               "l"(src), "l"(pol)
+               : "memory");
+}
+__device__ __forceinline__ int2 ld_record(const int2 *p) {
+  int2 v;
+  asm("ld.global.nc.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+// Software pipeline of the FP32 sweep, per thread, in rings of kSteps slots (the step loop is unrolled by kSteps
+// so that every slot index is a constant): at step s the thread
+//   - issues asynchronous copies of its previous-step deviations for step s+3 and of the cell table entry of
+//     step s+2 (whose record arrived two steps earlier) into shared memory, as one cp.async group,
+//   - waits until the groups holding step s's deviations and table entry have landed,
+//   - computes step s and stores its new deviations to global memory,
+//   - loads the record of step s+4 into a register.
+constexpr int kSteps = 4;
+
 template <int NP>
 __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
-  const int64_t item = (int64_t)blockIdx.x * kSweepBlock + threadIdx.x;
+  __shared__ __align__(16) float sdev[kSteps][kSweepBlock * NP];
+  __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
+  __shared__ __align__(16) float sdB[kSteps][kSweepBlock];
+  const int tid = threadIdx.x;
+  const int64_t item = (int64_t)blockIdx.x * kSweepBlock + tid;
   const bool live = item < a.n_items;
   const int2 it = live ? a.items[item] : make_int2(0, 0);
   const TrackDev tr = v.tracks[it.x];
@@ -272,105 +350,204 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
 
   const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
   float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W + gi * NP;
-  const int4 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
+  const int2 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
   const int rstep = sense ? -1 : 1;
   const int64_t cbase = (int64_t)ch * v.ncell * L.gc + gi;
   const float4 *cd = a.cdat + cbase;
   const float *cdB = a.cdB + cbase;
-  double *acc = a.acc + (int64_t)ch * v.ncell * kOutputs * L.gc + gi;
 
-  float inv_sinz[NP], sinz[NP], w0[NP];
+  float inv_sinz[NP], sinz[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const PolarDev pd = v.polar[tr.pair * NP + p];
     inv_sinz[p] = pd.inv_sinzf;
     sinz[p] = pd.sinzf;
-    w0[p] = pd.wf;
   }
-  const PairDev pr = v.pairs[tr.pair];
-  const float sg = sense ? -1.f : 1.f;
-  const float fx = sg * pr.cf, fy = sg * pr.sf, fxx = pr.cf * pr.cf, fxy = pr.cf * pr.sf, fyy = pr.sf * pr.sf;
   // entering intensity (scaled), split like B so that I_in - B keeps the precision of the difference
   const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
 
-  // software pipeline: the record of step s+1 and the cell data and deviations of step s are in flight
-  // while step s-1 is computed
-  int4 r_cur = make_int4(0, 0, 0, 0), r_next = make_int4(0, 0, 0, 0);
-  float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
-  float dB = 0.f;
-  float dv[NP];
+  // prologue: records of steps 0..3; groups 0, 1, 2 = {deviations 0, table 0}, {deviations 1, table 1},
+  // {deviations 2}
+  int2 recs[kSteps];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) dv[p] = 0.f;
-  if (nseg > 0) {
-    r_cur = ld_record(rec);
-    q = ld_table4(cd + (int64_t)r_cur.x * L.gc, pol_keep);
-    dB = ld_table1(cdB + (int64_t)r_cur.x * L.gc, pol_keep);
-    load_dev<NP>(I, dv, pol_stream);
-    if (nseg > 1) r_next = ld_record(rec + rstep);
+  for (int k = 0; k < kSteps; ++k) recs[k] = k < nseg ? ld_record(rec + k * rstep) : make_int2(0, 0);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (k < nseg) {
+      copy_dev_async<NP>(&sdev[k][tid * NP], I + (int64_t)k * W, pol_stream);
+      if (k < 2) {
+        copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc, pol_keep);
+        copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc, pol_keep);
+      }
+    }
+    cp_async_commit();
   }
   float psi[NP];
-  float bhi_prev = in_hi, blo_prev = in_lo;   // the boundary acts as the "previous cell" of step 0
 #pragma unroll
   for (int p = 0; p < NP; ++p) psi[p] = 0.f;
-  for (int s = 0; s < nmax; ++s) {
-    if (s < nseg) {
-      // prefetch step s+1
-      float4 qn = q;
-      float dBn = dB;
-      float dvn[NP];
-      int4 rnn = r_next;
-      if (s + 1 < nseg) {
-        qn = ld_table4(cd + (int64_t)r_next.x * L.gc, pol_keep);
-        dBn = ld_table1(cdB + (int64_t)r_next.x * L.gc, pol_keep);
-        load_dev<NP>(I + W, dvn, pol_stream);
-        if (s + 2 < nseg) rnn = ld_record(rec + (s + 2) * rstep);
+  float bhi_prev = in_hi, blo_prev = in_lo;   // the boundary acts as the "previous cell" of step 0
+  for (int s0 = 0; s0 < nmax; s0 += kSteps) {
+#pragma unroll
+    for (int u = 0; u < kSteps; ++u) {
+      const int s = s0 + u;
+      if (s < nseg) {
+        // group s+3: deviations of step s+3, table entry of step s+2
+        if (s + 3 < nseg) copy_dev_async<NP>(&sdev[(u + 3) % kSteps][tid * NP], I + (int64_t)3 * W, pol_stream);
+        if (s + 2 < nseg) {
+          const int c2 = recs[(u + 2) % kSteps].x;
+          copy16_async(&stab[(u + 2) % kSteps][tid], cd + (int64_t)c2 * L.gc, pol_keep);
+          copy4_async(&sdB[(u + 2) % kSteps][tid], cdB + (int64_t)c2 * L.gc, pol_keep);
+        }
+        cp_async_commit();
+        cp_async_wait<2>();   // groups up to s+1 (deviations of step s, table entry of step s) have landed
+        float dv[NP];
+        if constexpr (NP % 4 == 0) {
+#pragma unroll
+          for (int p = 0; p < NP; p += 4) {
+            const float4 t4 = *reinterpret_cast<const float4 *>(&sdev[u][tid * NP + p]);
+            dv[p] = t4.x;
+            dv[p + 1] = t4.y;
+            dv[p + 2] = t4.z;
+            dv[p + 3] = t4.w;
+          }
+        } else {
+#pragma unroll
+          for (int p = 0; p < NP; ++p) dv[p] = sdev[u][tid * NP + p];
+        }
+        const float4 q = stab[u][tid];
+        const float dB = sdB[u][tid];
+        // step s
+        const float len = __int_as_float(recs[u].y);
+        const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
+        const float kl = q.x * len;
+        const float rkl = rcp_approx(kl);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          psi[p] += jump;
+          float E1, ex;
+          attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
+          const float d = fmaf(dv[p], q.y, dB);
+          const float x = psi[p] - d;
+          dv[p] = fmaf(x, E1, d);
+          psi[p] = fmaf(x, ex, d);
+        }
+        store_dev<NP>(I, dv, pol_stream);
+        bhi_prev = q.z;
+        blo_prev = q.w;
+        I += W;
+        if (s + kSteps < nseg) recs[u] = ld_record(rec + (s + kSteps) * rstep);
       }
-      // step s
-      const int cell = r_cur.x;
-      const float len = __int_as_float(r_cur.y), af = __int_as_float(r_cur.z);
-      const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
-      const float kl = q.x * len;
-      const float rkl = rcp_approx(kl);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+// FP32 path, cell moments: one thread per (chunk, cell, group), consecutive groups of a cell in consecutive
+// lanes.  The thread sums, over the (track, sense) segments crossing its cell, the swept deviations of its group
+// (NP contiguous values per segment; the lanes of a cell read one contiguous block) weighted by
+// omega (A/V) (1, Omega, Omega Omega).  A cell's entries come grouped by azimuth pair: within a pair the
+// polar folds S0 = sum_p w_p dev_p, S1 = sum_p w_p sin(zeta_p) dev_p (signed by the sense),
+// S2 = sum_p w_p sin^2(zeta_p) dev_p are summed in FP32 (a few same-pair segments); across pairs the six sums
+// are carried as unevaluated pairs of FP32 words (hi + lo, TwoSum: a 48-bit significand), then assembled in FP64:
+//   E = (B geo0 + D)/c, F = D_F, N_ab = B geo_ab + D_ab, and B_ref := B.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+// Entries are taken kGatherBatch at a time so that their state loads are in flight together (each cell's entry
+// list is padded to a multiple of kGatherBatch with zero-area entries of its last pair).
+constexpr int kGatherBatch = 4;
+
+template <int NP>
+__global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+  extern __shared__ float coef[];   // [pair][3][NP] {w, w sin, w sin^2}, then [pair][2] {cos, sin}
+  float *csn = coef + 3 * NP * v.n_pairs;
+  for (int i = threadIdx.x; i < v.n_pairs * NP; i += blockDim.x) {
+    const int pr = i / NP, p = i - pr * NP;
+    const float w = v.polar[i].wf, sz = v.polar[i].sinzf;
+    coef[(pr * 3 + 0) * NP + p] = w;
+    coef[(pr * 3 + 1) * NP + p] = w * sz;
+    coef[(pr * 3 + 2) * NP + p] = (w * sz) * sz;
+  }
+  for (int i = threadIdx.x; i < v.n_pairs; i += blockDim.x) {
+    csn[2 * i] = v.pairs[i].cf;
+    csn[2 * i + 1] = v.pairs[i].sf;
+  }
+  __syncthreads();
+  const int ch = blockIdx.y;
+  const int g0 = ch * L.gc;
+  const int gcount = min(L.gc, v.G - g0);
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)v.ncell * gcount) return;
+  const int cell = (int)(t / gcount), gi = (int)(t - (int64_t)cell * gcount);
+  const int g = g0 + gi;
+  const int W = gcount * NP;
+  const float *I = (const float *)a.I + L.rows * (int64_t)NP * g0 + gi * NP;
+  const unsigned long long pol_stream = policy_evict_first();
+  float hi[kOutputs], lo[kOutputs];
+#pragma unroll
+  for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
+  const int64_t e0 = v.cell_off[cell], e1 = v.cell_off[cell + 1];
+  int cur = e1 > e0 ? (__ldg(&v.gent[e0].z) >> 1) : 0;
+  float P0 = 0.f, P1 = 0.f, P2 = 0.f;
+  auto flush = [&]() {
+    const float cf = csn[2 * cur], sf = csn[2 * cur + 1];
+    two_sum_add(hi[0], lo[0], P0);
+    two_sum_add(hi[1], lo[1], cf * P1);
+    two_sum_add(hi[2], lo[2], sf * P1);
+    two_sum_add(hi[3], lo[3], (cf * cf) * P2);
+    two_sum_add(hi[4], lo[4], (cf * sf) * P2);
+    two_sum_add(hi[5], lo[5], (sf * sf) * P2);
+  };
+  for (int64_t e = e0; e < e1; e += kGatherBatch) {
+    int4 en[kGatherBatch];
+#pragma unroll
+    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(v.gent + e + b);
+    float dv[kGatherBatch][NP];
+#pragma unroll
+    for (int b = 0; b < kGatherBatch; ++b) load_dev<NP>(I + (int64_t)en[b].x * W, dv[b], pol_stream);
+#pragma unroll
+    for (int b = 0; b < kGatherBatch; ++b) {
+      const int pr = en[b].z >> 1;
+      if (pr != cur) {
+        flush();
+        cur = pr;
+        P0 = P1 = P2 = 0.f;
+      }
+      const float *c0 = coef + pr * 3 * NP;
       float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        psi[p] += jump;
-        float E1, ex;
-        attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
-        const float d = fmaf(dv[p], q.y, dB);
-        const float x = psi[p] - d;
-        const float pb = fmaf(x, E1, d);
-        psi[p] = fmaf(x, ex, d);
-        dv[p] = pb;
-        const float t0 = w0[p] * pb;
-        S0 += t0;
-        const float t1 = t0 * sinz[p];
-        S1 += t1;
-        S2 = fmaf(t1, sinz[p], S2);
+        S0 = fmaf(c0[p], dv[b][p], S0);
+        S1 = fmaf(c0[NP + p], dv[b][p], S1);
+        S2 = fmaf(c0[2 * NP + p], dv[b][p], S2);
       }
-      store_dev<NP>(I, dv, pol_stream);
-      S0 *= af;
-      S1 *= af;
-      S2 *= af;
-      double *ac = acc + (int64_t)cell * (kOutputs * L.gc);
-      red_f64(ac, f32_to_f64(S0), pol_keep);
-      red_f64(ac + L.gc, f32_to_f64(fx * S1), pol_keep);
-      red_f64(ac + 2 * L.gc, f32_to_f64(fy * S1), pol_keep);
-      red_f64(ac + 3 * L.gc, f32_to_f64(fxx * S2), pol_keep);
-      red_f64(ac + 4 * L.gc, f32_to_f64(fxy * S2), pol_keep);
-      red_f64(ac + 5 * L.gc, f32_to_f64(fyy * S2), pol_keep);
-      bhi_prev = q.z;
-      blo_prev = q.w;
-      I += W;
-      r_cur = r_next;
-      r_next = rnn;
-      q = qn;
-      dB = dBn;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) dv[p] = dvn[p];
+      const float af = __int_as_float(en[b].y);
+      P0 = fmaf(af, S0, P0);
+      P1 = fmaf((en[b].z & 1) ? -af : af, S1, P1);
+      P2 = fmaf(af, S2, P2);
     }
   }
+  if (e1 > e0) flush();
+  // FP64 work here is per (cell, group), not per update: conversions by integer operations, one add per sum
+  double D[kOutputs];
+#pragma unroll
+  for (int k = 0; k < kOutputs; ++k) D[k] = f32_to_f64(hi[k]) + f32_to_f64(lo[k]);
+  const double is = a.scale[1];   // the deviations are in the state's scaled units (exact power of two)
+  const int64_t idx = (int64_t)g * v.ncell + cell;
+  const double B = a.B[idx];
+  a.out.E[idx] = (B * v.geo[cell] + D[0] * is) * a.inv_c;
+  a.out.Fx[idx] = D[1] * is;
+  a.out.Fy[idx] = D[2] * is;
+  a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + D[3] * is;
+  a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + D[4] * is;
+  a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + D[5] * is;
+  a.Bref[idx] = B;   // the new deviations refer to this step's B
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -496,8 +673,12 @@ int grid_for(int64_t n, int block) {
 }  // namespace
 
 cudaError_t launch_prep(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
-  const Layout L = layout_for(v, prec);
-  prep_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, L, prec == MOLC_FP32);
+  Layout L = layout_for(v, prec);
+  if (prec == MOLC_FP64) L.gc = L.n_chunks = 1;   // input checks only: one group per tile row, all groups
+  if (L.gc > 32 || L.n_chunks > 65535) return cudaErrorInvalidConfiguration;
+  const int n_tiles = (v.ncell + kPrepCells - 1) / kPrepCells;
+  const dim3 grid((unsigned)std::min(n_tiles, 152 * 16), (unsigned)(prec == MOLC_FP64 ? v.G : L.n_chunks));
+  prep_kernel<<<grid, 128, 0, st>>>(v, a, L, prec == MOLC_FP32);
   return cudaGetLastError();
 }
 
@@ -529,7 +710,37 @@ cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_
 }
 
 cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
-  finalize_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, layout_for(v, prec));
+  const Layout L = layout_for(v, prec);
+  if (prec == MOLC_FP64) {
+    finalize_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, L);
+    return cudaGetLastError();
+  }
+  const int64_t blocks = ((int64_t)v.ncell * L.gc + 127) / 128;
+  if (blocks > 0x7fffffff || L.n_chunks > 65535) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)blocks, (unsigned)L.n_chunks);
+  const size_t smem = (size_t)v.n_pairs * (3 * v.n_polar + 2) * sizeof(float);
+  if (smem > kMaxGatherSmem) return cudaErrorInvalidConfiguration;
+  switch (v.n_polar) {
+#define MOLC_MOMENTS(NP)                                                                                       \
+  case NP:                                                                                                     \
+    if (smem > 48 * 1024) {                                                                                    \
+      cudaError_t e = cudaFuncSetAttribute(moments_fp32_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                           (int)smem);                                                         \
+      if (e != cudaSuccess) return e;                                                                          \
+    }                                                                                                          \
+    moments_fp32_kernel<NP><<<grid, 128, smem, st>>>(v, a, L);                                                 \
+    break;
+    MOLC_MOMENTS(1)
+    MOLC_MOMENTS(2)
+    MOLC_MOMENTS(3)
+    MOLC_MOMENTS(4)
+    MOLC_MOMENTS(5)
+    MOLC_MOMENTS(6)
+    MOLC_MOMENTS(7)
+    MOLC_MOMENTS(8)
+#undef MOLC_MOMENTS
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

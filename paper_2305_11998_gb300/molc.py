@@ -28,7 +28,8 @@ MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")
 EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "molc_intensity_count",
             "molc_intensity_bytes", "molc_intensity_init", "molc_sweep", "molc_closure", "molc_intensity_export",
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
-            "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch")
+            "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
+            "molc_kernel_time_parts")
 
 
 class MolcError(RuntimeError):
@@ -92,6 +93,7 @@ def load(build_if_needed: bool = True):
         "molc_tracks_export": (C.c_int, [vp, i64p, i64p, dp, ip, ip, dp, dp]),
         "molc_kernel_timing": (C.c_int, [vp, C.c_int]),
         "molc_kernel_time": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
+        "molc_kernel_time_parts": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_device_status": (C.c_int, [vp, ip]),
         "molc_last_error": (C.c_char_p, []),
         "molc_destroy": (None, [vp]),
@@ -261,6 +263,13 @@ class Plan:
         n = C.c_int()
         _check(self._lib.molc_kernel_time(self._h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def kernel_time_parts(self):
+        """({"prep", "sweep", "moments"} summed milliseconds, timed calls) since the last call."""
+        ms = (C.c_double * 3)()
+        n = C.c_int()
+        _check(self._lib.molc_kernel_time_parts(self._h, ms, C.byref(n)))
+        return dict(zip(("prep", "sweep", "moments"), list(ms))), n.value
 
     def device_status(self) -> int:
         code = C.c_int()

@@ -40,7 +40,7 @@ def assert_moments_close(a, b, c):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_static_scratch_matches_sweep_two_calls_in_a_row(molc, prec):
-    wl = synth.WORKLOADS["fc64_g17_d128"]      # 64^2 x 17 groups: 3.3 MB (FP64) / 4.7 MB (FP32) of workspace
+    wl = synth.WORKLOADS["fc64_g17_d128"]      # 64^2 x 17 groups: 3.3 MB (FP64) / 1.4 MB (FP32) of workspace
     d = wl.inputs(2)
     P = molc.Plan.from_workload(wl)
     k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
