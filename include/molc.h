@@ -118,8 +118,9 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
 molc_status molc_plan_get_info(const molc_plan *plan, molc_plan_info *info);
 
 /* The opaque intensity state I^{n-1} of one precision: one element per (segment, direction, group) (FP64: 8
- * bytes, FP32: 4) holding the deviation of the segment average from the cell's Planck intensity, followed by
- * that reference Planck intensity per (group, cell) in FP64 and a small header.  The FP32 state works in units
+ * bytes, FP32: 4, laid out for the sweep kernel with a little padding) holding the deviation of the segment
+ * average from the cell's Planck intensity, followed by that reference Planck intensity per (group, cell) in
+ * FP64 and a small header.  The FP32 state works in units
  * scaled by a power of two (chosen by molc_intensity_init so that max B maps near 2^100), which keeps
  * intensities down to ~1e-68 of max B in the normal FP32 range.  molc_intensity_count gives the elements,
  * molc_intensity_bytes the bytes to allocate (256-byte aligned device memory).  The layout is private to the

@@ -94,6 +94,9 @@ struct molc_plan {
   int64_t n_items32 = 0;
   int64_t *d_cell_off = nullptr;
   int4 *d_gent = nullptr;
+  int64_t *d_boff = nullptr;
+  int *d_track_pos = nullptr;
+  int64_t bundle_slots = 0;   // FP32 state: step slots of all bundles (boff[n_blocks])
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
@@ -300,7 +303,7 @@ void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
                   p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
-                  p->d_cell_off, p->d_gent};
+                  p->d_cell_off, p->d_gent, p->d_boff, p->d_track_pos};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -649,11 +652,23 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   }
   p->n_items32 = (int64_t)items.size();
   p->acc_elems = (size_t)ncell * kOutputs * p->G;   // FP64 sweep accumulators
+  std::vector<int> track_pos(T);
+  for (int64_t i = 0; i < T; ++i) track_pos[order[i]] = (int)i;
+  // FP32 state bundles: block b of the sweep owns as many step slots as its longest item
+  const int64_t n_blocks32 = (p->n_items32 + kSweepBlock - 1) / kSweepBlock;
+  std::vector<int64_t> boff(n_blocks32 + 1, 0);
+  for (int64_t b = 0; b < n_blocks32; ++b) {
+    int longest = 0;
+    for (int64_t i = b * kSweepBlock; i < std::min(p->n_items32, (b + 1) * kSweepBlock); ++i)
+      longest = std::max(longest, td[items[i].x].nseg);
+    boff[b + 1] = boff[b] + longest;
+  }
+  p->bundle_slots = boff[n_blocks32];
 
   // ---- FP32 cell moments are gathered per cell from the swept state: for every cell, one entry per (track,
-  // sense) segment crossing it, {state row, A/V (f32 bits), 2 pair + sense, 0}, rows as the sweep writes them
-  // (track t, sense +: row 2 seg_off + j for its j-th segment; sense -: row 2 seg_off + nseg + (nseg - 1 - j)).
-  // Entries of a cell are in track order, so the gathered sums are deterministic.
+  // sense) segment crossing it, {position 2 track_pos + sense, step along that sense, A/V (f32 bits),
+  // 2 pair + sense}; the + sense reaches the track's j-th segment at step j, the - sense at step nseg - 1 - j.
+  // Entries of a cell are in track order (so grouped by azimuth pair), and the gathered sums deterministic.
   if (2 * S > (int64_t)0x7fffffff) {
     delete p;
     return fail(MOLC_ERR_INVALID_ARG, "create: too many segments for the FP32 state rows");
@@ -679,14 +694,14 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         int afb;
         std::memcpy(&afb, &af, 4);
         const int c = p->seg_cell[q];
-        gent[pos[c]++] = make_int4((int)(2 * t.seg_off + j), afb, 2 * t.pair, 0);
-        gent[pos[c]++] = make_int4((int)(2 * t.seg_off + t.nseg + (t.nseg - 1 - j)), afb, 2 * t.pair + 1, 0);
+        gent[pos[c]++] = make_int4(2 * track_pos[k], j, afb, 2 * t.pair);
+        gent[pos[c]++] = make_int4(2 * track_pos[k] + 1, t.nseg - 1 - j, afb, 2 * t.pair + 1);
       }
     }
     for (int i = 0; i < ncell; ++i)
       for (int64_t e = pos[i]; e < cell_off[i + 1]; ++e) {
         gent[e] = gent[pos[i] - 1];
-        gent[e].y = 0;   // zero area
+        gent[e].z = 0;   // zero area
       }
   }
 
@@ -721,6 +736,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_status, (const int *)nullptr, 1, "status")
   UP(d_cell_off, cell_off.data(), cell_off.size(), "cell entry offsets")
   UP(d_gent, gent.data(), gent.size(), "cell entries")
+  UP(d_boff, boff.data(), boff.size(), "state bundles")
+  UP(d_track_pos, track_pos.data(), track_pos.size(), "track positions")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
@@ -747,6 +764,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.status = p->d_status;
   v.cell_off = p->d_cell_off;
   v.gent = p->d_gent;
+  v.boff = p->d_boff;
+  v.track_pos = p->d_track_pos;
   *out = p;
   return MOLC_OK;
 }
@@ -772,18 +791,23 @@ int64_t molc_intensity_count(const molc_plan *p) {
   return p ? 2 * (int64_t)p->n_polar * p->view.n_track_segments * p->G : 0;
 }
 
+// Elements of the stored deviations: FP64, one per (segment, direction, group); FP32, the bundle slots.
+static int64_t state_elems(const molc_plan *p, molc_precision prec) {
+  return prec == MOLC_FP64 ? molc_intensity_count(p) : p->bundle_slots * kSweepBlock * p->n_polar;
+}
+
 size_t molc_intensity_bytes(const molc_plan *p, molc_precision prec) {
   if (!p) return 0;
-  return header_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell) + kHeaderBytes;
+  return header_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell) + kHeaderBytes;
 }
 
 static double *bref_of(const molc_plan *p, molc_precision prec, void *I) {
-  return (double *)((char *)I + bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4));
+  return (double *)((char *)I + bref_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4));
 }
 
 static double *header_of(const molc_plan *p, molc_precision prec, void *I) {
   return (double *)((char *)I +
-                    header_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell));
+                    header_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell));
 }
 
 static molc_status check_prec(const molc_plan *p, molc_precision prec, const char *who) {
@@ -802,7 +826,7 @@ molc_status molc_intensity_init(molc_plan *p, molc_precision prec, void *I, cons
   DeviceGuard dg(p->device);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nb = (size_t)p->G * p->view.ncell * sizeof(double);
-  cudaError_t e = cudaMemsetAsync(I, 0, bref_offset(molc_intensity_count(p), prec == MOLC_FP64 ? 8 : 4), st);
+  cudaError_t e = cudaMemsetAsync(I, 0, bref_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(bref_of(p, prec, I), B, nb, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = launch_set_scale(p->view, prec, B, header_of(p, prec, I), st);
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "intensity_init");

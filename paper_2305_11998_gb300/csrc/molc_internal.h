@@ -11,6 +11,7 @@ namespace molc {
 constexpr int kMaxPolarFP32 = 8;     // FP32 sweep: polar cosines per azimuth handled by one half-warp
 constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators per (cell, group)
 constexpr int kGatherPad = 4;        // FP32 moments: each cell's entry list is padded to a multiple of this
+constexpr int kSweepBlock = 128;     // FP32 sweep: work items (threads) per block = width of a state bundle
 constexpr size_t kMaxGatherSmem = 200 * 1024;  // FP32 moments: per-pair coefficient table in shared memory
 
 // Device status bits (the first one set wins in molc_device_status).
@@ -59,11 +60,23 @@ struct PlanView {
   int *status;
   int gc32;                     // FP32 sweep: groups per chunk
   const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into gent
-  const int4 *gent;             // FP32 moments: per cell, {state row, A/V f32 bits, 2 pair + sense, 0}
+  const int4 *gent;             // FP32 moments: per cell, {track-sense position, step, A/V f32 bits, 2 pair + sense}
+  const int64_t *boff;          // FP32 state: [n_blocks + 1] first step slot of each bundle
+  const int *track_pos;         // FP32 items: position of each track in the longest-first order
 };
 
-// Layout of the opaque intensity state: groups are tiled in chunks of `gc` groups; within a chunk, rows of
-// width gcount*n_polar are ordered (track, sense, step); element (chunk, row, g_local, p).
+// FP32 state, "bundle" layout: the work items (track, sense, group) of sweep block b, i.e. items
+// [128 b, 128 b + 128), own the step slots [boff[b], boff[b+1]) (boff[b+1] - boff[b] = the longest track of the
+// block); slot t holds the NP deviations of the block's 128 items side by side, so a block reads and writes
+// 128 * NP contiguous values per step.  Items are numbered chunk-major: item = chunk * 2 T gc + pos * gcount + g_local,
+// pos = 2 * track_pos[track] + sense.
+__host__ __device__ inline int64_t bundle_index(const int64_t *boff, int64_t item, int s, int NP) {
+  return ((boff[item / kSweepBlock] + s) * kSweepBlock + item % kSweepBlock) * NP;
+}
+
+// Group tiling of the opaque intensity state: groups are tiled in chunks of `gc` groups.  FP64 state: within a
+// chunk, rows of width gcount*n_polar are ordered (track, sense, step); element (chunk, row, g_local, p).
+// FP32 state: the bundle layout below.
 struct Layout {
   int gc;                  // groups per chunk (FP64: G, FP32: PlanView::gc32)
   int n_chunks;

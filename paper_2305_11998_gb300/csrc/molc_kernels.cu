@@ -164,7 +164,6 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
 // processed in chunks (chunk-major item order) so that a chunk's cell table and FP64 accumulators stay
 // resident in L2 while the deviations stream through HBM.
 // ---------------------------------------------------------------------------------------------------------
-constexpr int kSweepBlock = 128;
 
 // (1 - e^-tau)/tau and e^-tau in FP32.  With h = e^(-tau/2) (ex2.approx):
 //   tau < 1/2:  E1 = h sinh(tau/2) / (tau/2), the even Taylor series in y = tau^2/4 to y^3 (truncation
@@ -191,33 +190,12 @@ __device__ __forceinline__ double f32_to_f64(float x) {
   return __hiloint2double((int)hi, (int)(u << 29));
 }
 
-// L2 eviction policies (sm_80+ createpolicy) and loads/stores/reductions carrying them: the streamed state is
-// evict-first (used once per sweep), the cell table and the FP64 accumulators of the current group chunk are
-// evict-last (reused by every characteristic crossing the cell).
+// L2 eviction policy (sm_80+ createpolicy) for the streamed state, which each pass touches once: evict-first,
+// so that the cell tables and segment records stay in L2.
 __device__ __forceinline__ unsigned long long policy_evict_first() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
-}
-__device__ __forceinline__ unsigned long long policy_evict_last() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ float4 ld_table4(const float4 *p, unsigned long long pol) {
-  float4 v;
-  asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-      : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ float ld_table1(const float *p, unsigned long long pol) {
-  float v;
-  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-  return v;
-}
-__device__ __forceinline__ void red_f64(double *p, double v, unsigned long long pol) {
-  asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
 }
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -232,19 +210,19 @@ __device__ __forceinline__ void load_dev(const float *p, float (&v)[NP], unsigne
   if constexpr (NP % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 4)
-      asm("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+      asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
           : "=f"(v[i]), "=f"(v[i + 1]), "=f"(v[i + 2]), "=f"(v[i + 3])
           : "l"(p + i), "l"(pol));
   } else if constexpr (NP % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 2)
-      asm("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+      asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
           : "=f"(v[i]), "=f"(v[i + 1])
           : "l"(p + i), "l"(pol));
   } else {
 #pragma unroll
     for (int i = 0; i < NP; ++i)
-      asm("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v[i]) : "l"(p + i), "l"(pol));
+      asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v[i]) : "l"(p + i), "l"(pol));
   }
 }
 template <int NP>
@@ -273,47 +251,41 @@ __device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsign
 // 16-byte pieces where NP * 4 bytes allow, else 8- or 4-byte pieces (the thread's deviations start at a multiple
 // of NP * 4 bytes of a 256-byte aligned state).
 template <int NP>
-__device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src, unsigned long long pol) {
+__device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   if constexpr (NP % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 4)
-      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
   } else if constexpr (NP % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 2)
-      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
   } else {
 #pragma unroll
     for (int i = 0; i < NP; ++i)
-      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
   }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-__device__ __forceinline__ void copy16_async(void *dst_smem, const void *src, unsigned long long pol) {
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst_smem)),
-               "l"(src), "l"(pol)
+__device__ __forceinline__ void copy16_async(void *dst_smem, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void copy4_async(void *dst_smem, const void *src, unsigned long long pol) {
-  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(
-                   (unsigned)__cvta_generic_to_shared(dst_smem)),
-               "l"(src), "l"(pol)
+__device__ __forceinline__ void copy4_async(void *dst_smem, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
                : "memory");
 }
 __device__ __forceinline__ int2 ld_record(const int2 *p) {
   int2 v;
-  asm("ld.global.nc.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  // volatile: a load the compiler cannot see as one must not be executed speculatively (callers guard the
+  // address range with a condition)
+  asm volatile("ld.global.nc.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
 
@@ -340,7 +312,6 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   const int g0 = ch * L.gc;
   const int gcount = min(L.gc, v.G - g0);
   const int g = g0 + gi;
-  const int W = gcount * NP;
   const int nseg = live ? tr.nseg : 0;
   // warp-uniform trip count
   int nmax = nseg;
@@ -348,8 +319,11 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(kFull, nmax, o));
   if (nmax == 0) return;
 
-  const unsigned long long pol_stream = policy_evict_first(), pol_keep = policy_evict_last();
-  float *I = (float *)a.I + L.rows * (int64_t)NP * g0 + (2 * tr.seg_off + (int64_t)sense * nseg) * W + gi * NP;
+  const unsigned long long pol_stream = policy_evict_first();
+  // floats between consecutive steps of one item (bundle layout); a run-time value, so that the copies below
+  // address through registers
+  const int64_t stride = (int64_t)kSweepBlock * v.n_polar;
+  float *I = (float *)a.I + (v.boff[blockIdx.x] * kSweepBlock + tid) * NP;
   const int2 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
   const int rstep = sense ? -1 : 1;
   const int64_t cbase = (int64_t)ch * v.ncell * L.gc + gi;
@@ -375,10 +349,10 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     if (k < nseg) {
-      copy_dev_async<NP>(&sdev[k][tid * NP], I + (int64_t)k * W, pol_stream);
+      copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride);
       if (k < 2) {
-        copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc, pol_keep);
-        copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc, pol_keep);
+        copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc);
+        copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc);
       }
     }
     cp_async_commit();
@@ -393,11 +367,11 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
       const int s = s0 + u;
       if (s < nseg) {
         // group s+3: deviations of step s+3, table entry of step s+2
-        if (s + 3 < nseg) copy_dev_async<NP>(&sdev[(u + 3) % kSteps][tid * NP], I + (int64_t)3 * W, pol_stream);
+        if (s + 3 < nseg) copy_dev_async<NP>(&sdev[(u + 3) % kSteps][tid * NP], I + 3 * stride);
         if (s + 2 < nseg) {
           const int c2 = recs[(u + 2) % kSteps].x;
-          copy16_async(&stab[(u + 2) % kSteps][tid], cd + (int64_t)c2 * L.gc, pol_keep);
-          copy4_async(&sdB[(u + 2) % kSteps][tid], cdB + (int64_t)c2 * L.gc, pol_keep);
+          copy16_async(&stab[(u + 2) % kSteps][tid], cd + (int64_t)c2 * L.gc);
+          copy4_async(&sdB[(u + 2) % kSteps][tid], cdB + (int64_t)c2 * L.gc);
         }
         cp_async_commit();
         cp_async_wait<2>();   // groups up to s+1 (deviations of step s, table entry of step s) have landed
@@ -435,7 +409,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
         store_dev<NP>(I, dv, pol_stream);
         bhi_prev = q.z;
         blo_prev = q.w;
-        I += W;
+        I += stride;
         if (s + kSteps < nseg) recs[u] = ld_record(rec + (s + kSteps) * rstep);
       }
     }
@@ -486,14 +460,14 @@ __global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs
   if (t >= (int64_t)v.ncell * gcount) return;
   const int cell = (int)(t / gcount), gi = (int)(t - (int64_t)cell * gcount);
   const int g = g0 + gi;
-  const int W = gcount * NP;
-  const float *I = (const float *)a.I + L.rows * (int64_t)NP * g0 + gi * NP;
+  const int64_t item0 = (int64_t)ch * 2 * v.n_tracks * L.gc + gi;   // item of (position 0, this group)
+  const float *I = (const float *)a.I;
   const unsigned long long pol_stream = policy_evict_first();
   float hi[kOutputs], lo[kOutputs];
 #pragma unroll
   for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
   const int64_t e0 = v.cell_off[cell], e1 = v.cell_off[cell + 1];
-  int cur = e1 > e0 ? (__ldg(&v.gent[e0].z) >> 1) : 0;
+  int cur = e1 > e0 ? (__ldg(&v.gent[e0].w) >> 1) : 0;
   float P0 = 0.f, P1 = 0.f, P2 = 0.f;
   auto flush = [&]() {
     const float cf = csn[2 * cur], sf = csn[2 * cur + 1];
@@ -510,10 +484,11 @@ __global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs
     for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(v.gent + e + b);
     float dv[kGatherBatch][NP];
 #pragma unroll
-    for (int b = 0; b < kGatherBatch; ++b) load_dev<NP>(I + (int64_t)en[b].x * W, dv[b], pol_stream);
+    for (int b = 0; b < kGatherBatch; ++b)
+      load_dev<NP>(I + bundle_index(v.boff, item0 + (int64_t)en[b].x * gcount, en[b].y, NP), dv[b], pol_stream);
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) {
-      const int pr = en[b].z >> 1;
+      const int pr = en[b].w >> 1;
       if (pr != cur) {
         flush();
         cur = pr;
@@ -527,9 +502,9 @@ __global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs
         S1 = fmaf(c0[NP + p], dv[b][p], S1);
         S2 = fmaf(c0[2 * NP + p], dv[b][p], S2);
       }
-      const float af = __int_as_float(en[b].y);
+      const float af = __int_as_float(en[b].z);
       P0 = fmaf(af, S0, P0);
-      P1 = fmaf((en[b].z & 1) ? -af : af, S1, P1);
+      P1 = fmaf((en[b].w & 1) ? -af : af, S1, P1);
       P2 = fmaf(af, S2, P2);
     }
   }
@@ -609,7 +584,7 @@ __global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx
 // looping over polar cosines and the selected groups.  Ibar = B_ref(cell) + delta.
 template <class T>
 __global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *Bref, const double *scale,
-                                      int g_begin, int g_count, double *canon, int to_canon) {
+                                      int g_begin, int g_count, double *canon, int to_canon, int bundle) {
   const int NP = v.n_polar;
   const double sc = scale[0], is = scale[1];
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < L.rows;
@@ -626,7 +601,11 @@ __global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *
       const int64_t cs = v.dir_seg_off[dir] + (sense ? tr.canon_minus : tr.canon_plus) + s;
       for (int g = g_begin; g < g_begin + g_count; ++g) {
         const int ch = g / L.gc, gl = g - ch * L.gc, gcount = min(L.gc, v.G - ch * L.gc);
-        T *el = I + L.rows * (int64_t)NP * (ch * L.gc) + row * (int64_t)(gcount * NP) + gl * NP + p;
+        T *el = bundle ? I + bundle_index(v.boff,
+                                          (int64_t)ch * 2 * v.n_tracks * L.gc +
+                                              (int64_t)(2 * v.track_pos[t] + sense) * gcount + gl,
+                                          s, NP) + p
+                       : I + L.rows * (int64_t)NP * (ch * L.gc) + row * (int64_t)(gcount * NP) + gl * NP + p;
         const double br = Bref[(int64_t)g * v.ncell + cell];
         double *cv = canon + cs * g_count + (g - g_begin);
         if (to_canon)
@@ -756,10 +735,10 @@ cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *
   const Layout L = layout_for(v, prec);
   if (prec == MOLC_FP64)
     intensity_copy_kernel<double><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (double *)I, Bref, scale, g_begin,
-                                                                         g_count, canon, to_canon);
+                                                                         g_count, canon, to_canon, 0);
   else
     intensity_copy_kernel<float><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (float *)I, Bref, scale, g_begin,
-                                                                       g_count, canon, to_canon);
+                                                                       g_count, canon, to_canon, 1);
   return cudaGetLastError();
 }
 
