@@ -95,7 +95,7 @@ struct molc_plan {
   int64_t *d_cell_off = nullptr;
   int4 *d_gent = nullptr;
   int64_t *d_boff = nullptr;
-  int *d_track_pos = nullptr;
+  int *d_block_order = nullptr;
   int64_t bundle_slots = 0;   // FP32 state: step slots of all bundles (boff[n_blocks])
   size_t acc_elems = 0;
   size_t device_bytes = 0;
@@ -303,7 +303,7 @@ void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
                   p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
-                  p->d_cell_off, p->d_gent, p->d_boff, p->d_track_pos};
+                  p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -630,43 +630,57 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     seg32[q] = r;
   }
 
-  // ---- FP32 work items: one thread per (track, sense, group), ordered chunk-major, then by decreasing track
-  // length, then track, sense and group.  Groups are tiled in chunks of up to 32; the threads of one (track,
-  // sense) are consecutive, so a warp's record and cell-table loads are shared by up to 32 lanes.
+  // ---- FP32 work items: one thread per (track, sense, group), numbered chunk-major, then by azimuth pair,
+  // sense, track (the tracks of a pair are adjacent in space) and group.  Groups are tiled in chunks of up to
+  // 32; the threads of one (track, sense) are consecutive, so a warp's record and cell-table loads are shared
+  // by up to 32 lanes, and a sweep block (128 consecutive items) holds neighbouring parallel tracks of one
+  // sense, which cross neighbouring cells at the same steps.  Blocks are launched longest first (block_order)
+  // for load balance.
   const int gc32 = std::min(p->G, 32);
   const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
-  std::vector<int64_t> order(T);
-  for (int64_t k = 0; k < T; ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return td[a].nseg > td[b].nseg; });
-  if (T > (int64_t)0x7fffffff) {
+  if (T > (int64_t)0x3fffffff) {
     delete p;
     return fail(MOLC_ERR_INVALID_ARG, "create: too many characteristics");
   }
   std::vector<int2> items;
   items.reserve((size_t)T * 2 * p->G);
+  std::vector<std::pair<int, int>> ts_order;   // (track, sense) in item order
+  ts_order.reserve((size_t)(2 * T));
+  for (int j = 0; j < p->n_pairs; ++j)
+    for (int sense = 0; sense < 2; ++sense)
+      for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) {
+        td[k].pos[sense] = (int)ts_order.size();
+        ts_order.emplace_back((int)k, sense);
+      }
   for (int ch = 0; ch < nch32; ++ch) {
     const int gcount = std::min(gc32, p->G - ch * gc32);
-    for (int64_t k : order)
-      for (int sense = 0; sense < 2; ++sense)
-        for (int gi = 0; gi < gcount; ++gi) items.push_back(make_int2((int)k, sense | (gi << 1) | (ch << 16)));
+    for (const auto &ks : ts_order)
+      for (int gi = 0; gi < gcount; ++gi)
+        items.push_back(make_int2(ks.first, ks.second | (gi << 1) | (ch << 16)));
   }
   p->n_items32 = (int64_t)items.size();
   p->acc_elems = (size_t)ncell * kOutputs * p->G;   // FP64 sweep accumulators
-  std::vector<int> track_pos(T);
-  for (int64_t i = 0; i < T; ++i) track_pos[order[i]] = (int)i;
   // FP32 state bundles: block b of the sweep owns as many step slots as its longest item
   const int64_t n_blocks32 = (p->n_items32 + kSweepBlock - 1) / kSweepBlock;
+  if (n_blocks32 > (int64_t)0x7fffffff) {
+    delete p;
+    return fail(MOLC_ERR_INVALID_ARG, "create: too many work items");
+  }
   std::vector<int64_t> boff(n_blocks32 + 1, 0);
+  std::vector<int> blen(n_blocks32), block_order(n_blocks32);
   for (int64_t b = 0; b < n_blocks32; ++b) {
     int longest = 0;
     for (int64_t i = b * kSweepBlock; i < std::min(p->n_items32, (b + 1) * kSweepBlock); ++i)
       longest = std::max(longest, td[items[i].x].nseg);
+    blen[b] = longest;
     boff[b + 1] = boff[b] + longest;
+    block_order[b] = (int)b;
   }
+  std::stable_sort(block_order.begin(), block_order.end(), [&](int x, int y) { return blen[x] > blen[y]; });
   p->bundle_slots = boff[n_blocks32];
 
   // ---- FP32 cell moments are gathered per cell from the swept state: for every cell, one entry per (track,
-  // sense) segment crossing it, {position 2 track_pos + sense, step along that sense, A/V (f32 bits),
+  // sense) segment crossing it, {item position of the (track, sense), step along that sense, A/V (f32 bits),
   // 2 pair + sense}; the + sense reaches the track's j-th segment at step j, the - sense at step nseg - 1 - j.
   // Entries of a cell are in track order (so grouped by azimuth pair), and the gathered sums deterministic.
   if (2 * S > (int64_t)0x7fffffff) {
@@ -694,8 +708,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         int afb;
         std::memcpy(&afb, &af, 4);
         const int c = p->seg_cell[q];
-        gent[pos[c]++] = make_int4(2 * track_pos[k], j, afb, 2 * t.pair);
-        gent[pos[c]++] = make_int4(2 * track_pos[k] + 1, t.nseg - 1 - j, afb, 2 * t.pair + 1);
+        gent[pos[c]++] = make_int4(t.pos[0], j, afb, 2 * t.pair);
+        gent[pos[c]++] = make_int4(t.pos[1], t.nseg - 1 - j, afb, 2 * t.pair + 1);
       }
     }
     for (int i = 0; i < ncell; ++i)
@@ -737,7 +751,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_cell_off, cell_off.data(), cell_off.size(), "cell entry offsets")
   UP(d_gent, gent.data(), gent.size(), "cell entries")
   UP(d_boff, boff.data(), boff.size(), "state bundles")
-  UP(d_track_pos, track_pos.data(), track_pos.size(), "track positions")
+  UP(d_block_order, block_order.data(), block_order.size(), "block order")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_acc, (const double *)nullptr, p->acc_elems, "accumulators")
@@ -765,7 +779,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.cell_off = p->d_cell_off;
   v.gent = p->d_gent;
   v.boff = p->d_boff;
-  v.track_pos = p->d_track_pos;
+  v.block_order = p->d_block_order;
   *out = p;
   return MOLC_OK;
 }

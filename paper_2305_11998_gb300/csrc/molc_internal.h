@@ -30,6 +30,7 @@ struct TrackDev {
   int entry_minus;      // edge the - sense enters through (= exit edge of the + sense)
   int64_t canon_plus;   // offset of this track's segments within the + sense direction's canonical block
   int64_t canon_minus;  // same for the - sense (tracks are in reverse order there)
+  int pos[2];           // FP32 work items: position of the (track, + / - sense) in the item order
 };
 
 struct PairDev {
@@ -60,16 +61,16 @@ struct PlanView {
   int *status;
   int gc32;                     // FP32 sweep: groups per chunk
   const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into gent
-  const int4 *gent;             // FP32 moments: per cell, {track-sense position, step, A/V f32 bits, 2 pair + sense}
+  const int4 *gent;             // FP32 moments: per cell, {item position, step, A/V f32 bits, 2 pair + sense}
   const int64_t *boff;          // FP32 state: [n_blocks + 1] first step slot of each bundle
-  const int *track_pos;         // FP32 items: position of each track in the longest-first order
+  const int *block_order;       // FP32 sweep: bundle swept by each block of the launch (longest first)
 };
 
 // FP32 state, "bundle" layout: the work items (track, sense, group) of sweep block b, i.e. items
 // [128 b, 128 b + 128), own the step slots [boff[b], boff[b+1]) (boff[b+1] - boff[b] = the longest track of the
 // block); slot t holds the NP deviations of the block's 128 items side by side, so a block reads and writes
-// 128 * NP contiguous values per step.  Items are numbered chunk-major: item = chunk * 2 T gc + pos * gcount + g_local,
-// pos = 2 * track_pos[track] + sense.
+// 128 * NP contiguous values per step.  Items are numbered chunk-major:
+// item = chunk * 2 T gc + pos[sense] * gcount + g_local, pos = TrackDev::pos (pair, then sense, then track).
 __host__ __device__ inline int64_t bundle_index(const int64_t *boff, int64_t item, int s, int NP) {
   return ((boff[item / kSweepBlock] + s) * kSweepBlock + item % kSweepBlock) * NP;
 }

@@ -225,6 +225,31 @@ __device__ __forceinline__ void load_dev(const float *p, float (&v)[NP], unsigne
       asm volatile("ld.global.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v[i]) : "l"(p + i), "l"(pol));
   }
 }
+// The same through L2 with the default policy (ld.global.cg): the moment gather reads pieces of the state that
+// share sectors with pieces other cells read at about the same time.
+template <int NP>
+__device__ __forceinline__ void load_dev_cg(const float *p, float (&v)[NP]) {
+  if constexpr (NP % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 4) {
+      const float4 t = __ldcg(reinterpret_cast<const float4 *>(p + i));
+      v[i] = t.x;
+      v[i + 1] = t.y;
+      v[i + 2] = t.z;
+      v[i + 3] = t.w;
+    }
+  } else if constexpr (NP % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < NP; i += 2) {
+      const float2 t = __ldcg(reinterpret_cast<const float2 *>(p + i));
+      v[i] = t.x;
+      v[i + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) v[i] = __ldcg(p + i);
+  }
+}
 template <int NP>
 __device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsigned long long pol) {
   if constexpr (NP % 4 == 0) {
@@ -304,7 +329,8 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
   __shared__ __align__(16) float sdB[kSteps][kSweepBlock];
   const int tid = threadIdx.x;
-  const int64_t item = (int64_t)blockIdx.x * kSweepBlock + tid;
+  const int bundle = v.block_order[blockIdx.x];
+  const int64_t item = (int64_t)bundle * kSweepBlock + tid;
   const bool live = item < a.n_items;
   const int2 it = live ? a.items[item] : make_int2(0, 0);
   const TrackDev tr = v.tracks[it.x];
@@ -323,7 +349,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   // floats between consecutive steps of one item (bundle layout); a run-time value, so that the copies below
   // address through registers
   const int64_t stride = (int64_t)kSweepBlock * v.n_polar;
-  float *I = (float *)a.I + (v.boff[blockIdx.x] * kSweepBlock + tid) * NP;
+  float *I = (float *)a.I + (v.boff[bundle] * kSweepBlock + tid) * NP;
   const int2 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
   const int rstep = sense ? -1 : 1;
   const int64_t cbase = (int64_t)ch * v.ncell * L.gc + gi;
@@ -462,7 +488,6 @@ __global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs
   const int g = g0 + gi;
   const int64_t item0 = (int64_t)ch * 2 * v.n_tracks * L.gc + gi;   // item of (position 0, this group)
   const float *I = (const float *)a.I;
-  const unsigned long long pol_stream = policy_evict_first();
   float hi[kOutputs], lo[kOutputs];
 #pragma unroll
   for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
@@ -485,7 +510,7 @@ __global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs
     float dv[kGatherBatch][NP];
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b)
-      load_dev<NP>(I + bundle_index(v.boff, item0 + (int64_t)en[b].x * gcount, en[b].y, NP), dv[b], pol_stream);
+      load_dev_cg<NP>(I + bundle_index(v.boff, item0 + (int64_t)en[b].x * gcount, en[b].y, NP), dv[b]);
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) {
       const int pr = en[b].w >> 1;
@@ -603,7 +628,7 @@ __global__ void intensity_copy_kernel(PlanView v, Layout L, T *I, const double *
         const int ch = g / L.gc, gl = g - ch * L.gc, gcount = min(L.gc, v.G - ch * L.gc);
         T *el = bundle ? I + bundle_index(v.boff,
                                           (int64_t)ch * 2 * v.n_tracks * L.gc +
-                                              (int64_t)(2 * v.track_pos[t] + sense) * gcount + gl,
+                                              (int64_t)tr.pos[sense] * gcount + gl,
                                           s, NP) + p
                        : I + L.rows * (int64_t)NP * (ch * L.gc) + row * (int64_t)(gcount * NP) + gl * NP + p;
         const double br = Bref[(int64_t)g * v.ncell + cell];
