@@ -159,10 +159,10 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
 // ---------------------------------------------------------------------------------------------------------
 // FP32 production sweep.  One thread per (track, sense, group): the thread walks its track in its sense and
 // carries all NP polar cosines of the azimuth in registers (the in-plane track is shared by them).  Threads of
-// a warp hold consecutive groups of the same track-sense, so the cell table gathers, the previous-step
-// deviations (NP contiguous values per thread, vector loads) and the atomics are coalesced.  Groups are
-// processed in chunks (chunk-major item order) so that a chunk's cell table and FP64 accumulators stay
-// resident in L2 while the deviations stream through HBM.
+// a warp hold consecutive groups of the same track-sense, so the record and cell-table loads are shared and
+// coalesced; the previous-step deviations stream in and out in the bundle layout (a block's 128 threads read
+// and write 128 * NP contiguous values per step).  The sweep does no reduction: the cell moments are gathered
+// afterwards from the swept state (moments_fp32_kernel).
 // ---------------------------------------------------------------------------------------------------------
 
 // (1 - e^-tau)/tau and e^-tau in FP32.  With h = e^(-tau/2) (ex2.approx):
@@ -460,11 +460,11 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
 }
 
 // Entries are taken kGatherBatch at a time so that their state loads are in flight together (each cell's entry
-// list is padded to a multiple of kGatherBatch with zero-area entries of its last pair).
-constexpr int kGatherBatch = 4;
+// list is padded to a multiple of kGatherPad with zero-area entries of its last pair, so the batch must equal it).
+constexpr int kGatherBatch = kGatherPad;
 
 template <int NP>
-__global__ void __launch_bounds__(128) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
   extern __shared__ float coef[];   // [pair][3][NP] {w, w sin, w sin^2}, then [pair][2] {cos, sin}
   float *csn = coef + 3 * NP * v.n_pairs;
   for (int i = threadIdx.x; i < v.n_pairs * NP; i += blockDim.x) {
