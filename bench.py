@@ -27,6 +27,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
+from paper_2305_11998_gb300 import dist as pdist  # noqa: E402
 
 WORKLOAD = "fc512_g17_d128"
 METRIC = "segment×group updates/s"
@@ -49,13 +50,6 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the FP32 sweeps (warmup + steps), for profiler captures")
     return ap.parse_args()
-
-
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
 
 
 def measured_peaks():
@@ -139,7 +133,7 @@ def cpu_oracle_sample(wl, d, max_seconds=12.0):
 
 
 def run_reference(args):
-    ws, rank, _ = dist_env()
+    ws, rank, _ = pdist.env()
     if rank != 0:
         return
     wl = synth.WORKLOADS[args.workload]
@@ -177,7 +171,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    ws, rank, local = dist_env()
+    ws, rank, local = pdist.env()
     if ws > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -185,7 +179,7 @@ def run_ours(args):
     import paper_2305_11998_gb300 as molc
 
     wl = synth.WORKLOADS[args.workload]
-    d = wl.inputs(seed=rank)
+    d = wl.inputs(seed=pdist.instance_seed(0, rank))
     P = molc.Plan.from_workload(wl)
     info = P.info
     G, ncell = wl.G, wl.ncell
@@ -223,18 +217,14 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = pdist.max_over_ranks(e0.elapsed_time(e1), dev)
     parts, kern_n = P.kernel_time_parts()
     kern_ms = parts["sweep"]
     P.kernel_timing(False)
     clocks = sampler.stop() if sampler else None
     status = P.device_status()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_step = ms / args.steps
-    value = ws * info.n_updates * args.steps / (ms / 1e3)
+    value = pdist.weak_scaling_rate(info.n_updates * args.steps, ws, ms / 1e3)
 
     # roofline of the dominant kernel (the FP32 sweep): algorithmic bytes per launch / average launch time
     gc = info.fp32_groups_per_warp
@@ -285,12 +275,8 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1)
-        if ws > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ws * info.n_updates * args.steps / (ems / 1e3), "unit": "updates/s",
+        ems = pdist.max_over_ranks(e0.elapsed_time(e1), dev)
+        e2e = {"value": pdist.weak_scaling_rate(info.n_updates * args.steps, ws, ems / 1e3), "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / args.steps}
 
     # the plain FP64 GPU sweep on the same workload (the speed-up denominator)
