@@ -57,6 +57,9 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 #define MOLC_AREA_RENORM 1u /* scale A_{k,s} per (cell, azimuth) so that sum over C(i,m) of A = cell area */
 #define MOLC_HOST_ONLY 2u   /* build the characteristic grid on the host only (no device memory, no GPU needed):
                                only molc_plan_get_info, molc_tracks_export and molc_destroy accept such a plan */
+#define MOLC_AUTOTUNE 4u    /* time the FP32 sweep's compiled staging depths on this plan during molc_create
+                               (temporary device memory of about one FP32 state) and keep the fastest; the
+                               choice changes no result, only speed (molc_plan_info.fp32_sweep_depth) */
 
 typedef struct {
   int nx, ny;               /* material cells (>= 1) */
@@ -99,6 +102,7 @@ typedef struct {
   int64_t n_updates;        /* segment x direction x group updates per sweep (= n_segments G) */
   int fp32_groups_per_warp; /* groups per chunk of the FP32 sweep (chunks run one after another) */
   size_t device_bytes;      /* device memory the plan holds */
+  int fp32_sweep_depth;     /* staging depth of the FP32 sweep (steps of look-ahead; MOLC_AUTOTUNE picks it) */
 } molc_plan_info;
 
 /* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,
@@ -175,6 +179,40 @@ molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa
 molc_status molc_sweep_static_scratch(molc_plan *plan, molc_precision prec, const double *kappa,
                                       const double *B, double c, double dt, void *I, const double *bnd,
                                       const molc_moments *out, molc_stream stream);
+
+/* ---- Batched FP32 sweep of many independent instances (plans of any sizes, group counts and quadratures on
+ * one device): every step runs as one launch of each kernel over the work of all instances (one sweep launch
+ * per distinct (polar count, staging depth) and one moment launch per polar count), with the sweep blocks of
+ * all instances scheduled longest first.  Built for many uneven problems in one time-stepping loop, where
+ * per-instance launches would leave most of the GPU idle.  The paper sweeps one problem; this is the
+ * production packaging of the same per-instance sweep (results are bit-identical to molc_sweep + molc_closure
+ * per instance). */
+typedef struct molc_batch molc_batch;
+
+/* Per-instance arguments, as for molc_sweep (device pointers) plus optional Eddington factors. */
+typedef struct {
+  const double *kappa, *B;      /* device [G][cell] */
+  double c, dt;                 /* > 0 */
+  void *I;                      /* device FP32 state of this instance's plan (molc_intensity_init'ed) */
+  const double *bnd;            /* device [4][G] */
+  molc_moments out;             /* device, each [G][cell] */
+  double *fxx, *fxy, *fyy;      /* device [G][cell] (f = N / (c E), as molc_closure), or all NULL */
+} molc_sweep_args;
+
+/* plans: host array of n (>= 1) plans created on the current device (not MOLC_HOST_ONLY, at most 8 polar
+ * cosines); the batch keeps pointers to them (destroy the batch first).  Builds the block maps (device). */
+molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out);
+
+/* Record the per-instance arguments (host array of n, copied to the device synchronously).  Call again whenever
+ * a buffer changes; molc_batch_sweep uses the last recorded arguments. */
+molc_status molc_batch_bind(molc_batch *batch, const molc_sweep_args *args);
+
+/* One backward-Euler step of every instance (molc_sweep in FP32, then the factors where requested).
+ * Asynchronous on `stream`; no allocation and no host synchronisation, so a step (or several) can be captured
+ * in a CUDA graph and replayed.  Device status words are per plan (molc_device_status). */
+molc_status molc_batch_sweep(molc_batch *batch, molc_stream stream);
+
+void molc_batch_destroy(molc_batch *batch);
 
 /* Eddington factors of each cell and group, f = N / (c E) (Eq. 7 with the cell averages of Eq. 15):
  * fxx, fxy, fyy device [G][cell]; f_zz = 1 - f_xx - f_yy.  f_grey: device [3][cell] or NULL, the

@@ -97,6 +97,7 @@ struct molc_plan {
   int64_t *d_boff = nullptr;
   int *d_block_order = nullptr;
   int64_t bundle_slots = 0;   // FP32 state: step slots of all bundles (boff[n_blocks])
+  int64_t n_blocks32 = 0;     // FP32 sweep blocks (bundles)
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
@@ -310,6 +311,78 @@ void free_device(molc_plan *p) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
 
+size_t state_bytes_fp32(const molc_plan *p);
+double *bref_ptr(const molc_plan *p, molc_precision prec, void *I);
+double *header_ptr(const molc_plan *p, molc_precision prec, void *I);
+
+// Autotuner of the FP32 sweep: times each compiled staging depth on this plan (one warm-up and three timed
+// launches of the sweep kernel each, on temporary inputs: kappa = B = boundary = 0, c = dt = 1, an FP32 state
+// initialised from B) and keeps the fastest.  The depth changes no arithmetic, only the timing.  Allocates its
+// temporaries for the duration of the call.
+molc_status autotune(molc_plan *p) {
+  DeviceGuard dg(p->device);
+  const int64_t cg = (int64_t)p->G * p->view.ncell;
+  void *I = nullptr;
+  double *in = nullptr;   // kappa, B [G][cell], bnd [4][G]
+  double *mom = nullptr;  // 6 x [G][cell]
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&I, state_bytes_fp32(p));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&in, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&mom, 6 * cg * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(in, 0, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best = p->view.sweep_depth;
+  if (e == cudaSuccess) {
+    SweepArgs a{};
+    a.kappa = in;
+    a.B = in + cg;
+    a.bnd = in + 2 * cg;
+    a.c = a.dt = 1.0;
+    a.inv_c = a.inv_cdt = 1.0;
+    a.I = I;
+    a.Bref = bref_ptr(p, MOLC_FP32, I);
+    a.scale = header_ptr(p, MOLC_FP32, I);
+    a.out = molc_moments{mom, mom + cg, mom + 2 * cg, mom + 3 * cg, mom + 4 * cg, mom + 5 * cg};
+    a.cdat = p->d_cdat;
+    a.cdB = p->d_cdB;
+    a.items = p->d_items32;
+    a.n_items = p->n_items32;
+    e = cudaMemset(I, 0, state_bytes_fp32(p));
+    if (e == cudaSuccess) e = cudaMemcpy(a.Bref, a.B, cg * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = launch_set_scale(p->view, MOLC_FP32, a.B, const_cast<double *>(a.scale), nullptr);
+    if (e == cudaSuccess) e = launch_prep(p->view, MOLC_FP32, a, nullptr);
+    float best_ms = 0;
+    for (int d : kSweepDepths) {
+      if (e != cudaSuccess) break;
+      PlanView v = p->view;
+      v.sweep_depth = d;
+      e = launch_sweep_fp32(v, a, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_sweep_fp32(v, a, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && (best_ms == 0 || ms < best_ms)) {
+        best_ms = ms;
+        best = d;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (mom) cudaFree(mom);
+  if (in) cudaFree(in);
+  if (I) cudaFree(I);
+  if (e != cudaSuccess) return cuda_fail(e, "create: autotune");
+  p->view.sweep_depth = best;
+  int code = 0;
+  cudaMemcpy(&code, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemset(p->d_status, 0, sizeof(int));   // the temporaries' checks leave no trace
+  return MOLC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -395,7 +468,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   if (groups->G < 1 || groups->G > 4096) return fail(MOLC_ERR_INVALID_ARG, "create: need 1 <= G <= 4096");
   if (!finite_pos(ray_spacing)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing must be > 0");
   if (layout != MOLC_RAYS_UNIFORM && layout != MOLC_RAYS_PAPER) return fail(MOLC_ERR_INVALID_ARG, "create: layout");
-  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY)) return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
+  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE))
+    return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
   const int n = quad->n;
   if (n < 2 || !quad->mu || !quad->cos_phi || !quad->sin_phi || !quad->w)
     return fail(MOLC_ERR_INVALID_ARG, "create: bad quadrature");
@@ -678,6 +752,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   }
   std::stable_sort(block_order.begin(), block_order.end(), [&](int x, int y) { return blen[x] > blen[y]; });
   p->bundle_slots = boff[n_blocks32];
+  p->n_blocks32 = n_blocks32;
 
   // ---- FP32 cell moments are gathered per cell from the swept state: for every cell, one entry per (track,
   // sense) segment crossing it, {item position of the (track, sense), step along that sense, A/V (f32 bits),
@@ -729,6 +804,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.n_tracks = T;
   v.n_track_segments = S;
   v.gc32 = gc32;
+  v.sweep_depth = 4;
   if (p->host_only) {
     *out = p;
     return MOLC_OK;
@@ -780,6 +856,14 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.gent = p->d_gent;
   v.boff = p->d_boff;
   v.block_order = p->d_block_order;
+  if ((flags & MOLC_AUTOTUNE) && nch32) {
+    st = autotune(p);
+    if (st != MOLC_OK) {
+      free_device(p);
+      delete p;
+      return st;
+    }
+  }
   *out = p;
   return MOLC_OK;
 }
@@ -798,6 +882,7 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->n_updates = info->n_segments * p->G;
   info->fp32_groups_per_warp = p->view.gc32;
   info->device_bytes = p->device_bytes;
+  info->fp32_sweep_depth = p->view.sweep_depth;
   return MOLC_OK;
 }
 
@@ -819,9 +904,22 @@ static double *bref_of(const molc_plan *p, molc_precision prec, void *I) {
   return (double *)((char *)I + bref_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4));
 }
 
+extern "C++" {
+namespace {
+size_t state_bytes_fp32(const molc_plan *p) { return molc_intensity_bytes(p, MOLC_FP32); }
+}  // namespace
+}
+
 static double *header_of(const molc_plan *p, molc_precision prec, void *I) {
   return (double *)((char *)I +
                     header_offset(state_elems(p, prec), prec == MOLC_FP64 ? 8 : 4, p->G, p->view.ncell));
+}
+
+extern "C++" {
+namespace {
+double *bref_ptr(const molc_plan *p, molc_precision prec, void *I) { return bref_of(p, prec, I); }
+double *header_ptr(const molc_plan *p, molc_precision prec, void *I) { return header_of(p, prec, I); }
+}  // namespace
 }
 
 static molc_status check_prec(const molc_plan *p, molc_precision prec, const char *who) {
@@ -955,6 +1053,213 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
   e = launch_finalize(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: finalize");
   return MOLC_OK;
+}
+
+}  // extern "C"
+
+struct molc_batch {
+  int device = 0;
+  std::vector<molc_plan *> plans;
+  molc::BatchInst *d_inst = nullptr;
+  std::vector<molc::BatchInst> h_inst;
+  int4 *d_prep = nullptr;
+  int n_prep = 0;
+  struct SweepClass {
+    int n_polar, depth;
+    int2 *d_map;
+    int n;
+  };
+  struct MomentClass {
+    int n_polar;
+    int4 *d_map;
+    int n;
+    size_t smem;
+  };
+  std::vector<SweepClass> sweeps;
+  std::vector<MomentClass> moments;
+  int2 *d_closure = nullptr;
+  int n_closure = 0;
+  bool bound = false;
+  bool want_closure = false;
+};
+
+namespace {
+void batch_free(molc_batch *b) {
+  DeviceGuard dg(b->device);
+  if (b->d_inst) cudaFree(b->d_inst);
+  if (b->d_prep) cudaFree(b->d_prep);
+  if (b->d_closure) cudaFree(b->d_closure);
+  for (auto &c : b->sweeps)
+    if (c.d_map) cudaFree(c.d_map);
+  for (auto &c : b->moments)
+    if (c.d_map) cudaFree(c.d_map);
+  delete b;
+}
+
+template <class T> cudaError_t upload_vec(T **dst, const std::vector<T> &v) {
+  *dst = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void **)dst, v.size() * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+}  // namespace
+
+extern "C" {
+
+molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) {
+  if (!out) return fail(MOLC_ERR_INVALID_ARG, "batch_create: out is NULL");
+  *out = nullptr;
+  if (!plans || n < 1) return fail(MOLC_ERR_INVALID_ARG, "batch_create: need n >= 1 plans");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i]) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is NULL", i);
+    if (plans[i]->host_only) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is MOLC_HOST_ONLY", i);
+    if (plans[i]->n_polar > kMaxPolarFP32 || plans[i]->n_items32 == 0)
+      return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d has no FP32 sweep (more than %d polar cosines)", i,
+                  kMaxPolarFP32);
+    if (plans[i]->device != dev) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is on another device", i);
+  }
+  auto b = new molc_batch();
+  b->device = dev;
+  b->plans.assign(plans, plans + n);
+  b->h_inst.resize(n);
+  // block maps
+  std::vector<int4> prep;
+  std::map<std::pair<int, int>, std::vector<std::pair<int, int2>>> sw;   // (np, depth) -> (length, block)
+  std::map<int, std::vector<int4>> mo;
+  std::map<int, size_t> mo_smem;
+  std::vector<int2> clo;
+  for (int i = 0; i < n; ++i) {
+    const molc_plan *p = plans[i];
+    const PlanView &v = p->view;
+    const Layout L = layout_for(v, MOLC_FP32);
+    const int n_tiles = (v.ncell + 31) / 32;
+    for (int ch = 0; ch < L.n_chunks; ++ch)
+      for (int t = 0; t < n_tiles; ++t) prep.push_back(make_int4(i, ch, t, ch == 0 && t == 0));
+    // bundle lengths from the plan's host copy of the offsets
+    std::vector<int64_t> boff(p->n_blocks32 + 1);
+    if (cudaMemcpy(boff.data(), p->d_boff, boff.size() * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      batch_free(b);
+      return fail(MOLC_ERR_CUDA, "batch_create: reading bundle offsets");
+    }
+    auto &cls = sw[{p->n_polar, v.sweep_depth}];
+    for (int64_t k = 0; k < p->n_blocks32; ++k)
+      cls.push_back({(int)(boff[k + 1] - boff[k]), make_int2(i, (int)k)});
+    auto &m = mo[p->n_polar];
+    for (int ch = 0; ch < L.n_chunks; ++ch) {
+      const int gcount = std::min(L.gc, v.G - ch * L.gc);
+      const int64_t nb = ((int64_t)v.ncell * gcount + 127) / 128;
+      for (int64_t k = 0; k < nb; ++k) m.push_back(make_int4(i, ch, (int)k, 0));
+    }
+    mo_smem[p->n_polar] = std::max(mo_smem[p->n_polar], (size_t)v.n_pairs * (3 * v.n_polar + 2) * sizeof(float));
+    for (int k = 0; k < (v.ncell + 255) / 256; ++k) clo.push_back(make_int2(i, k));
+  }
+  cudaError_t e = cudaMalloc((void **)&b->d_inst, n * sizeof(BatchInst));
+  if (e == cudaSuccess) e = upload_vec(&b->d_prep, prep);
+  b->n_prep = (int)prep.size();
+  if (e == cudaSuccess) e = upload_vec(&b->d_closure, clo);
+  b->n_closure = (int)clo.size();
+  for (auto &kv : sw) {
+    if (e != cudaSuccess) break;
+    auto &lst = kv.second;
+    std::stable_sort(lst.begin(), lst.end(), [](const std::pair<int, int2> &x, const std::pair<int, int2> &y) {
+      return x.first > y.first;   // longest bundles first, across instances
+    });
+    std::vector<int2> map(lst.size());
+    for (size_t k = 0; k < lst.size(); ++k) map[k] = lst[k].second;
+    molc_batch::SweepClass c{kv.first.first, kv.first.second, nullptr, (int)map.size()};
+    e = upload_vec(&c.d_map, map);
+    b->sweeps.push_back(c);
+  }
+  for (auto &kv : mo) {
+    if (e != cudaSuccess) break;
+    molc_batch::MomentClass c{kv.first, nullptr, (int)kv.second.size(), mo_smem[kv.first]};
+    e = upload_vec(&c.d_map, kv.second);
+    b->moments.push_back(c);
+  }
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e, "batch_create");
+  }
+  *out = b;
+  return MOLC_OK;
+}
+
+molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
+  if (!b || !args) return fail(MOLC_ERR_INVALID_ARG, "batch_bind: NULL argument");
+  bool any_f = false;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const molc_sweep_args &x = args[i];
+    const molc_plan *p = b->plans[i];
+    if (!x.kappa || !x.B || !x.I || !x.bnd || !x.out.E || !x.out.Fx || !x.out.Fy || !x.out.Nxx || !x.out.Nxy ||
+        !x.out.Nyy)
+      return fail(MOLC_ERR_INVALID_ARG, "batch_bind: instance %zu: NULL argument", i);
+    if (!finite_pos(x.c) || !finite_pos(x.dt))
+      return fail(MOLC_ERR_INVALID_ARG, "batch_bind: instance %zu: need c > 0 and dt > 0", i);
+    const bool f = x.fxx || x.fxy || x.fyy;
+    if (f && !(x.fxx && x.fxy && x.fyy))
+      return fail(MOLC_ERR_INVALID_ARG, "batch_bind: instance %zu: give all of fxx, fxy, fyy or none", i);
+    any_f |= f;
+    BatchInst &h = b->h_inst[i];
+    h.v = p->view;
+    h.L = layout_for(p->view, MOLC_FP32);
+    SweepArgs &a = h.a;
+    a = SweepArgs{};
+    a.kappa = x.kappa;
+    a.B = x.B;
+    a.bnd = x.bnd;
+    a.c = x.c;
+    a.dt = x.dt;
+    a.inv_c = 1.0 / x.c;
+    a.inv_cdt = 1.0 / (x.c * x.dt);
+    a.I = x.I;
+    a.Bref = bref_of(p, MOLC_FP32, x.I);
+    a.scale = header_of(p, MOLC_FP32, x.I);
+    a.out = x.out;
+    a.cdat = p->d_cdat;
+    a.cdB = p->d_cdB;
+    a.acc = nullptr;
+    a.items = p->d_items32;
+    a.n_items = p->n_items32;
+    h.fxx = x.fxx;
+    h.fxy = x.fxy;
+    h.fyy = x.fyy;
+  }
+  DeviceGuard dg(b->device);
+  cudaError_t e = cudaMemcpy(b->d_inst, b->h_inst.data(), b->h_inst.size() * sizeof(BatchInst),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_bind");
+  b->bound = true;
+  b->want_closure = any_f;
+  return MOLC_OK;
+}
+
+molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
+  if (!b) return fail(MOLC_ERR_INVALID_ARG, "batch_sweep: NULL batch");
+  if (!b->bound) return fail(MOLC_ERR_INVALID_ARG, "batch_sweep: no arguments bound (molc_batch_bind)");
+  DeviceGuard dg(b->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: prep");
+  for (auto &c : b->sweeps) {
+    e = launch_sweep_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.depth, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: sweep");
+  }
+  for (auto &c : b->moments) {
+    e = launch_moments_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.smem, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: moments");
+  }
+  if (b->want_closure) {
+    e = launch_closure_batch(b->d_inst, b->d_closure, b->n_closure, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: closure");
+  }
+  return MOLC_OK;
+}
+
+void molc_batch_destroy(molc_batch *b) {
+  if (b) batch_free(b);
 }
 
 molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, double *fxx, double *fxy,

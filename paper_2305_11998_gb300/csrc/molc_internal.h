@@ -64,7 +64,10 @@ struct PlanView {
   const int4 *gent;             // FP32 moments: per cell, {item position, step, A/V f32 bits, 2 pair + sense}
   const int64_t *boff;          // FP32 state: [n_blocks + 1] first step slot of each bundle
   const int *block_order;       // FP32 sweep: bundle swept by each block of the launch (longest first)
+  int sweep_depth;              // FP32 sweep: staging depth D (one of kSweepDepths; autotuned or 4)
 };
+
+constexpr int kSweepDepths[] = {3, 4, 6};   // compiled staging depths of the FP32 sweep
 
 // FP32 state, "bundle" layout: the work items (track, sense, group) of sweep block b, i.e. items
 // [128 b, 128 b + 128), own the step slots [boff[b], boff[b+1]) (boff[b+1] - boff[b] = the longest track of the
@@ -117,6 +120,14 @@ struct SweepArgs {
   int64_t n_items;
 };
 
+// One instance of a batched FP32 sweep, as the batched kernels read it (device memory).
+struct BatchInst {
+  PlanView v;
+  SweepArgs a;
+  Layout L;
+  double *fxx, *fxy, *fyy;   // Eddington factors, or all null
+};
+
 // Kernel launchers (molc_kernels.cu).  Return cudaSuccess or the launch error.
 cudaError_t launch_prep(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st);
 cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_t st);
@@ -129,6 +140,16 @@ cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *
                                   cudaStream_t st);
 cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const double *B, double *header,
                              cudaStream_t st);
+// Batched FP32 kernels: one launch each over the blocks of all instances listed in a block map
+// (prep: int4 {instance, chunk, tile, check boundary}; sweep: int2 {instance, bundle}, one launch per
+// (polar count, staging depth) class; moments: int4 {instance, chunk, block, 0}, one launch per polar count;
+// closure: int2 {instance, cell block}).
+cudaError_t launch_prep_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
+cudaError_t launch_sweep_fp32_batch(const BatchInst *inst, const int2 *map, int blocks, int n_polar, int depth,
+                                    cudaStream_t st);
+cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, int blocks, int n_polar,
+                                      size_t smem, cudaStream_t st);
+cudaError_t launch_closure_batch(const BatchInst *inst, const int2 *map, int blocks, cudaStream_t st);
 
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;

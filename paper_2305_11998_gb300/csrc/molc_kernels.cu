@@ -48,18 +48,20 @@ __device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int
 // ---------------------------------------------------------------------------------------------------------
 constexpr int kPrepCells = 32;   // cells per tile of prep_kernel
 
-// Tiles of kPrepCells cells x the groups of one chunk (blockIdx.y): [g][cell] inputs are read along cells, the
-// [chunk][cell][gc] tables are staged in shared memory and written out contiguously.
-__global__ void __launch_bounds__(128) prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
+// Tiles of kPrepCells cells x the groups of one chunk: [g][cell] inputs are read along cells, the
+// [chunk][cell][gc] tables are staged in shared memory and written out contiguously.  A block takes tiles
+// tile0, tile0 + tstride, ...; check_bnd: this block also checks the boundary values.
+__device__ __forceinline__ void prep_tiles(const PlanView &v, const SweepArgs &a, const Layout &L, int fp32,
+                                           int chunk, int tile0, int tstride, bool check_bnd) {
   __shared__ float4 t4[kPrepCells * 32];
   __shared__ float t1[kPrepCells * 32];
   const float inv_cdt_f = (float)a.inv_cdt;
   const double sc = a.scale[0];
-  const int g0 = blockIdx.y * L.gc;
+  const int g0 = chunk * L.gc;
   const int gcount = min(L.gc, v.G - g0);
   bool bad = false, range = false;
   const int n_tiles = (v.ncell + kPrepCells - 1) / kPrepCells;
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  for (int tile = tile0; tile < n_tiles; tile += tstride) {
     const int c0 = tile * kPrepCells;
     const int nc = min(kPrepCells, v.ncell - c0);
     for (int k = threadIdx.x; k < kPrepCells * gcount; k += blockDim.x) {
@@ -93,13 +95,24 @@ __global__ void __launch_bounds__(128) prep_kernel(PlanView v, SweepArgs a, Layo
       __syncthreads();
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0)
+  if (check_bnd)
     for (int i = threadIdx.x; i < 4 * v.G; i += blockDim.x) {
       bad |= bad_input(a.bnd[i]);
       range |= fp32 && !(a.bnd[i] * sc < kScaledMax);
     }
   if (bad) atomicOr(v.status, kStatusNonfinite);
   if (range && !bad) atomicOr(v.status, kStatusRange);
+}
+
+__global__ void __launch_bounds__(128) prep_kernel(PlanView v, SweepArgs a, Layout L, int fp32) {
+  prep_tiles(v, a, L, fp32, blockIdx.y, blockIdx.x, gridDim.x, blockIdx.x == 0 && blockIdx.y == 0);
+}
+
+// Batched (FP32): block j prepares tile map[j].z of chunk map[j].y of instance map[j].x.
+__global__ void __launch_bounds__(128) prep_batch_kernel(const BatchInst *inst, const int4 *map) {
+  const int4 m = map[blockIdx.x];
+  const BatchInst &b = inst[m.x];
+  prep_tiles(b.v, b.a, b.L, 1, m.y, m.z, 1 << 30, m.w != 0);
 }
 
 // ---------------------------------------------------------------------------------------------------------
@@ -314,22 +327,24 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
   return v;
 }
 
-// Software pipeline of the FP32 sweep, per thread, in rings of kSteps slots (the step loop is unrolled by kSteps
-// so that every slot index is a constant): at step s the thread
-//   - issues asynchronous copies of its previous-step deviations for step s+3 and of the cell table entry of
-//     step s+2 (whose record arrived two steps earlier) into shared memory, as one cp.async group,
+// Software pipeline of the FP32 sweep, per thread, in rings of D slots (D = staging depth, chosen per plan by
+// the autotuner; the step loop is unrolled by D so that every slot index is a constant): at step s the thread
+//   - issues asynchronous copies of its previous-step deviations for step s+D-1 and of the cell table entry of
+//     step s+D-2 (whose record arrived two steps earlier) into shared memory, as one cp.async group,
 //   - waits until the groups holding step s's deviations and table entry have landed,
 //   - computes step s and stores its new deviations to global memory,
-//   - loads the record of step s+4 into a register.
-constexpr int kSteps = 4;
-
-template <int NP>
-__global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+//   - loads the record of step s+D into a register.
+// Group accounting: the prologue commits D-1 groups (deviations of steps 0..D-2, table entries of steps
+// 0..D-3) and step s commits one; step s's deviations are in group s and its table entry in group s+1 (group s
+// for s <= D-3), so waiting until at most D-2 groups are pending is enough.
+template <int NP, int D>
+__device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle) {
+  static_assert(D >= 3, "the staging depth needs D >= 3");
+  constexpr int kSteps = D;
   __shared__ __align__(16) float sdev[kSteps][kSweepBlock * NP];
   __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
   __shared__ __align__(16) float sdB[kSteps][kSweepBlock];
   const int tid = threadIdx.x;
-  const int bundle = v.block_order[blockIdx.x];
   const int64_t item = (int64_t)bundle * kSweepBlock + tid;
   const bool live = item < a.n_items;
   const int2 it = live ? a.items[item] : make_int2(0, 0);
@@ -367,16 +382,15 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
 
-  // prologue: records of steps 0..3; groups 0, 1, 2 = {deviations 0, table 0}, {deviations 1, table 1},
-  // {deviations 2}
+  // prologue: records of steps 0..D-1; groups 0..D-2 = {deviations k, table k (k <= D-3)}
   int2 recs[kSteps];
 #pragma unroll
   for (int k = 0; k < kSteps; ++k) recs[k] = k < nseg ? ld_record(rec + k * rstep) : make_int2(0, 0);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kSteps - 1; ++k) {
     if (k < nseg) {
       copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride);
-      if (k < 2) {
+      if (k < kSteps - 2) {
         copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc);
         copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc);
       }
@@ -392,15 +406,16 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
     for (int u = 0; u < kSteps; ++u) {
       const int s = s0 + u;
       if (s < nseg) {
-        // group s+3: deviations of step s+3, table entry of step s+2
-        if (s + 3 < nseg) copy_dev_async<NP>(&sdev[(u + 3) % kSteps][tid * NP], I + 3 * stride);
-        if (s + 2 < nseg) {
-          const int c2 = recs[(u + 2) % kSteps].x;
-          copy16_async(&stab[(u + 2) % kSteps][tid], cd + (int64_t)c2 * L.gc);
-          copy4_async(&sdB[(u + 2) % kSteps][tid], cdB + (int64_t)c2 * L.gc);
+        // group s+D-1: deviations of step s+D-1, table entry of step s+D-2
+        if (s + kSteps - 1 < nseg)
+          copy_dev_async<NP>(&sdev[(u + kSteps - 1) % kSteps][tid * NP], I + (kSteps - 1) * stride);
+        if (s + kSteps - 2 < nseg) {
+          const int c2 = recs[(u + kSteps - 2) % kSteps].x;
+          copy16_async(&stab[(u + kSteps - 2) % kSteps][tid], cd + (int64_t)c2 * L.gc);
+          copy4_async(&sdB[(u + kSteps - 2) % kSteps][tid], cdB + (int64_t)c2 * L.gc);
         }
         cp_async_commit();
-        cp_async_wait<2>();   // groups up to s+1 (deviations of step s, table entry of step s) have landed
+        cp_async_wait<kSteps - 2>();   // deviations and table entry of step s have landed
         float dv[NP];
         if constexpr (NP % 4 == 0) {
 #pragma unroll
@@ -443,6 +458,19 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, Swe
   cp_async_wait<0>();
 }
 
+template <int NP, int D>
+__global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+  sweep_fp32_body<NP, D>(v, a, L, v.block_order[blockIdx.x]);
+}
+
+// Batched: block j sweeps bundle map[j].y of instance map[j].x (blocks of all instances, longest first).
+template <int NP, int D>
+__global__ void __launch_bounds__(kSweepBlock) sweep_fp32_batch_kernel(const BatchInst *inst, const int2 *map) {
+  const int2 m = map[blockIdx.x];
+  const BatchInst &b = inst[m.x];
+  sweep_fp32_body<NP, D>(b.v, b.a, b.L, m.y);
+}
+
 // FP32 path, cell moments: one thread per (chunk, cell, group), consecutive groups of a cell in consecutive
 // lanes.  The thread sums, over the (track, sense) segments crossing its cell, the swept deviations of its group
 // (NP contiguous values per segment; the lanes of a cell read one contiguous block) weighted by
@@ -463,8 +491,10 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
 // list is padded to a multiple of kGatherPad with zero-area entries of its last pair, so the batch must equal it).
 constexpr int kGatherBatch = kGatherPad;
 
+// One block: threads t0 .. t0+127 of chunk ch ((cell, group) pairs, groups fastest).
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+__device__ __forceinline__ void moments_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int ch,
+                                                  int64_t t0) {
   extern __shared__ float coef[];   // [pair][3][NP] {w, w sin, w sin^2}, then [pair][2] {cos, sin}
   float *csn = coef + 3 * NP * v.n_pairs;
   for (int i = threadIdx.x; i < v.n_pairs * NP; i += blockDim.x) {
@@ -479,10 +509,9 @@ __global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(Plan
     csn[2 * i + 1] = v.pairs[i].sf;
   }
   __syncthreads();
-  const int ch = blockIdx.y;
   const int g0 = ch * L.gc;
   const int gcount = min(L.gc, v.G - g0);
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = t0 + threadIdx.x;
   if (t >= (int64_t)v.ncell * gcount) return;
   const int cell = (int)(t / gcount), gi = (int)(t - (int64_t)cell * gcount);
   const int g = g0 + gi;
@@ -550,6 +579,20 @@ __global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(Plan
   a.Bref[idx] = B;   // the new deviations refer to this step's B
 }
 
+template <int NP>
+__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+  moments_fp32_body<NP>(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
+}
+
+// Batched: block j handles threads 128 map[j].z .. of chunk map[j].y of instance map[j].x.
+template <int NP>
+__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
+                                                                                 const int4 *map) {
+  const int4 m = map[blockIdx.x];
+  const BatchInst &b = inst[m.x];
+  moments_fp32_body<NP>(b.v, b.a, b.L, m.y, (int64_t)m.z * blockDim.x);
+}
+
 // ---------------------------------------------------------------------------------------------------------
 // finalize: cell assembly.  acc holds sum_m omega_m sum_{C(i,m)} (A/V) psibar (times Omega components);
 // the B_i part uses the geometric moments geo = sum_m omega_m sum_{C(i,m)} A/V (times Omega components).
@@ -580,9 +623,9 @@ __global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
 }
 
 // f = N / (c E) per group (Eq. 7 with the cell averages of Eq. 15); <f>_E = sum_g N_g / (c sum_g E_g).
-__global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx, double *fxy, double *fyy,
-                               double *fgrey) {
-  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void closure_cells(const PlanView &v, const molc_moments &m, double c, double *fxx,
+                                              double *fxy, double *fyy, double *fgrey, int cell0, int cstride) {
+  for (int cell = cell0; cell < v.ncell; cell += cstride) {
     double se = 0, sxx = 0, sxy = 0, syy = 0;
     for (int g = 0; g < v.G; ++g) {
       const int64_t i = (int64_t)g * v.ncell + cell;
@@ -603,6 +646,19 @@ __global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx
       fgrey[2 * (int64_t)v.ncell + cell] = syy * inv;
     }
   }
+}
+
+__global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx, double *fxy, double *fyy,
+                               double *fgrey) {
+  closure_cells(v, m, c, fxx, fxy, fyy, fgrey, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// Batched: block j closes cells 256 map[j].y .. of instance map[j].x (instances with closure outputs only).
+__global__ void __launch_bounds__(256) closure_batch_kernel(const BatchInst *inst, const int2 *map) {
+  const int2 m = map[blockIdx.x];
+  const BatchInst &b = inst[m.x];
+  if (!b.fxx) return;
+  closure_cells(b.v, b.a.out, b.a.c, b.fxx, b.fxy, b.fyy, nullptr, m.y * blockDim.x + threadIdx.x, 1 << 30);
 }
 
 // Canonical segment averages <-> deviation state: one thread per row (track, sense, step) of the layout,
@@ -694,23 +750,34 @@ cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_
   return cudaGetLastError();
 }
 
+template <int D>
+static cudaError_t sweep_fp32_depth(const PlanView &v, const SweepArgs &a, const Layout &L, dim3 grid,
+                                    cudaStream_t st) {
+  switch (v.n_polar) {
+    case 1: sweep_fp32_kernel<1, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 2: sweep_fp32_kernel<2, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 3: sweep_fp32_kernel<3, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 4: sweep_fp32_kernel<4, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 5: sweep_fp32_kernel<5, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 6: sweep_fp32_kernel<6, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 7: sweep_fp32_kernel<7, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 8: sweep_fp32_kernel<8, D><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
   const Layout L = layout_for(v, MOLC_FP32);
   const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-  const dim3 grid((unsigned)blocks), block(kSweepBlock);
-  switch (v.n_polar) {
-    case 1: sweep_fp32_kernel<1><<<grid, block, 0, st>>>(v, a, L); break;
-    case 2: sweep_fp32_kernel<2><<<grid, block, 0, st>>>(v, a, L); break;
-    case 3: sweep_fp32_kernel<3><<<grid, block, 0, st>>>(v, a, L); break;
-    case 4: sweep_fp32_kernel<4><<<grid, block, 0, st>>>(v, a, L); break;
-    case 5: sweep_fp32_kernel<5><<<grid, block, 0, st>>>(v, a, L); break;
-    case 6: sweep_fp32_kernel<6><<<grid, block, 0, st>>>(v, a, L); break;
-    case 7: sweep_fp32_kernel<7><<<grid, block, 0, st>>>(v, a, L); break;
-    case 8: sweep_fp32_kernel<8><<<grid, block, 0, st>>>(v, a, L); break;
+  const dim3 grid((unsigned)blocks);
+  switch (v.sweep_depth) {
+    case 3: return sweep_fp32_depth<3>(v, a, L, grid, st);
+    case 4: return sweep_fp32_depth<4>(v, a, L, grid, st);
+    case 6: return sweep_fp32_depth<6>(v, a, L, grid, st);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st) {
@@ -751,6 +818,74 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
                            double *fyy, double *f_grey, cudaStream_t st) {
   closure_kernel<<<grid_for(v.ncell, 256), 256, 0, st>>>(v, m, c, fxx, fxy, fyy, f_grey);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  prep_batch_kernel<<<blocks, 128, 0, st>>>(inst, map);
+  return cudaGetLastError();
+}
+
+template <int D>
+static cudaError_t sweep_fp32_batch_depth(const BatchInst *inst, const int2 *map, int blocks, int n_polar,
+                                          cudaStream_t st) {
+  switch (n_polar) {
+    case 1: sweep_fp32_batch_kernel<1, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 2: sweep_fp32_batch_kernel<2, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 3: sweep_fp32_batch_kernel<3, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 4: sweep_fp32_batch_kernel<4, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 5: sweep_fp32_batch_kernel<5, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 6: sweep_fp32_batch_kernel<6, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 7: sweep_fp32_batch_kernel<7, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    case 8: sweep_fp32_batch_kernel<8, D><<<blocks, kSweepBlock, 0, st>>>(inst, map); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp32_batch(const BatchInst *inst, const int2 *map, int blocks, int n_polar, int depth,
+                                    cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  switch (depth) {
+    case 3: return sweep_fp32_batch_depth<3>(inst, map, blocks, n_polar, st);
+    case 4: return sweep_fp32_batch_depth<4>(inst, map, blocks, n_polar, st);
+    case 6: return sweep_fp32_batch_depth<6>(inst, map, blocks, n_polar, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, int blocks, int n_polar,
+                                      size_t smem, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  if (smem > kMaxGatherSmem) return cudaErrorInvalidConfiguration;
+  switch (n_polar) {
+#define MOLC_MOMENTS_B(NP)                                                                                     \
+  case NP:                                                                                                     \
+    if (smem > 48 * 1024) {                                                                                    \
+      cudaError_t e = cudaFuncSetAttribute(moments_fp32_batch_kernel<NP>,                                      \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);            \
+      if (e != cudaSuccess) return e;                                                                          \
+    }                                                                                                          \
+    moments_fp32_batch_kernel<NP><<<blocks, 128, smem, st>>>(inst, map);                                       \
+    break;
+    MOLC_MOMENTS_B(1)
+    MOLC_MOMENTS_B(2)
+    MOLC_MOMENTS_B(3)
+    MOLC_MOMENTS_B(4)
+    MOLC_MOMENTS_B(5)
+    MOLC_MOMENTS_B(6)
+    MOLC_MOMENTS_B(7)
+    MOLC_MOMENTS_B(8)
+#undef MOLC_MOMENTS_B
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_closure_batch(const BatchInst *inst, const int2 *map, int blocks, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  closure_batch_kernel<<<blocks, 256, 0, st>>>(inst, map);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ FP64, FP32 = 0, 1
 RAYS_UNIFORM, RAYS_PAPER = 0, 1
 AREA_RENORM = 1
 HOST_ONLY = 2
+AUTOTUNE = 4
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 LAYOUT = {"uniform": RAYS_UNIFORM, "paper": RAYS_PAPER, RAYS_UNIFORM: RAYS_UNIFORM, RAYS_PAPER: RAYS_PAPER}
 STATUS = {0: "MOLC_OK", 1: "MOLC_ERR_INVALID_ARG", 2: "MOLC_ERR_OUT_OF_MEMORY", 3: "MOLC_ERR_CUDA",
@@ -29,7 +30,8 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_intensity_bytes", "molc_intensity_init", "molc_sweep", "molc_closure", "molc_intensity_export",
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
-            "molc_kernel_time_parts")
+            "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
+            "molc_batch_destroy")
 
 
 class MolcError(RuntimeError):
@@ -60,7 +62,13 @@ class _Info(C.Structure):
     _fields_ = [("G", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_dir", C.c_int), ("n_azim_pairs", C.c_int),
                 ("n_polar", C.c_int), ("n_tracks", C.c_int64), ("n_track_segments", C.c_int64),
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int)]
+
+
+class _SweepArgs(C.Structure):
+    _fields_ = [("kappa", C.c_void_p), ("B", C.c_void_p), ("c", C.c_double), ("dt", C.c_double),
+                ("I", C.c_void_p), ("bnd", C.c_void_p), ("out", _Moments), ("fxx", C.c_void_p),
+                ("fxy", C.c_void_p), ("fyy", C.c_void_p)]
 
 
 _lib = None
@@ -96,6 +104,10 @@ def load(build_if_needed: bool = True):
         "molc_kernel_time_parts": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_device_status": (C.c_int, [vp, ip]),
         "molc_last_error": (C.c_char_p, []),
+        "molc_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
+        "molc_batch_bind": (C.c_int, [vp, C.POINTER(_SweepArgs)]),
+        "molc_batch_sweep": (C.c_int, [vp, vp]),
+        "molc_batch_destroy": (None, [vp]),
         "molc_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -152,13 +164,14 @@ class PlanInfo:
     n_updates: int
     fp32_groups_per_warp: int
     device_bytes: int
+    fp32_sweep_depth: int
 
 
 class Plan:
     """molc_create / molc_sweep / molc_closure on torch tensors (float64, CUDA, contiguous)."""
 
     def __init__(self, nx, ny, lx, ly, mu, cos_phi, sin_phi, w, G, spacing, layout="uniform", renorm=True,
-                 x0=0.0, y0=0.0, edges=None, host_only=False):
+                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False):
         lib = load()
         self._lib = lib
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, cos_phi, sin_phi, w)]
@@ -168,7 +181,8 @@ class Plan:
         groups = _Groups(G, _dp(e) if e is not None else None)
         h = C.c_void_p()
         _check(lib.molc_create(C.byref(grid), C.byref(quad), C.byref(groups), float(spacing), LAYOUT[layout],
-                               (AREA_RENORM if renorm else 0) | (HOST_ONLY if host_only else 0), C.byref(h)))
+                               (AREA_RENORM if renorm else 0) | (HOST_ONLY if host_only else 0) |
+                               (AUTOTUNE if autotune else 0), C.byref(h)))
         self._h = h
         inf = _Info()
         _check(lib.molc_plan_get_info(h, C.byref(inf)))
@@ -177,10 +191,12 @@ class Plan:
         self.ncell = nx * ny
 
     @classmethod
-    def from_workload(cls, wl, quad=None, spacing=None, layout="uniform", renorm=True, host_only=False):
+    def from_workload(cls, wl, quad=None, spacing=None, layout="uniform", renorm=True, host_only=False,
+                      autotune=False):
         q = quad if quad is not None else wl.quadrature()
         return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G,
-                   wl.spacing if spacing is None else spacing, layout, renorm, edges=wl.edges(), host_only=host_only)
+                   wl.spacing if spacing is None else spacing, layout, renorm, edges=wl.edges(), host_only=host_only,
+                   autotune=autotune)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -289,3 +305,43 @@ class Plan:
                                             d["entry"].ctypes.data_as(ip), d["cell"].ctypes.data_as(ip),
                                             _dp(d["len"]), _dp(d["area"])))
         return d
+
+
+class Batch:
+    """molc_batch_*: one batched FP32 step over many plans (instances) on one device."""
+
+    def __init__(self, plans):
+        self._lib = load()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = C.c_void_p()
+        _check(self._lib.molc_batch_create(arr, len(self.plans), C.byref(h)))
+        self._h = h
+        self._args = None
+
+    def bind(self, args):
+        """args: one dict per instance with kappa, B, c, dt, I, bnd, out (moments dict) and optionally f
+        (dict fxx, fxy, fyy)."""
+        arr = (_SweepArgs * len(self.plans))()
+        for i, a in enumerate(args):
+            f = a.get("f")
+            arr[i] = _SweepArgs(_ptr(a["kappa"]), _ptr(a["B"]), float(a["c"]), float(a["dt"]), _ptr(a["I"]),
+                                _ptr(a["bnd"]), _Moments(*[a["out"][k].data_ptr() for k in MOMENTS]),
+                                *([_ptr(f["fxx"]), _ptr(f["fxy"]), _ptr(f["fyy"])] if f else [None] * 3))
+        _check(self._lib.molc_batch_bind(self._h, arr))
+        self._args = args     # keep the tensors alive while bound
+
+    def sweep(self, stream=None):
+        _check(self._lib.molc_batch_sweep(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.molc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

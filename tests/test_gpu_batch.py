@@ -1,0 +1,139 @@
+"""GPU: batched FP32 sweep over uneven instances (one launch per kernel class), CUDA-graph replay, autotuner.
+
+The batched kernels run the same per-instance arithmetic as molc_sweep + molc_closure, and the FP32 path is
+deterministic (no atomics), so every result is compared bit for bit with the per-instance calls; the
+per-instance path itself is checked against the oracle in test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def molc():
+    import paper_2305_11998_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+# uneven instances: cells per side, groups, polar x azimuthal directions, ray spacing h/div (three polar classes,
+# G = 37 spans two group chunks)
+SHAPES = [(16, 4, 2, 16, 2), (24, 17, 3, 24, 4), (32, 8, 4, 32, 2), (12, 32, 2, 16, 4), (20, 37, 4, 16, 2),
+          (8, 17, 3, 8, 2)]
+
+
+def make_instances(molc, autotune=False):
+    out = []
+    for i, (n, G, npol, naz, div) in enumerate(SHAPES):
+        wl = synth.Workload(f"b{i}", n, n, 6.0, G, 0.001, 100.0, npol, naz, div, 1)
+        d = wl.inputs(10 + i)
+        P = molc.Plan.from_workload(wl, autotune=autotune)
+        out.append((wl, d, P))
+    return out
+
+
+def new_args(P, wl, d, closure):
+    B = dev(d["B"])
+    I = P.new_intensity("fp32").zero_()
+    P.intensity_init("fp32", I, B)
+    a = dict(kappa=dev(d["kappa"]), B=B, c=d["c"], dt=d["dt"], I=I, bnd=dev(d["bnd"]), out=P.new_moments())
+    if closure:
+        a["f"] = {k: torch.empty((wl.G, wl.ncell), dtype=torch.float64, device="cuda") for k in ("fxx", "fxy", "fyy")}
+    return a
+
+
+def per_instance_step(P, a):
+    P.sweep("fp32", a["kappa"], a["B"], a["c"], a["dt"], a["I"], a["bnd"], out=a["out"])
+    if "f" in a:
+        f = P.closure(a["out"], a["c"])
+        for k in ("fxx", "fxy", "fyy"):
+            a["f"][k].copy_(f[k])
+
+
+def assert_same(a, b):
+    assert torch.equal(a["I"], b["I"])
+    for k in a["out"]:
+        assert torch.equal(a["out"][k], b["out"][k]), k
+    if "f" in a:
+        for k in a["f"]:
+            assert torch.equal(a["f"][k], b["f"][k]), k
+
+
+def test_batch_matches_per_instance(molc):
+    inst = make_instances(molc)
+    ref = [new_args(P, wl, d, closure=(i % 2 == 0)) for i, (wl, d, P) in enumerate(inst)]
+    got = [new_args(P, wl, d, closure=(i % 2 == 0)) for i, (wl, d, P) in enumerate(inst)]
+    batch = molc.Batch([P for _, _, P in inst])
+    batch.bind(got)
+    for _ in range(3):
+        for (wl, d, P), a in zip(inst, ref):
+            per_instance_step(P, a)
+        batch.sweep()
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        assert_same(a, b)
+    for _, _, P in inst:
+        assert P.device_status() == 0
+    batch.close()
+
+
+def test_batch_steps_replayed_from_a_cuda_graph(molc):
+    inst = make_instances(molc)
+    eager = [new_args(P, wl, d, closure=True) for wl, d, P in inst]
+    graph = [new_args(P, wl, d, closure=True) for wl, d, P in inst]
+    be = molc.Batch([P for _, _, P in inst])
+    be.bind(eager)
+    bg = molc.Batch([P for _, _, P in inst])
+    bg.bind(graph)
+    # two steps per graph, replayed twice = four steps
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bg.sweep()
+        bg.sweep()
+    for _ in range(2):
+        g.replay()
+    for _ in range(4):
+        be.sweep()
+    torch.cuda.synchronize()
+    for a, b in zip(graph, eager):
+        assert_same(a, b)
+    be.close()
+    bg.close()
+
+
+def test_autotuned_plans_give_identical_results(molc):
+    base = make_instances(molc)[:3]
+    tuned = make_instances(molc, autotune=True)[:3]
+    for (wl, d, P), (_, _, Q) in zip(base, tuned):
+        assert Q.info.fp32_sweep_depth in (3, 4, 6)
+        assert P.info.fp32_sweep_depth == 4
+        a = new_args(P, wl, d, closure=False)
+        b = new_args(Q, wl, d, closure=False)
+        for _ in range(2):
+            per_instance_step(P, a)
+            per_instance_step(Q, b)
+        torch.cuda.synchronize()
+        assert_same(a, b)
+        assert Q.device_status() == 0
+
+
+def test_batch_rejects_bad_arguments(molc):
+    inst = make_instances(molc)[:2]
+    batch = molc.Batch([P for _, _, P in inst])
+    with pytest.raises(molc.MolcError):
+        batch.sweep()                         # nothing bound yet
+    args = [new_args(P, wl, d, closure=False) for wl, d, P in inst]
+    args[1]["c"] = -1.0
+    with pytest.raises(molc.MolcError):
+        batch.bind(args)
+    batch.close()
