@@ -345,10 +345,106 @@ def run_kernel_only(args):
     P.close()
 
 
+def run_batch(args):
+    """The batched production pattern: 64 seeded uneven instances (cells per side 32-256, 8/17/32 groups, 2-4
+    polar x 16-64 azimuthal directions, spacing h/2 or h/4), autotuned plans, all instances stepped by one
+    molc_batch_sweep per step (sweep + Eddington factors), the K timed steps captured in one CUDA graph and
+    replayed once.  Compared with looping the per-instance FP32 sweep and the plain FP64 sweep over the
+    instances."""
+    import torch
+    import paper_2305_11998_gb300 as molc
+    dev = torch.device("cuda")
+    wls = synth.batch_instances(64)
+    t0 = time.perf_counter()
+    plans = [molc.Plan.from_workload(wl, autotune=True) for wl in wls]
+    t_plan = time.perf_counter() - t0
+    n_upd = sum(P.info.n_updates for P in plans)
+    args_list, inputs = [], []
+    for wl, P in zip(wls, plans):
+        d = wl.inputs(seed=wl.extra["seed"])
+        k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
+        I = P.new_intensity("fp32", dev)
+        P.intensity_init("fp32", I, B)
+        f = {x: torch.empty((wl.G, wl.ncell), dtype=torch.float64, device=dev) for x in ("fxx", "fxy", "fyy")}
+        args_list.append(dict(kappa=k, B=B, c=d["c"], dt=d["dt"], I=I, bnd=bnd, out=P.new_moments(dev), f=f))
+        inputs.append(d)
+    batch = molc.Batch(plans)
+    batch.bind(args_list)
+    for _ in range(max(args.warmup, 0)):
+        batch.sweep()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(args.steps):
+            batch.sweep()
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    status = max(P.device_status() for P in plans)
+    # the same steps as per-instance calls (FP32 sweep + closure per plan, no batching, no graph)
+    e0.record()
+    for _ in range(2):
+        for P, a in zip(plans, args_list):
+            P.sweep("fp32", a["kappa"], a["B"], a["c"], a["dt"], a["I"], a["bnd"], out=a["out"])
+            P.closure(a["out"], a["c"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_loop32 = e0.elapsed_time(e1) / 2
+    # the plain FP64 sweep looped over the instances (FP32 states released first)
+    for a in args_list:
+        a["I"] = None
+    batch.close()
+    del g
+    torch.cuda.empty_cache()
+    I64 = [P.new_intensity("fp64", dev) for P in plans]
+    for P, a, I in zip(plans, args_list, I64):
+        P.intensity_init("fp64", I, a["B"])
+        P.sweep("fp64", a["kappa"], a["B"], a["c"], a["dt"], I, a["bnd"], out=a["out"])
+    torch.cuda.synchronize()
+    e0.record()
+    for P, a, I in zip(plans, args_list, I64):
+        P.sweep("fp64", a["kappa"], a["B"], a["c"], a["dt"], I, a["bnd"], out=a["out"])
+        P.closure(a["out"], a["c"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    depths = {}
+    for P in plans:
+        depths[P.info.fp32_sweep_depth] = depths.get(P.info.fp32_sweep_depth, 0) + 1
+    line = {"metric": METRIC, "value": n_upd * args.steps / (ms / 1e3), "unit": "updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64: 64 seeded uneven instances, cells per side 32-256, 8/17/32 groups, "
+                                   "2-4 x 16-64 directions, spacing h/2 or h/4",
+                       "updates_per_step": n_upd, "step": "molc_batch_sweep (FP32 sweep + Eddington factors), "
+                                                          "K steps in one CUDA graph",
+                       "state_gb": sum(P.intensity_bytes("fp32") for P in plans) / 1e9,
+                       "plan_seconds_with_autotune": t_plan, "autotuned_depths": depths},
+            "per_instance_fp32": {"value": n_upd / (ms_loop32 / 1e3), "ms_per_step": ms_loop32},
+            "fp64_plain_loop": {"value": n_upd / (ms64 / 1e3), "ms_per_step": ms64,
+                                "speedup_batch_over_fp64_loop": ms64 / (ms / args.steps)},
+            "clocks": clocks, "device_status": status}
+    print(json.dumps(line), flush=True)
+    for P in plans:
+        P.close()
+
+
 def main():
     args = parse()
     if args.kernel_only:
         run_kernel_only(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
