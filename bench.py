@@ -314,7 +314,7 @@ def run_ours(args):
                            "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
                            "step": "molc_sweep (FP32) + molc_closure"},
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 4 * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
+                "gpu_launches": 5 * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
         print(json.dumps(line), flush=True)
     P.close()
     if ws > 1:
@@ -439,10 +439,55 @@ def run_batch(args):
         P.close()
 
 
+def run_refine(args):
+    """Refinement stress: 128x128 cells, 17 groups, 8 polar x 64 azimuthal directions, cold start with the left
+    edge driven at 1 keV; the material grid is fixed while the ray spacing goes h/2, h/4, h/8, h/16.  T is
+    advanced between steps by the host FP64 energy balance driven by the FP64 sweep at h/2; at every spacing the
+    FP32 and FP64 sweeps step through that same T sequence.  Reports, per spacing, the FP32 and FP64 sweep
+    throughput and the largest FP32 error against FP64 over the steps."""
+    import torch
+    import paper_2305_11998_gb300 as molc
+    from paper_2305_11998_gb300 import multistep
+    wl = synth.WORKLOADS["fc128_g17_d512"]
+    steps = min(args.steps, wl.steps)
+    t0 = time.perf_counter()
+    Pref = molc.Plan.from_workload(wl)
+    Ts = multistep.temperature_sequence(Pref, wl, wl.temperature(), steps)
+    t_seq = time.perf_counter() - t0
+    Pref.close()
+    rows = []
+    for div in (2, 4, 8, 16):
+        P = molc.Plan.from_workload(wl, spacing=wl.h / div, autotune=True)
+        n_upd = P.info.n_updates
+        t32, t64 = [], []
+        m64 = multistep.run_sequence(P, wl, Ts, "fp64", on_step=lambda n, m, ms: t64.append(ms))
+        torch.cuda.empty_cache()
+        m32 = multistep.run_sequence(P, wl, Ts, "fp32", on_step=lambda n, m, ms: t32.append(ms))
+        worst = {}
+        for a, b in zip(m32, m64):
+            for k, v in multistep.precision_errors(a, b, wl.c).items():
+                worst[k] = max(worst.get(k, 0.0), v)
+        ms32 = float(np.median(t32[1:] if len(t32) > 1 else t32))
+        ms64 = float(np.median(t64[1:] if len(t64) > 1 else t64))
+        rows.append({"spacing": f"h/{div}", "updates_per_step": n_upd, "fp32_ms": ms32, "fp32_updates_per_s": n_upd / (ms32 / 1e3),
+                     "fp64_ms": ms64, "fp64_updates_per_s": n_upd / (ms64 / 1e3), "speedup": ms64 / ms32,
+                     "fp32_vs_fp64_max_error": worst, "fp32_sweep_depth": P.info.fp32_sweep_depth,
+                     "device_status": P.device_status()})
+        P.close()
+        torch.cuda.empty_cache()
+    T = Ts[-1]
+    print(json.dumps({"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, {wl.n_polar}x{wl.n_azim} "
+                                  f"directions, cold start, left edge at 1 keV, {steps} steps",
+                      "temperature_sequence_seconds": t_seq, "T_range_keV": [float(T.min()), float(T.max())],
+                      "per_spacing": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.kernel_only:
         run_kernel_only(args)
+    elif args.workload == "refine":
+        run_refine(args)
     elif args.workload == "batch64":
         run_batch(args)
     elif args.impl == "reference":

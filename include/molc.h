@@ -39,9 +39,9 @@ typedef enum {
   MOLC_ERR_NONFINITE_INPUT = 4,  /* device status: kappa, B or the boundary held NaN/Inf or a negative value */
   MOLC_ERR_TIMEOUT = 5,          /* reserved: a bounded device wait gave up */
   MOLC_ERR_INTERNAL = 6,
-  MOLC_ERR_RANGE = 7             /* device status: B or the boundary exceeds the range of an FP32 state (its
-                                    power-of-two scale is set by molc_intensity_init from max B, with 2^24
-                                    headroom) */
+  MOLC_ERR_RANGE = 7             /* device status: a scaled value exceeds the range of an FP32 state (cannot
+                                    happen for finite inputs: the state's power-of-two scale follows
+                                    max(B, boundary) at every sweep) */
 } molc_status;
 
 typedef enum { MOLC_FP64 = 0, MOLC_FP32 = 1 } molc_precision;
@@ -124,9 +124,10 @@ molc_status molc_plan_get_info(const molc_plan *plan, molc_plan_info *info);
 /* The opaque intensity state I^{n-1} of one precision: one element per (segment, direction, group) (FP64: 8
  * bytes, FP32: 4, laid out for the sweep kernel with a little padding) holding the deviation of the segment
  * average from the cell's Planck intensity, followed by that reference Planck intensity per (group, cell) in
- * FP64 and a small header.  The FP32 state works in units
- * scaled by a power of two (chosen by molc_intensity_init so that max B maps near 2^100), which keeps
- * intensities down to ~1e-68 of max B in the normal FP32 range.  molc_intensity_count gives the elements,
+ * FP64 and a small header.  The FP32 state works in units scaled by a power of two that maps max(B, boundary)
+ * near 2^100 (set by molc_intensity_init from B, and reset by any sweep whose max(B, boundary) has moved by more
+ * than ~2^8 from it, the stored deviations being rescaled exactly as they are read), which keeps intensities down
+ * to ~1e-68 of that maximum in the normal FP32 range.  molc_intensity_count gives the elements,
  * molc_intensity_bytes the bytes to allocate (256-byte aligned device memory).  The layout is private to the
  * library; use export/import to read or write segment averages. */
 int64_t molc_intensity_count(const molc_plan *plan);

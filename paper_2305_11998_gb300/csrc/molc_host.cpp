@@ -975,6 +975,9 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   if (prec == MOLC_FP64) {   // the FP32 path gathers its moments and has no accumulators
     e = cudaMemsetAsync(p->d_acc, 0, (size_t)p->G * p->view.ncell * kOutputs * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
+  } else {
+    e = launch_update_scale(p->view, B, bnd, header_of(p, prec, I), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep: scale");
   }
   const bool timed = p->timing && p->n_timed < kMaxTimed;
   cudaEvent_t *ev = timed ? &p->ev[4 * (size_t)p->n_timed] : nullptr;
@@ -1045,6 +1048,9 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
   if (prec == MOLC_FP64) {
     e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
+  } else {
+    e = launch_update_scale(p->view, B, bnd, header_of(p, prec, I), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: scale");
   }
   e = launch_prep(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: prep");
@@ -1241,7 +1247,9 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
   if (!b->bound) return fail(MOLC_ERR_INVALID_ARG, "batch_sweep: no arguments bound (molc_batch_bind)");
   DeviceGuard dg(b->device);
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
+  cudaError_t e = launch_update_scale_batch(b->d_inst, (int)b->plans.size(), st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: scale");
+  e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: prep");
   for (auto &c : b->sweeps) {
     e = launch_sweep_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.depth, st);

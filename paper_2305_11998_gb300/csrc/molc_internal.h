@@ -97,7 +97,7 @@ inline Layout layout_for(const PlanView &v, molc_precision prec) {
 }
 
 // Byte offset of the reference Planck block inside an intensity state of `count` elements of `esize` bytes,
-// and of the header after it: {scale, 1/scale, scratch (max B bits)}.
+// and of the header after it: {scale, 1/scale, scratch (max bits), factor to this step's scale, block count}.
 inline size_t bref_offset(int64_t count, int esize) { return ((size_t)count * esize + 255) / 256 * 256; }
 inline size_t header_offset(int64_t count, int esize, int G, int ncell) {
   return bref_offset(count, esize) + ((size_t)G * ncell * 8 + 255) / 256 * 256;
@@ -144,6 +144,10 @@ cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const doubl
 // (prep: int4 {instance, chunk, tile, check boundary}; sweep: int2 {instance, bundle}, one launch per
 // (polar count, staging depth) class; moments: int4 {instance, chunk, block, 0}, one launch per polar count;
 // closure: int2 {instance, cell block}).
+// Sweep-time scale update of an FP32 state from max(B, boundary) (see update_scale in molc_kernels.cu).
+cudaError_t launch_update_scale(const PlanView &v, const double *B, const double *bnd, double *header,
+                                cudaStream_t st);
+cudaError_t launch_update_scale_batch(const BatchInst *inst, int n, cudaStream_t st);
 cudaError_t launch_prep_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
 cudaError_t launch_sweep_fp32_batch(const BatchInst *inst, const int2 *map, int blocks, int n_polar, int depth,
                                     cudaStream_t st);

@@ -381,6 +381,7 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   // entering intensity (scaled), split like B so that I_in - B keeps the precision of the difference
   const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
+  const float rescale = (float)a.scale[3];   // power of two: the stored deviations to this step's scale
 
   // prologue: records of steps 0..D-1; groups 0..D-2 = {deviations k, table k (k <= D-3)}
   int2 recs[kSteps];
@@ -430,6 +431,8 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
           for (int p = 0; p < NP; ++p) dv[p] = sdev[u][tid * NP + p];
         }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) dv[p] *= rescale;
         const float4 q = stab[u][tid];
         const float dB = sdB[u][tid];
         // step s
@@ -512,6 +515,7 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   const int g0 = ch * L.gc;
   const int gcount = min(L.gc, v.G - g0);
   const int64_t t = t0 + threadIdx.x;
+  if (ch == 0 && t == 0) const_cast<double *>(a.scale)[3] = 1.0;   // the state is in this step's scale now
   if (t >= (int64_t)v.ncell * gcount) return;
   const int cell = (int)(t / gcount), gi = (int)(t - (int64_t)cell * gcount);
   const int g = g0 + gi;
@@ -721,6 +725,91 @@ __global__ void set_scale_kernel(const unsigned long long *mx, double *header, i
   }
   header[0] = s;
   header[1] = 1.0 / s;
+  header[3] = 1.0;
+  reinterpret_cast<unsigned long long *>(header)[2] = 0;   // the sweep-time reduction starts from zero
+  reinterpret_cast<unsigned int *>(header + 4)[0] = 0;     // and with no block counted
+}
+
+// Sweep-time scale of an FP32 state: the scale follows max(B, boundary) so that the largest scaled intensity
+// stays near 2^100.  It is kept while that maximum, scaled, has its exponent in [93, 108]; otherwise it is reset
+// to 2^(100 - e), max = f 2^e.  header[3] = new scale / old scale (a power of two) is the factor by which this
+// step's sweep multiplies the stored deviations as it reads them; the moment kernel sets it back to 1.
+__device__ __forceinline__ void update_scale(unsigned long long mbits, double *header) {
+  const double m = __longlong_as_double((long long)mbits);
+  const double s = header[0];
+  double f = 1.0;
+  if (m > 0.0 && isfinite(m)) {
+    int em = 0, es = 0;
+    frexp(m, &em);
+    frexp(s, &es);
+    const int e = em + es - 1;   // exponent of m * s (s is a power of two)
+    if (e < 93 || e > 108) {
+      const double sn = ldexp(1.0, kScaleTargetExp - em);
+      f = sn / s;
+      header[0] = sn;
+      header[1] = 1.0 / sn;
+    }
+  }
+  header[3] = f;
+}
+
+// One launch: every block folds its share of B (block 0 also the boundary) into header[2] by atomicMax; the
+// last block to finish (counted in header[4]) updates the scale and leaves both words at zero for the next call.
+__global__ void __launch_bounds__(256) update_scale_kernel(const double *B, int64_t n, const double *bnd, int nb,
+                                                         double *header) {
+  __shared__ unsigned long long red[8];
+  unsigned long long *mx = reinterpret_cast<unsigned long long *>(header + 2);
+  unsigned int *cnt = reinterpret_cast<unsigned int *>(header + 4);
+  unsigned long long m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = B[i];
+    if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
+  }
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const double x = bnd[i];
+      if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    if (m) atomicMax(mx, m);
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == gridDim.x - 1) {   // last block: every other block's maximum is in place
+      __threadfence();
+      const unsigned long long all = atomicMax(mx, 0ull);
+      update_scale(all, header);
+      *mx = 0;
+      *cnt = 0;
+    }
+  }
+}
+
+// Batched: one block per instance reduces max(B, boundary) and updates that instance's scale.
+__global__ void __launch_bounds__(256) update_scale_batch_kernel(const BatchInst *inst) {
+  __shared__ unsigned long long red[8];
+  const BatchInst &b = inst[blockIdx.x];
+  const int64_t n = (int64_t)b.v.G * b.v.ncell;
+  unsigned long long m = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double x = b.a.B[i];
+    if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
+  }
+  for (int i = threadIdx.x; i < 4 * b.v.G; i += blockDim.x) {
+    const double x = b.a.bnd[i];
+    if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    update_scale(m, const_cast<double *>(b.a.scale));
+  }
 }
 
 int grid_for(int64_t n, int block) {
@@ -818,6 +907,19 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
                            double *fyy, double *f_grey, cudaStream_t st) {
   closure_kernel<<<grid_for(v.ncell, 256), 256, 0, st>>>(v, m, c, fxx, fxy, fyy, f_grey);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_scale(const PlanView &v, const double *B, const double *bnd, double *header,
+                                cudaStream_t st) {
+  const int64_t n = (int64_t)v.G * v.ncell;
+  update_scale_kernel<<<std::min(grid_for(n, 256), 152 * 4), 256, 0, st>>>(B, n, bnd, 4 * v.G, header);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_scale_batch(const BatchInst *inst, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  update_scale_batch_kernel<<<n, 256, 0, st>>>(inst);
   return cudaGetLastError();
 }
 
