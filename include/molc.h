@@ -222,6 +222,17 @@ void molc_batch_destroy(molc_batch *batch);
 molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c, double *fxx, double *fxy,
                          double *fyy, double *f_grey, molc_stream stream);
 
+/* Spectrum-averaged coefficients of the effective grey problem (Sec. 2, Eqs. 8-9), per cell from the group
+ * moments and opacities:
+ *   out[0] = <kappa>_E = sum_g kappa_g E_g / sum_g E_g,
+ *   out[1] = <kappa>_B = sum_g kappa_g B_g / sum_g B_g (the emission average of the grey energy balance, Eq. 6),
+ *   out[2], out[3] = K_R = diag(<kappa>_|Fx|, <kappa>_|Fy|), <u>_|Fa| = sum_g u_g |F_a,g| / sum_g |F_a,g|,
+ *   out[4], out[5] = eta = sum_g (kappa_g - K_R) F_g / sum_g E_g (x and y components).
+ * m: device moments [G][cell] (E, Fx, Fy used); kappa, B: device [G][cell]; out: device [6][cell] FP64.  A
+ * cell whose denominator is zero gets 0.  Asynchronous on `stream`. */
+molc_status molc_grey_coefficients(const molc_plan *plan, const molc_moments *m, const double *kappa,
+                                   const double *B, double *out, molc_stream stream);
+
 /* Canonical intensity layout: [n_segments][g_count] FP64 segment averages, direction-major in quadrature
  * order; within a direction, characteristics by increasing offset along (-sin phi, cos phi) and segments in
  * traversal order.  export: canon := I (groups g_begin .. g_begin+g_count-1).  import: I := canon for the same

@@ -184,3 +184,22 @@ def closure(E, Nxx, Nxy, Nyy, c):
 
 def real_bits(precision: str) -> int:
     return _load().oracle_real_bits(PREC[precision])
+
+
+def grey_coefficients(E, Fx, Fy, kappa, B):
+    """Spectrum averages of the effective grey problem (Sec. 2, Eqs. 8-9) per cell, from [G][ncell] arrays:
+    <kappa>_E = sum kappa E / sum E, <kappa>_B = sum kappa B / sum B, K_R = diag(<kappa>_|Fx|, <kappa>_|Fy|)
+    with <u>_|F| = sum u |F| / sum |F|, and eta = sum (kappa - K_R) F / sum E.  Zero where a denominator is zero."""
+    E, Fx, Fy, kappa, B = (np.asarray(a, dtype=np.float64) for a in (E, Fx, Fy, kappa, B))
+
+    def avg(w):
+        den = w.sum(0)
+        return np.where(den > 0, (kappa * w).sum(0) / np.where(den > 0, den, 1.0), 0.0)
+
+    kE, kB, kx, ky = avg(E), avg(B), avg(np.abs(Fx)), avg(np.abs(Fy))
+    se = E.sum(0)
+    safe = np.where(se > 0, se, 1.0)
+    ex = np.where(se > 0, ((kappa - kx) * Fx).sum(0) / safe, 0.0)
+    ey = np.where(se > 0, ((kappa - ky) * Fy).sum(0) / safe, 0.0)
+    return dict(kappa_E=kE, kappa_B=kB, KRx=kx, KRy=ky, eta_x=ex, eta_y=ey)
+

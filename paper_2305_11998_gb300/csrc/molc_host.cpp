@@ -1281,6 +1281,17 @@ molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, do
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "closure");
 }
 
+molc_status molc_grey_coefficients(const molc_plan *p, const molc_moments *m, const double *kappa, const double *B,
+                                   double *out, molc_stream stream) {
+  if (!p || !m || !m->E || !m->Fx || !m->Fy || !kappa || !B || !out)
+    return fail(MOLC_ERR_INVALID_ARG, "grey_coefficients: NULL argument");
+  if (p->host_only)
+    return fail(MOLC_ERR_INVALID_ARG, "grey_coefficients: the plan was created with MOLC_HOST_ONLY");
+  DeviceGuard dg(p->device);
+  cudaError_t e = launch_grey(p->view, *m, kappa, B, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "grey_coefficients");
+}
+
 static molc_status intensity_copy(const molc_plan *p, molc_precision prec, void *I, int g_begin, int g_count,
                                   double *canon, const double *B, bool to_canon, molc_stream stream,
                                   const char *who) {

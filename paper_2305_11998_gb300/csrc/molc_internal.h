@@ -135,6 +135,8 @@ cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_
 cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st);
 cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
                            double *fyy, double *f_grey, cudaStream_t st);
+cudaError_t launch_grey(const PlanView &v, const molc_moments &m, const double *kappa, const double *B,
+                        double *out, cudaStream_t st);
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
                                   const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
                                   cudaStream_t st);

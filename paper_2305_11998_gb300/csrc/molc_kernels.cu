@@ -652,6 +652,41 @@ __device__ __forceinline__ void closure_cells(const PlanView &v, const molc_mome
   }
 }
 
+// Grey-problem coefficients (Eqs. 8-9), one thread per cell, all in FP64: <kappa>_E, <kappa>_B, the flux-weighted
+// K_R = diag(<kappa>_|Fx|, <kappa>_|Fy|) and eta = sum_g (kappa_g - K_R) F_g / sum_g E_g.
+__global__ void grey_kernel(PlanView v, molc_moments m, const double *kappa, const double *B, double *out) {
+  for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < v.ncell; cell += gridDim.x * blockDim.x) {
+    double se = 0, ske = 0, sb = 0, skb = 0, sfx = 0, skfx = 0, sfy = 0, skfy = 0;
+    for (int g = 0; g < v.G; ++g) {
+      const int64_t i = (int64_t)g * v.ncell + cell;
+      const double k = kappa[i], E = m.E[i], b = B[i], fx = fabs(m.Fx[i]), fy = fabs(m.Fy[i]);
+      se += E;
+      ske += k * E;
+      sb += b;
+      skb += k * b;
+      sfx += fx;
+      skfx += k * fx;
+      sfy += fy;
+      skfy += k * fy;
+    }
+    const double kE = se > 0 ? ske / se : 0.0, kB = sb > 0 ? skb / sb : 0.0;
+    const double kx = sfx > 0 ? skfx / sfx : 0.0, ky = sfy > 0 ? skfy / sfy : 0.0;
+    double ex = 0, ey = 0;
+    for (int g = 0; g < v.G; ++g) {
+      const int64_t i = (int64_t)g * v.ncell + cell;
+      ex += (kappa[i] - kx) * m.Fx[i];
+      ey += (kappa[i] - ky) * m.Fy[i];
+    }
+    const int64_t n = v.ncell;
+    out[cell] = kE;
+    out[n + cell] = kB;
+    out[2 * n + cell] = kx;
+    out[3 * n + cell] = ky;
+    out[4 * n + cell] = se > 0 ? ex / se : 0.0;
+    out[5 * n + cell] = se > 0 ? ey / se : 0.0;
+  }
+}
+
 __global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx, double *fxy, double *fyy,
                                double *fgrey) {
   closure_cells(v, m, c, fxx, fxy, fyy, fgrey, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
@@ -901,6 +936,12 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 #undef MOLC_MOMENTS
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grey(const PlanView &v, const molc_moments &m, const double *kappa, const double *B,
+                        double *out, cudaStream_t st) {
+  grey_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, m, kappa, B, out);
   return cudaGetLastError();
 }
 

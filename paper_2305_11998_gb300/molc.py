@@ -31,7 +31,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
-            "molc_batch_destroy")
+            "molc_batch_destroy", "molc_grey_coefficients")
 
 
 class MolcError(RuntimeError):
@@ -96,6 +96,7 @@ def load(build_if_needed: bool = True):
         "molc_sweep_static_scratch": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp,
                                                 C.POINTER(_Moments), vp]),
         "molc_closure": (C.c_int, [vp, C.POINTER(_Moments), C.c_double, vp, vp, vp, vp, vp]),
+        "molc_grey_coefficients": (C.c_int, [vp, C.POINTER(_Moments), vp, vp, vp, vp]),
         "molc_intensity_export": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "molc_intensity_import": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp, vp]),
         "molc_tracks_export": (C.c_int, [vp, i64p, i64p, dp, ip, ip, dp, dp]),
@@ -269,6 +270,16 @@ class Plan:
         if grey:
             f["grey"] = fg
         return f
+
+    GREY = ("kappa_E", "kappa_B", "KRx", "KRy", "eta_x", "eta_y")
+
+    def grey_coefficients(self, moments, kappa, B, stream=None):
+        """molc_grey_coefficients: {name: [cell] tensor} for kappa_E, kappa_B, KRx, KRy, eta_x, eta_y."""
+        out = torch.empty((6, self.ncell), dtype=torch.float64, device=kappa.device)
+        m = _Moments(*[moments[k].data_ptr() for k in MOMENTS])
+        _check(self._lib.molc_grey_coefficients(self._h, C.byref(m), _ptr(kappa), _ptr(B), _ptr(out),
+                                                _stream(stream)))
+        return dict(zip(self.GREY, out))
 
     def kernel_timing(self, enable: bool = True):
         _check(self._lib.molc_kernel_timing(self._h, int(enable)))

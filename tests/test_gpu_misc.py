@@ -77,6 +77,25 @@ def test_closure_and_grey_average(molc):
     P.close()
 
 
+def test_grey_coefficients_against_their_definition(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(2)
+    P = molc.Plan.from_workload(wl)
+    k, B = dev(d["kappa"]), dev(d["B"])
+    I = P.new_intensity("fp64")
+    P.intensity_init("fp64", I, B)
+    m = P.sweep("fp64", k, B, d["c"], d["dt"], I, dev(d["bnd"]))
+    got = {kk: v.cpu().numpy() for kk, v in P.grey_coefficients(m, k, B).items()}
+    mh = host(m)
+    ref = oracle.grey_coefficients(mh["E"], mh["Fx"], mh["Fy"], d["kappa"], d["B"])
+    for kk in ("kappa_E", "kappa_B", "KRx", "KRy"):
+        assert np.allclose(got[kk], ref[kk], rtol=1e-13, atol=0), kk
+    scale = np.max(np.abs(d["kappa"])) * (np.abs(mh["Fx"]) + np.abs(mh["Fy"])).sum(0) / mh["E"].sum(0)
+    for kk in ("eta_x", "eta_y"):
+        assert np.all(np.abs(got[kk] - ref[kk]) <= 1e-13 * scale), kk
+    P.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_export_import_roundtrip(molc, prec):
     wl = synth.WORKLOADS["fc16_g4_d32"]

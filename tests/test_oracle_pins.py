@@ -331,3 +331,28 @@ def test_multistep_relaxes_towards_steady_state():
     rate = 1 / (1 + d["c"] * d["dt"] * kmin)
     for a, b in zip(deltas[:-1], deltas[1:]):
         assert b <= a * rate * 1.0000001 + 1e-300
+
+
+def test_grey_coefficients_special_cases():
+    """Eqs. 8-9: one group, or an opacity the same in every group, gives every average = that opacity and
+    eta = 0; a single nonzero flux group picks that group's opacity for K_R."""
+    rng = np.random.default_rng(5)
+    G, n = 5, 7
+    E = rng.uniform(0.1, 1.0, (G, n))
+    Fx, Fy = rng.uniform(-1, 1, (G, n)), rng.uniform(-1, 1, (G, n))
+    B = rng.uniform(0.1, 1.0, (G, n))
+    k1 = np.tile(rng.uniform(1, 5, (1, n)), (G, 1))
+    r = oracle.grey_coefficients(E, Fx, Fy, k1, B)
+    for name in ("kappa_E", "kappa_B", "KRx", "KRy"):
+        assert np.allclose(r[name], k1[0], rtol=1e-15), name
+    assert np.max(np.abs(r["eta_x"])) < 1e-15 * np.max(k1) * np.max(np.abs(Fx)) / E.sum(0).min() * G
+    kg = rng.uniform(1, 5, (G, n))
+    Fx1 = np.zeros((G, n))
+    Fx1[2] = rng.uniform(0.5, 1.0, n)
+    r = oracle.grey_coefficients(E, Fx1, Fy, kg, B)
+    # (kappa |F| / |F| may differ from kappa by an ulp, and eta by that ulp times |F| / sum E)
+    assert np.allclose(r["KRx"], kg[2], rtol=2e-16, atol=0)
+    assert np.all(np.abs(r["eta_x"]) <= 4e-16 * kg[2] * Fx1[2] / E.sum(0))
+    r1 = oracle.grey_coefficients(E[:1], Fx[:1], Fy[:1], kg[:1], B[:1])
+    assert np.allclose(r1["kappa_E"], kg[0], rtol=2e-16, atol=0)
+    assert np.all(np.abs(r1["eta_y"]) <= 4e-16 * kg[0] * np.abs(Fy[0]) / E[0])
