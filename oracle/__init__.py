@@ -55,9 +55,9 @@ def _load():
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)
         lib.oracle_count.argtypes = [C.POINTER(_Geom), i64p]
-        lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp]
+        lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp, ip]
         lib.oracle_sweep.argtypes = [C.POINTER(_Geom), C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
-                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int]
+                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int, dp]
         for f in (lib.oracle_count, lib.oracle_tracks, lib.oracle_sweep):
             f.restype = C.c_int
         lib.oracle_real_bits.argtypes = [C.c_int]
@@ -122,19 +122,28 @@ def tracks(geom: Geometry, precision: str = "quad") -> dict:
     g = geom._c()
     d = dict(dir_ray_off=np.zeros(geom.mu.size + 1, np.int64), ray_seg_off=np.zeros(nr + 1, np.int64),
              width=np.zeros(nr), entry=np.zeros(nr, np.int32), cell=np.zeros(ns, np.int32), len=np.zeros(ns),
-             area=np.zeros(ns))
+             area=np.zeros(ns), face=np.zeros(ns, np.int32))
     i64 = C.POINTER(C.c_int64)
     ip = C.POINTER(C.c_int)
     rc = lib.oracle_tracks(C.byref(g), PREC[precision], d["dir_ray_off"].ctypes.data_as(i64),
                            d["ray_seg_off"].ctypes.data_as(i64), _dp(d["width"]), d["entry"].ctypes.data_as(ip),
-                           d["cell"].ctypes.data_as(ip), _dp(d["len"]), _dp(d["area"]))
+                           d["cell"].ctypes.data_as(ip), _dp(d["len"]), _dp(d["area"]), d["face"].ctypes.data_as(ip))
     if rc:
         raise RuntimeError(f"oracle_tracks failed ({rc})")
     return d
 
 
+FACE_MOMENTS = ("face_E", "face_Fx", "face_Fy", "face_Nxx", "face_Nxy", "face_Nyy")
+
+
+def n_faces(geom: Geometry) -> int:
+    """x-faces (nx + 1) ny, then y-faces nx (ny + 1)."""
+    return (geom.nx + 1) * geom.ny + geom.nx * (geom.ny + 1)
+
+
 def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
-          want_I=True, want_exit=False, threads=None, I_as_deviation=False, I_prev_is_deviation=False) -> dict:
+          want_I=True, want_exit=False, threads=None, I_as_deviation=False, I_prev_is_deviation=False,
+          want_faces=False) -> dict:
     """One backward-Euler sweep.  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
     (I^{n-1} = B of the segment's cell); with I_prev_is_deviation, I_prev holds deviations from B of the
     segment's cell (so a state carried between steps as deviations keeps its precision).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
@@ -157,12 +166,13 @@ def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precis
     out = np.zeros((len(MOMENTS), Gsub, geom.ncell))
     I_new = np.zeros((ns, Gsub)) if want_I else None
     I_exit = np.zeros((nr, Gsub)) if want_exit else None
+    fout = np.zeros((6, Gsub, n_faces(geom))) if want_faces else None
     g = geom._c()
     nthreads = threads or max(1, min(os.cpu_count() or 1, 64))
     rc = lib.oracle_sweep(C.byref(g), PREC[precision], G, _dp(kappa), _dp(B), float(c), float(dt), _dp(bnd),
                           _dp(I_prev), gl.ctypes.data_as(C.POINTER(C.c_int)) if gl is not None else None,
                           0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads),
-                          int(bool(I_as_deviation)), int(bool(I_prev_is_deviation)))
+                          int(bool(I_as_deviation)), int(bool(I_prev_is_deviation)), _dp(fout))
     if rc:
         raise RuntimeError(f"oracle_sweep failed ({rc})")
     res = {k: out[i] for i, k in enumerate(MOMENTS)}
@@ -170,6 +180,8 @@ def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precis
         res["I"] = I_new
     if want_exit:
         res["I_exit"] = I_exit
+    if want_faces:
+        res.update({k: fout[i] for i, k in enumerate(FACE_MOMENTS)})
     return res
 
 

@@ -94,6 +94,7 @@ template <class R> struct Ray {
   R width;
   int entry;                  // edge the characteristic enters through
   std::vector<int> cell;      // segments in traversal order
+  std::vector<int> face;      // face each segment enters through (its upwind face; numbering in face_of)
   std::vector<R> len;         // in-plane length l
   std::vector<R> area;        // A = l w (after optional renormalisation)
 };
@@ -209,6 +210,24 @@ static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
     ray.len.push_back(b - a);
     ray.area.push_back((b - a) * width);
   }
+  // Upwind face of every segment (Sec. 3, Eq. 16): the first enters through the entry edge; the others through
+  // the face shared with the previous segment's cell.  Faces: x-face (i, j) = the line x = x0 + i hx in row j,
+  // numbered j (nx + 1) + i; y-face (i, j) = the line y = y0 + j hy in column i, numbered (nx + 1) ny + j nx + i.
+  // A characteristic through a vertex (a diagonal step) is counted on the x-face of the cell it enters.
+  ray.face.clear();
+  const int nxf = (g.nx + 1) * g.ny;
+  for (size_t s = 0; s < ray.cell.size(); ++s) {
+    const int ix = ray.cell[s] % g.nx, iy = ray.cell[s] / g.nx;
+    int f;
+    if (s == 0) {
+      f = ray.entry == EDGE_L ? iy * (g.nx + 1) : ray.entry == EDGE_R ? iy * (g.nx + 1) + g.nx
+        : ray.entry == EDGE_B ? nxf + ix : nxf + g.ny * g.nx + ix;
+    } else {
+      const int px = ray.cell[s - 1] % g.nx, py = ray.cell[s - 1] / g.nx;
+      f = px != ix ? iy * (g.nx + 1) + std::max(px, ix) : nxf + std::max(py, iy) * g.nx + ix;
+    }
+    ray.face.push_back(f);
+  }
   return !ray.cell.empty();
 }
 
@@ -307,7 +326,7 @@ template <class R>
 static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
                             const double *kappa, const double *B, R inv_cdt, const double *bnd,
                             const double *I_prev, int64_t seg0, double *I_new, double *I_exit, int64_t ray0,
-                            int Gsub, int store_dev, int prev_dev, std::vector<R> *acc) {
+                            int Gsub, int store_dev, int prev_dev, std::vector<R> *acc, std::vector<R> *facc) {
   const Dir<R> &d = geo.dirs[geo.of[m]];
   const int64_t ncell = (int64_t)g.nx * g.ny;
   const R mu = g.mu[m];
@@ -333,6 +352,18 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
       const R Iout = I * e + (Q / kt) * one_m_e;                    // Eq. (12)
       const R alpha = R(1) / tau - e / one_m_e;                     // Eq. (13)
       const R Ibar = alpha * I + (R(1) - alpha) * Iout;             // Eq. (12)
+      if (facc) {   // Eq. (16): omega_m w_k times the intensity at the segment's upwind face
+        const int64_t nf = (int64_t)(g.nx + 1) * g.ny + (int64_t)g.nx * (g.ny + 1);
+        const int f = r.face[s];
+        const R ww = om * r.width;
+        R *fa = facc->data();
+        fa[MOM_D * nf + f] += ww * I;
+        fa[MOM_FX * nf + f] += ww * Ox * I;
+        fa[MOM_FY * nf + f] += ww * Oy * I;
+        fa[MOM_NXX * nf + f] += ww * Ox * Ox * I;
+        fa[MOM_NXY * nf + f] += ww * Ox * Oy * I;
+        fa[MOM_NYY * nf + f] += ww * Oy * Oy * I;
+      }
       const R wA = om * r.area[s];                                  // omega_m A_{k,s}, Eq. (14)-(15)
       const R dev = rabs(Ibar - B_i);
       R *a = acc->data();
@@ -356,7 +387,7 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
 template <class R>
 static int run_sweep(const oracle_geom *g, int G, const double *kappa, const double *B, double c, double dt,
                      const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                     double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev) {
+                     double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out) {
   if (check_geom(g)) return -1;
   if (G < 1 || !kappa || !B || !bnd || !(c > 0) || !(dt > 0) || !out) return -1;
   Geometry<R> geo;
@@ -381,15 +412,17 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
   const R V = R(g->lx / g->nx) * R(g->ly / g->ny);
   const int nblk = std::min(g->ndir, 16);
   if (nthreads < 1) nthreads = 1;
-  std::vector<std::vector<R>> acc(nblk);
+  std::vector<std::vector<R>> acc(nblk), facc(face_out ? nblk : 0);
+  const int64_t nf = (int64_t)(g->nx + 1) * g->ny + (int64_t)g->nx * (g->ny + 1);
   for (int gi = 0; gi < Gsub; ++gi) {
     for (auto &a : acc) a.assign((size_t)N_MOM * ncell, R(0));
+    for (auto &a : facc) a.assign((size_t)6 * nf, R(0));
     auto work = [&](int tid) {
       for (int b = tid; b < nblk; b += nthreads) {
         int m0 = (int)((int64_t)g->ndir * b / nblk), m1 = (int)((int64_t)g->ndir * (b + 1) / nblk);
         for (int m = m0; m < m1; ++m)
           sweep_direction<R>(*g, geo, m, gi, G, gl[gi], kappa, B, inv_cdt, bnd, I_prev, seg_off[m], I_new,
-                             I_exit, ray_off[m], Gsub, store_dev, prev_dev, &acc[b]);
+                             I_exit, ray_off[m], Gsub, store_dev, prev_dev, &acc[b], face_out ? &facc[b] : nullptr);
       }
     };
     int nt = std::min(nthreads, nblk);
@@ -406,13 +439,29 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
       const R scale = q == MOM_D ? R(1) / (R(c) * V) : R(1) / V;
       for (int64_t i = 0; i < ncell; ++i) o[i] = (double)(tot[(size_t)q * ncell + i] * scale);
     }
+    if (face_out) {
+      // face averages over the face length: E_f = (1/(c |f|)) sum omega w I, F_f, N_f = (1/|f|) sum ...
+      std::vector<R> ft((size_t)6 * nf, R(0));
+      for (int b = 0; b < nblk; ++b)
+        for (size_t q = 0; q < ft.size(); ++q) ft[q] += facc[b][q];
+      const R hx = R(g->lx / g->nx), hy = R(g->ly / g->ny);
+      const int64_t nxf = (int64_t)(g->nx + 1) * g->ny;
+      for (int q = 0; q < 6; ++q) {
+        double *o = face_out + ((int64_t)q * Gsub + gi) * nf;
+        for (int64_t f = 0; f < nf; ++f) {
+          const R len = f < nxf ? hy : hx;
+          const R scale = q == MOM_D ? R(1) / (R(c) * len) : R(1) / len;
+          o[f] = (double)(ft[(size_t)q * nf + f] * scale);
+        }
+      }
+    }
   }
   return 0;
 }
 
 template <class R>
 static int run_tracks(const oracle_geom *g, int64_t *counts, int64_t *dir_ray_off, int64_t *ray_seg_off,
-                      double *width, int *entry, int *cell, double *len, double *area) {
+                      double *width, int *entry, int *cell, double *len, double *area, int *face) {
   if (check_geom(g)) return -1;
   Geometry<R> geo;
   int rc = geo.build(*g);
@@ -431,6 +480,7 @@ static int run_tracks(const oracle_geom *g, int64_t *counts, int64_t *dir_ray_of
       entry[ri] = r.entry;
       for (size_t s = 0; s < r.cell.size(); ++s, ++si) {
         cell[si] = r.cell[s];
+        if (face) face[si] = r.face[s];
         len[si] = (double)r.len[s];
         area[si] = (double)r.area[s];
       }
@@ -446,16 +496,16 @@ extern "C" {
 // Sizes of the characteristic grid: counts[0] = characteristics summed over directions, counts[1] = segments
 // summed over directions (the length of the canonical per-group intensity array).  Returns 0 on success.
 int oracle_count(const oracle_geom *g, int64_t *counts) {
-  return run_tracks<double>(g, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return run_tracks<double>(g, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
 // The characteristic grid in canonical order.  precision: 0 = double, 1 = binary128 (values rounded to double).
 int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int64_t *ray_seg_off,
-                  double *width, int *entry, int *cell, double *len, double *area) {
+                  double *width, int *entry, int *cell, double *len, double *area, int *face) {
   if (!dir_ray_off || !ray_seg_off || !width || !entry || !cell || !len || !area) return -1;
   int64_t counts[2];
-  return precision ? run_tracks<real128>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area)
-                   : run_tracks<double>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area);
+  return precision ? run_tracks<real128>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area, face)
+                   : run_tracks<double>(g, counts, dir_ray_off, ray_seg_off, width, entry, cell, len, area, face);
 }
 
 // One backward-Euler sweep of every direction, characteristic and (selected) group.
@@ -470,13 +520,16 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 //   I_new      [nseg][Gsub]      canonical segment averages Ibar (may be NULL); with store_dev != 0 the
 //                                deviations Ibar - B of the segment's cell, formed in the oracle's precision
 //   I_exit     [nrays][Gsub]     intensity leaving each characteristic (may be NULL)
+//   face_out   [6][Gsub][nfaces] face averages E, Fx, Fy, Nxx, Nxy, Nyy of the intensity at the upwind face of
+//                                every segment, weighted by omega w (Eq. 16), or NULL; faces numbered as in
+//                                trace(): x-faces (nx+1) ny first, then y-faces nx (ny+1)
 int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa, const double *B, double c,
                  double dt, const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                 double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev) {
+                 double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out) {
   return precision ? run_sweep<real128>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev, prev_dev)
+                                       nthreads, store_dev, prev_dev, face_out)
                    : run_sweep<double>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev, prev_dev);
+                                       nthreads, store_dev, prev_dev, face_out);
 }
 
 int oracle_real_bits(int precision) { return precision ? (int)(sizeof(real128) * 8) : 64; }

@@ -356,3 +356,80 @@ def test_grey_coefficients_special_cases():
     r1 = oracle.grey_coefficients(E[:1], Fx[:1], Fy[:1], kg[:1], B[:1])
     assert np.allclose(r1["kappa_E"], kg[0], rtol=2e-16, atol=0)
     assert np.all(np.abs(r1["eta_y"]) <= 4e-16 * kg[0] * np.abs(Fy[0]) / E[0])
+
+
+def _face_geometry(nx, ny):
+    nxf = (nx + 1) * ny
+
+    def cells_of(f):
+        """(kind, index along the normal, index across): x-face (i, j) or y-face (i, j)."""
+        if f < nxf:
+            return "x", f % (nx + 1), f // (nx + 1)
+        f -= nxf
+        return "y", f % nx, f // nx
+    return nxf, cells_of
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_upwind_faces_are_the_faces_segments_enter_through(layout):
+    """Eq. 16 needs the upwind face of every segment: for the first segment the boundary face of the entry edge,
+    otherwise a face of the entered cell that the previous cell touches, on the side the characteristic comes
+    from (checked here from the cells and the direction, independently of how the oracle numbers them)."""
+    nx, ny = 5, 4
+    q = synth.product_quadrature(2, 16)
+    geom = oracle.Geometry(nx, ny, 2.5, 1.6, q.mu, q.cos_phi, q.sin_phi, q.w, 0.17, layout, 1 - layout)
+    t = oracle.tracks(geom, "double")
+    nxf, cells_of = _face_geometry(nx, ny)
+    for m in range(q.mu.size):
+        dx, dy = q.cos_phi[m], q.sin_phi[m]
+        for r in range(t["dir_ray_off"][m], t["dir_ray_off"][m + 1]):
+            s0, s1 = t["ray_seg_off"][r], t["ray_seg_off"][r + 1]
+            for s in range(s0, s1):
+                ix, iy = t["cell"][s] % nx, t["cell"][s] // nx
+                kind, a, b = cells_of(t["face"][s])
+                if kind == "x":
+                    assert b == iy and a == (ix if dx > 0 else ix + 1)
+                else:
+                    assert a == ix and b == (iy if dy > 0 else iy + 1)
+                if s == s0:
+                    e = t["entry"][r]
+                    normal = a if kind == "x" else b
+                    assert (kind, normal) == {0: ("x", 0), 1: ("x", nx), 2: ("y", 0), 3: ("y", ny)}[e]
+                else:
+                    px, py = t["cell"][s - 1] % nx, t["cell"][s - 1] // nx
+                    assert abs(px - ix) <= 1 and abs(py - iy) <= 1 and (px, py) != (ix, iy)
+                    if kind == "x":
+                        assert px != ix        # crossed a vertical line
+                    else:
+                        assert px == ix and py != iy
+
+
+def test_face_moments_equilibrium_closed_form():
+    """Homogeneous medium in equilibrium (I = B everywhere), paper layout: the characteristics of direction m
+    that cross an interior x-face have widths summing to |face| |d_x| exactly (bands never straddle a vertex),
+    so E_f = (B/c) sum_m omega_m |d_x|, N_f = B sum_m omega_m |d_x| Omega Omega, F_f = 0 (Eq. 16 numerators);
+    likewise with |d_y| on y-faces."""
+    nx, ny = 4, 3
+    q = synth.product_quadrature(2, 16)
+    geom = oracle.Geometry(nx, ny, 2.0, 1.2, q.mu, q.cos_phi, q.sin_phi, q.w, 0.13, 1, 0)
+    G = 2
+    Bv = np.array([1.0, 3e-4])
+    kap = np.array([0.7, 40.0])
+    B = np.repeat(Bv[:, None], nx * ny, 1)
+    kappa = np.repeat(kap[:, None], nx * ny, 1)
+    bnd = np.repeat(Bv[None, :], 4, 0)
+    c = 2.0
+    r = oracle.sweep(geom, kappa, B, c, 0.5, bnd, precision="quad", want_I=False, want_faces=True)
+    sz = np.sqrt(1 - q.mu ** 2)
+    Ox, Oy = sz * q.cos_phi, sz * q.sin_phi
+    nxf = (nx + 1) * ny
+    xint = [j * (nx + 1) + i for j in range(ny) for i in range(1, nx)]
+    yint = [nxf + j * nx + i for j in range(1, ny) for i in range(nx)]
+    for faces, wdir in ((xint, np.abs(q.cos_phi)), (yint, np.abs(q.sin_phi))):
+        ww = q.w * wdir
+        exp = {"face_E": ww.sum() / c, "face_Fx": 0.0, "face_Fy": 0.0, "face_Nxx": (ww * Ox * Ox).sum(),
+               "face_Nxy": (ww * Ox * Oy).sum(), "face_Nyy": (ww * Oy * Oy).sum()}
+        for k, e in exp.items():
+            for g in range(G):
+                got = r[k][g, faces] / Bv[g]
+                assert np.max(np.abs(got - e)) <= 1e-13 * ww.sum(), (k, g)
