@@ -57,6 +57,9 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 #define MOLC_AREA_RENORM 1u /* scale A_{k,s} per (cell, azimuth) so that sum over C(i,m) of A = cell area */
 #define MOLC_HOST_ONLY 2u   /* build the characteristic grid on the host only (no device memory, no GPU needed):
                                only molc_plan_get_info, molc_tracks_export and molc_destroy accept such a plan */
+#define MOLC_FACES 8u       /* also accumulate the face moments of Eq. 16 in every molc_sweep (device memory for
+                               6 FP64 sums per (face, group); FP64 reductions per segment, so sweeps are slower);
+                               read them with molc_face_moments */
 #define MOLC_AUTOTUNE 4u    /* time the FP32 sweep's compiled staging depths on this plan during molc_create
                                (temporary device memory of about one FP32 state) and keep the fastest; the
                                choice changes no result, only speed (molc_plan_info.fp32_sweep_depth) */
@@ -103,6 +106,7 @@ typedef struct {
   int fp32_groups_per_warp; /* groups per chunk of the FP32 sweep (chunks run one after another) */
   size_t device_bytes;      /* device memory the plan holds */
   int fp32_sweep_depth;     /* staging depth of the FP32 sweep (steps of look-ahead; MOLC_AUTOTUNE picks it) */
+  int n_faces;              /* MOLC_FACES: (nx + 1) ny x-faces then nx (ny + 1) y-faces; else 0 */
 } molc_plan_info;
 
 /* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,
@@ -221,6 +225,18 @@ void molc_batch_destroy(molc_batch *batch);
  * A cell with E = 0 gets f = 0. */
 molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c, double *fxx, double *fxy,
                          double *fyy, double *f_grey, molc_stream stream);
+
+/* Face-average moments of the last molc_sweep in precision prec (plans created with MOLC_FACES), the
+ * quantities of the face Eddington tensor (Eq. 16): for every face f and group, with I_{k,s} the intensity at
+ * the upwind face of each segment whose upwind face is f (F(f, m)) and w_k its characteristic's width,
+ *   E_f = (1/(c |f|)) sum_m sum_{F(f,m)} omega_m w_k I,  F_f = (1/|f|) sum omega w Omega I,
+ *   N_f = (1/|f|) sum omega w Omega Omega I  (f_f = N_f / (c E_f) is the face tensor of Eq. 16).
+ * |f| = hy on x-faces, hx on y-faces.  Faces: x-face (i, j) on the line x = x0 + i hx in row j is number
+ * j (nx + 1) + i; y-face (i, j) on y = y0 + j hy in column i is (nx + 1) ny + j nx + i.  A segment entering
+ * through a vertex counts on the x-face of the cell it enters.  I: the state the sweep used (for its scale);
+ * out: device, each [G][n_faces] FP64.  Not produced by molc_batch_sweep. */
+molc_status molc_face_moments(const molc_plan *plan, molc_precision prec, const void *I, double c,
+                              const molc_moments *out, molc_stream stream);
 
 /* Spectrum-averaged coefficients of the effective grey problem (Sec. 2, Eqs. 8-9), per cell from the group
  * moments and opacities:

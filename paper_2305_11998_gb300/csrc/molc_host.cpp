@@ -95,6 +95,9 @@ struct molc_plan {
   int64_t *d_cell_off = nullptr;
   int4 *d_gent = nullptr;
   int64_t *d_boff = nullptr;
+  int2 *d_seg_face = nullptr;
+  double *d_facc = nullptr;
+  size_t facc_elems = 0;
   int *d_block_order = nullptr;
   int64_t bundle_slots = 0;   // FP32 state: step slots of all bundles (boff[n_blocks])
   int64_t n_blocks32 = 0;     // FP32 sweep blocks (bundles)
@@ -304,7 +307,7 @@ void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
                   p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
-                  p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order};
+                  p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order, p->d_seg_face, p->d_facc};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -468,7 +471,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   if (groups->G < 1 || groups->G > 4096) return fail(MOLC_ERR_INVALID_ARG, "create: need 1 <= G <= 4096");
   if (!finite_pos(ray_spacing)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing must be > 0");
   if (layout != MOLC_RAYS_UNIFORM && layout != MOLC_RAYS_PAPER) return fail(MOLC_ERR_INVALID_ARG, "create: layout");
-  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE))
+  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE | MOLC_FACES))
     return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
   const int n = quad->n;
   if (n < 2 || !quad->mu || !quad->cos_phi || !quad->sin_phi || !quad->w)
@@ -688,6 +691,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       d.pair = j;
       d.entry_plus = h.entry_plus;
       d.entry_minus = h.entry_minus;
+      d.width = h.width;
       d.canon_plus = h.seg_off - seg_base;
       d.canon_minus = pair_nseg[j] - (h.seg_off - seg_base) - h.nseg;
     }
@@ -805,6 +809,40 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.n_track_segments = S;
   v.gc32 = gc32;
   v.sweep_depth = 4;
+  v.hx = p->hx;
+  v.hy = p->hy;
+  // ---- face moments (Eq. 16, MOLC_FACES): the face each segment enters through, per sense.  The first segment
+  // of a sense enters through the boundary face of its entry edge; the others through the face they share with
+  // the cell walked before (a step through a vertex counts on the x-face of the cell entered).  Faces: x-face
+  // (i, j) = line x = x0 + i hx in row j, numbered j (nx + 1) + i; y-face (i, j) = line y = y0 + j hy in column
+  // i, numbered (nx + 1) ny + j nx + i.
+  std::vector<int2> seg_face;
+  const int nxf = (g.nx + 1) * g.ny;
+  v.n_faces = (flags & MOLC_FACES) ? nxf + g.nx * (g.ny + 1) : 0;
+  if (flags & MOLC_FACES) {
+    seg_face.assign((size_t)S, make_int2(0, 0));
+    auto edge_face = [&](int edge, int cell) {
+      const int ix = cell % g.nx, iy = cell / g.nx;
+      return edge == 0 ? iy * (g.nx + 1) : edge == 1 ? iy * (g.nx + 1) + g.nx
+           : edge == 2 ? nxf + ix : nxf + g.ny * g.nx + ix;
+    };
+    auto between = [&](int prev, int cell) {
+      const int ix = cell % g.nx, iy = cell / g.nx, px = prev % g.nx, py = prev / g.nx;
+      return px != ix ? iy * (g.nx + 1) + std::max(px, ix) : nxf + std::max(py, iy) * g.nx + ix;
+    };
+    for (int64_t k = 0; k < T; ++k) {
+      const TrackDev &t = td[k];
+      for (int j = 0; j < t.nseg; ++j) {
+        const int64_t q = t.seg_off + j;
+        const int c = p->seg_cell[q];
+        seg_face[q].x = j == 0 ? edge_face(t.entry_plus, c) : between(p->seg_cell[q - 1], c);
+        seg_face[q].y = j == t.nseg - 1 ? edge_face(t.entry_minus, c) : between(p->seg_cell[q + 1], c);
+      }
+    }
+    const int gcf = std::max(gc32, p->G);   // accumulators shared by both precisions: [chunk][face][6][gc]
+    p->facc_elems = (size_t)v.n_faces * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
+    (void)gcf;
+  }
   if (p->host_only) {
     *out = p;
     return MOLC_OK;
@@ -827,6 +865,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_cell_off, cell_off.data(), cell_off.size(), "cell entry offsets")
   UP(d_gent, gent.data(), gent.size(), "cell entries")
   UP(d_boff, boff.data(), boff.size(), "state bundles")
+  UP(d_seg_face, seg_face.data(), seg_face.size(), "segment faces")
+  UP(d_facc, (const double *)nullptr, p->facc_elems, "face accumulators")
   UP(d_block_order, block_order.data(), block_order.size(), "block order")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
@@ -856,6 +896,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.gent = p->d_gent;
   v.boff = p->d_boff;
   v.block_order = p->d_block_order;
+  v.seg_face = p->d_seg_face;
+  v.facc = p->d_facc;
   if ((flags & MOLC_AUTOTUNE) && nch32) {
     st = autotune(p);
     if (st != MOLC_OK) {
@@ -883,6 +925,7 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->fp32_groups_per_warp = p->view.gc32;
   info->device_bytes = p->device_bytes;
   info->fp32_sweep_depth = p->view.sweep_depth;
+  info->n_faces = p->view.n_faces;
   return MOLC_OK;
 }
 
@@ -972,6 +1015,10 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.items = p->d_items32;
   a.n_items = p->n_items32;
   cudaError_t e = cudaSuccess;
+  if (p->d_facc) {
+    e = cudaMemsetAsync(p->d_facc, 0, p->facc_elems * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep: clear face accumulators");
+  }
   if (prec == MOLC_FP64) {   // the FP32 path gathers its moments and has no accumulators
     e = cudaMemsetAsync(p->d_acc, 0, (size_t)p->G * p->view.ncell * kOutputs * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
@@ -1045,6 +1092,10 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
   a.cdB = prec == MOLC_FP32 ? (float *)(b + cdat_bytes) : nullptr;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
+  if (p->d_facc) {
+    e = cudaMemsetAsync(p->d_facc, 0, p->facc_elems * sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear face accumulators");
+  }
   if (prec == MOLC_FP64) {
     e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
@@ -1126,6 +1177,9 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
       return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d has no FP32 sweep (more than %d polar cosines)", i,
                   kMaxPolarFP32);
     if (plans[i]->device != dev) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is on another device", i);
+    if (plans[i]->d_facc)
+      return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d was created with MOLC_FACES (face moments come from "
+                                        "molc_sweep only)", i);
   }
   auto b = new molc_batch();
   b->device = dev;
@@ -1279,6 +1333,20 @@ molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, do
   DeviceGuard dg(p->device);
   cudaError_t e = launch_closure(p->view, *m, c, fxx, fxy, fyy, f_grey, (cudaStream_t)stream);
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "closure");
+}
+
+molc_status molc_face_moments(const molc_plan *p, molc_precision prec, const void *I, double c, const molc_moments *out,
+                              molc_stream stream) {
+  if (!p || !I || !out || !out->E || !out->Fx || !out->Fy || !out->Nxx || !out->Nxy || !out->Nyy)
+    return fail(MOLC_ERR_INVALID_ARG, "face_moments: NULL argument");
+  if (!finite_pos(c)) return fail(MOLC_ERR_INVALID_ARG, "face_moments: need c > 0");
+  molc_status s = check_prec(p, prec, "face_moments");
+  if (s) return s;
+  if (!p->d_facc) return fail(MOLC_ERR_INVALID_ARG, "face_moments: the plan was created without MOLC_FACES");
+  DeviceGuard dg(p->device);
+  const double *scale = prec == MOLC_FP32 ? header_of(p, prec, const_cast<void *>(I)) : nullptr;
+  cudaError_t e = launch_face_moments(p->view, prec, scale, c, *out, (cudaStream_t)stream);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "face_moments");
 }
 
 molc_status molc_grey_coefficients(const molc_plan *p, const molc_moments *m, const double *kappa, const double *B,

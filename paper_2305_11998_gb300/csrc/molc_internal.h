@@ -31,6 +31,7 @@ struct TrackDev {
   int64_t canon_plus;   // offset of this track's segments within the + sense direction's canonical block
   int64_t canon_minus;  // same for the - sense (tracks are in reverse order there)
   int pos[2];           // FP32 work items: position of the (track, + / - sense) in the item order
+  double width;         // w_k
 };
 
 struct PairDev {
@@ -65,6 +66,11 @@ struct PlanView {
   const int64_t *boff;          // FP32 state: [n_blocks + 1] first step slot of each bundle
   const int *block_order;       // FP32 sweep: bundle swept by each block of the launch (longest first)
   int sweep_depth;              // FP32 sweep: staging depth D (one of kSweepDepths; autotuned or 4)
+  // face moments (Eq. 16), plans created with MOLC_FACES only (else null / 0)
+  const int2 *seg_face;         // per track segment: upwind face of the + sense, of the - sense
+  double *facc;                 // [chunk][face][6][gc] FP64 sums of omega w I (1, Omega, Omega Omega)
+  int n_faces;                  // x-faces (nx + 1) ny, then y-faces nx (ny + 1)
+  double hx, hy;                // cell sizes (face lengths)
 };
 
 constexpr int kSweepDepths[] = {3, 4, 6};   // compiled staging depths of the FP32 sweep
@@ -135,6 +141,8 @@ cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_
 cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepArgs &a, cudaStream_t st);
 cudaError_t launch_closure(const PlanView &v, const molc_moments &m, double c, double *fxx, double *fxy,
                            double *fyy, double *f_grey, cudaStream_t st);
+cudaError_t launch_face_moments(const PlanView &v, molc_precision prec, const double *scale, double c,
+                                const molc_moments &out, cudaStream_t st);
 cudaError_t launch_grey(const PlanView &v, const molc_moments &m, const double *kappa, const double *B,
                         double *out, cudaStream_t st);
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,

@@ -148,6 +148,17 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
     const double Bc = Bg[cell];
     const double kt = kap[cell] + inv_cdt;
     psi = s == 0 ? Iin - Bc : psi + (Bprev - Bc);
+    if (v.facc) {   // Eq. (16): omega w times the intensity at the segment's upwind face
+      const int2 fc = v.seg_face[sgi];
+      double *fa = v.facc + (int64_t)(sense ? fc.y : fc.x) * kOutputs * v.G + g;
+      const double wi = pd.w * tr.width * (psi + Bc);
+      atomicAdd(fa + 0 * v.G, wi);
+      atomicAdd(fa + 1 * v.G, wi * Ox);
+      atomicAdd(fa + 2 * v.G, wi * Oy);
+      atomicAdd(fa + 3 * v.G, wi * Ox * Ox);
+      atomicAdd(fa + 4 * v.G, wi * Ox * Oy);
+      atomicAdd(fa + 5 * v.G, wi * Oy * Oy);
+    }
     const double d = (I[(int64_t)s * Q] + (Bref[cell] - Bc)) * (inv_cdt / kt);
     const double tau = kt * len * pd.inv_sinz;
     const double one_m_e = -expm1(-tau);
@@ -337,7 +348,7 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
 // Group accounting: the prologue commits D-1 groups (deviations of steps 0..D-2, table entries of steps
 // 0..D-3) and step s commits one; step s's deviations are in group s and its table entry in group s+1 (group s
 // for s <= D-3), so waiting until at most D-2 groups are pending is enough.
-template <int NP, int D>
+template <int NP, int D, bool FACES = false>
 __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle) {
   static_assert(D >= 3, "the staging depth needs D >= 3");
   constexpr int kSteps = D;
@@ -371,13 +382,19 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   const float4 *cd = a.cdat + cbase;
   const float *cdB = a.cdB + cbase;
 
-  float inv_sinz[NP], sinz[NP];
+  float inv_sinz[NP], sinz[NP], wf[FACES ? NP : 1];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const PolarDev pd = v.polar[tr.pair * NP + p];
     inv_sinz[p] = pd.inv_sinzf;
     sinz[p] = pd.sinzf;
+    if constexpr (FACES) wf[p] = pd.wf;
   }
+  // face moments (Eq. 16): faces of this sense's segments, in traversal order like the records
+  const int2 *sface = FACES ? v.seg_face + (sense ? tr.seg_off + nseg - 1 : tr.seg_off) : nullptr;
+  const float fx = FACES ? (float)((sense ? -1.0 : 1.0) * v.pairs[tr.pair].c) : 0.f;
+  const float fy = FACES ? (float)((sense ? -1.0 : 1.0) * v.pairs[tr.pair].s) : 0.f;
+  const float width = FACES ? (float)tr.width : 0.f;
   // entering intensity (scaled), split like B so that I_in - B keeps the precision of the difference
   const double bin = live ? a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g] * a.scale[0] : 0.0;
   const float in_hi = (float)bin, in_lo = (float)(bin - (double)in_hi);
@@ -441,8 +458,33 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
         const float kl = q.x * len;
         const float rkl = rcp_approx(kl);
 #pragma unroll
+        for (int p = 0; p < NP; ++p) psi[p] += jump;
+        if constexpr (FACES) {
+          // the intensity entering the segment, in scaled units: psi (relative to this cell) + B of this cell
+          const float Bc = q.z + q.w;
+          float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const float t0 = wf[p] * (psi[p] + Bc);
+            S0 += t0;
+            const float t1 = t0 * sinz[p];
+            S1 += t1;
+            S2 = fmaf(t1, sinz[p], S2);
+          }
+          const int2 fc = __ldg(sface + s * rstep);
+          double *fa = v.facc + ((int64_t)ch * v.n_faces + (sense ? fc.y : fc.x)) * kOutputs * L.gc + gi;
+          S0 *= width;
+          S1 *= width;
+          S2 *= width;
+          atomicAdd(fa, f32_to_f64(S0));
+          atomicAdd(fa + L.gc, f32_to_f64(fx * S1));
+          atomicAdd(fa + 2 * L.gc, f32_to_f64(fy * S1));
+          atomicAdd(fa + 3 * L.gc, f32_to_f64(fx * fx * S2));
+          atomicAdd(fa + 4 * L.gc, f32_to_f64(fx * fy * S2));
+          atomicAdd(fa + 5 * L.gc, f32_to_f64(fy * fy * S2));
+        }
+#pragma unroll
         for (int p = 0; p < NP; ++p) {
-          psi[p] += jump;
           float E1, ex;
           attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
           const float d = fmaf(dv[p], q.y, dB);
@@ -461,9 +503,9 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   cp_async_wait<0>();
 }
 
-template <int NP, int D>
+template <int NP, int D, bool FACES = false>
 __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
-  sweep_fp32_body<NP, D>(v, a, L, v.block_order[blockIdx.x]);
+  sweep_fp32_body<NP, D, FACES>(v, a, L, v.block_order[blockIdx.x]);
 }
 
 // Batched: block j sweeps bundle map[j].y of instance map[j].x (blocks of all instances, longest first).
@@ -896,6 +938,20 @@ cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_
   const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)blocks);
+  if (v.facc) {   // face moments requested: the variant with face reductions (staging depth 4)
+    switch (v.n_polar) {
+      case 1: sweep_fp32_kernel<1, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 2: sweep_fp32_kernel<2, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 3: sweep_fp32_kernel<3, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 4: sweep_fp32_kernel<4, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 5: sweep_fp32_kernel<5, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 6: sweep_fp32_kernel<6, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 7: sweep_fp32_kernel<7, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      case 8: sweep_fp32_kernel<8, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (v.sweep_depth) {
     case 3: return sweep_fp32_depth<3>(v, a, L, grid, st);
     case 4: return sweep_fp32_depth<4>(v, a, L, grid, st);
@@ -936,6 +992,34 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 #undef MOLC_MOMENTS
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// Face moments from the face sums: E_f = D is / (c |f|), F_f, N_f = sums is / |f|; is = 1/scale of the state
+// (1 for FP64), |f| = hy on x-faces, hx on y-faces.  One thread per (face, group).
+__global__ void face_moments_kernel(PlanView v, Layout L, const double *scale, double c, double hx, double hy,
+                                    molc_moments out) {
+  const int64_t n = (int64_t)v.n_faces * v.G;
+  const int nxf = (v.nx + 1) * v.ny;
+  const double is = scale ? scale[1] : 1.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = (int)(i / v.n_faces), f = (int)(i - (int64_t)g * v.n_faces);
+    const int ch = g / L.gc, gl = g - ch * L.gc;
+    const double *fa = v.facc + ((int64_t)ch * v.n_faces + f) * kOutputs * L.gc + gl;
+    const double r = is / (f < nxf ? hy : hx);
+    out.E[i] = fa[0] * r / c;
+    out.Fx[i] = fa[L.gc] * r;
+    out.Fy[i] = fa[2 * L.gc] * r;
+    out.Nxx[i] = fa[3 * L.gc] * r;
+    out.Nxy[i] = fa[4 * L.gc] * r;
+    out.Nyy[i] = fa[5 * L.gc] * r;
+  }
+}
+
+cudaError_t launch_face_moments(const PlanView &v, molc_precision prec, const double *scale, double c,
+                                const molc_moments &out, cudaStream_t st) {
+  const Layout L = layout_for(v, prec);
+  face_moments_kernel<<<grid_for((int64_t)v.n_faces * v.G, 256), 256, 0, st>>>(v, L, scale, c, v.hx, v.hy, out);
   return cudaGetLastError();
 }
 

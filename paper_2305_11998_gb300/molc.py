@@ -19,6 +19,7 @@ RAYS_UNIFORM, RAYS_PAPER = 0, 1
 AREA_RENORM = 1
 HOST_ONLY = 2
 AUTOTUNE = 4
+FACES = 8
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 LAYOUT = {"uniform": RAYS_UNIFORM, "paper": RAYS_PAPER, RAYS_UNIFORM: RAYS_UNIFORM, RAYS_PAPER: RAYS_PAPER}
 STATUS = {0: "MOLC_OK", 1: "MOLC_ERR_INVALID_ARG", 2: "MOLC_ERR_OUT_OF_MEMORY", 3: "MOLC_ERR_CUDA",
@@ -31,7 +32,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
-            "molc_batch_destroy", "molc_grey_coefficients")
+            "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments")
 
 
 class MolcError(RuntimeError):
@@ -62,7 +63,7 @@ class _Info(C.Structure):
     _fields_ = [("G", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_dir", C.c_int), ("n_azim_pairs", C.c_int),
                 ("n_polar", C.c_int), ("n_tracks", C.c_int64), ("n_track_segments", C.c_int64),
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
-                ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int)]
+                ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int)]
 
 
 class _SweepArgs(C.Structure):
@@ -97,6 +98,7 @@ def load(build_if_needed: bool = True):
                                                 C.POINTER(_Moments), vp]),
         "molc_closure": (C.c_int, [vp, C.POINTER(_Moments), C.c_double, vp, vp, vp, vp, vp]),
         "molc_grey_coefficients": (C.c_int, [vp, C.POINTER(_Moments), vp, vp, vp, vp]),
+        "molc_face_moments": (C.c_int, [vp, C.c_int, vp, C.c_double, C.POINTER(_Moments), vp]),
         "molc_intensity_export": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
         "molc_intensity_import": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp, vp]),
         "molc_tracks_export": (C.c_int, [vp, i64p, i64p, dp, ip, ip, dp, dp]),
@@ -166,13 +168,14 @@ class PlanInfo:
     fp32_groups_per_warp: int
     device_bytes: int
     fp32_sweep_depth: int
+    n_faces: int
 
 
 class Plan:
     """molc_create / molc_sweep / molc_closure on torch tensors (float64, CUDA, contiguous)."""
 
     def __init__(self, nx, ny, lx, ly, mu, cos_phi, sin_phi, w, G, spacing, layout="uniform", renorm=True,
-                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False):
+                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False, faces=False):
         lib = load()
         self._lib = lib
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, cos_phi, sin_phi, w)]
@@ -183,7 +186,7 @@ class Plan:
         h = C.c_void_p()
         _check(lib.molc_create(C.byref(grid), C.byref(quad), C.byref(groups), float(spacing), LAYOUT[layout],
                                (AREA_RENORM if renorm else 0) | (HOST_ONLY if host_only else 0) |
-                               (AUTOTUNE if autotune else 0), C.byref(h)))
+                               (AUTOTUNE if autotune else 0) | (FACES if faces else 0), C.byref(h)))
         self._h = h
         inf = _Info()
         _check(lib.molc_plan_get_info(h, C.byref(inf)))
@@ -193,11 +196,11 @@ class Plan:
 
     @classmethod
     def from_workload(cls, wl, quad=None, spacing=None, layout="uniform", renorm=True, host_only=False,
-                      autotune=False):
+                      autotune=False, faces=False):
         q = quad if quad is not None else wl.quadrature()
         return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G,
                    wl.spacing if spacing is None else spacing, layout, renorm, edges=wl.edges(), host_only=host_only,
-                   autotune=autotune)
+                   autotune=autotune, faces=faces)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -270,6 +273,14 @@ class Plan:
         if grey:
             f["grey"] = fg
         return f
+
+    def face_moments(self, prec, I, c, stream=None):
+        """molc_face_moments: {E, Fx, Fy, Nxx, Nxy, Nyy} of the faces, each [G][n_faces], of the last sweep."""
+        nf = self.info.n_faces
+        out = {k: torch.empty((self.G, nf), dtype=torch.float64, device=I.device) for k in MOMENTS}
+        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        _check(self._lib.molc_face_moments(self._h, PREC[prec], _ptr(I), float(c), C.byref(m), _stream(stream)))
+        return out
 
     GREY = ("kappa_E", "kappa_B", "KRx", "KRy", "eta_x", "eta_y")
 
