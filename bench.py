@@ -482,10 +482,64 @@ def run_refine(args):
                       "per_spacing": rows}), flush=True)
 
 
+def run_paper_layout(args):
+    """The paper's characteristic grid at its production spacing: 40 x 40 cells on 6 cm (h_mat = 0.15 cm),
+    h_moc = 1e-3 cm vertex bands, 17 groups, 4 x 36 = 144 directions; FP32 step (sweep + closure) timed over
+    the steps, FP64 sweep beside it, FP32 moments compared with FP64 after one step."""
+    import torch
+    import paper_2305_11998_gb300 as molc
+    from paper_2305_11998_gb300 import multistep
+    dev = torch.device("cuda")
+    wl = synth.Workload("fc40_paper", 40, 40, 6.0, 17, 0.001, 100.0, 4, 36, 150, 1, n_fronts=1)
+    d = wl.inputs(0)
+    q = wl.quadrature()
+    P = molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, 1e-3, "paper", False,
+                  autotune=True)
+    k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
+    I = P.new_intensity("fp32", dev)
+    P.intensity_init("fp32", I, B)
+    mom = P.new_moments(dev)
+    first = {kk: v.cpu().numpy() for kk, v in P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=mom).items()}
+    for _ in range(max(args.warmup, 0)):
+        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=mom)
+        P.closure(mom, wl.c)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.kernel_timing(True)
+    e0.record()
+    for _ in range(args.steps):
+        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=mom)
+        P.closure(mom, wl.c)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    parts, n = P.kernel_time_parts()
+    del I
+    torch.cuda.empty_cache()
+    I64 = P.new_intensity("fp64", dev)
+    P.intensity_init("fp64", I64, B)
+    e0.record()
+    ref = {kk: v.cpu().numpy() for kk, v in P.sweep("fp64", k, B, wl.c, wl.dt, I64, bnd, out=mom).items()}
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    info = P.info
+    print(json.dumps({"workload": "fc40_paper: 40x40 cells on 6 cm, paper layout h_moc = 1e-3 cm, 17 groups, "
+                                  "4x36 directions", "n_tracks": info.n_tracks, "updates_per_step": info.n_updates,
+                      "fp32_ms_per_step": ms, "fp32_updates_per_s": info.n_updates / (ms / 1e3),
+                      "kernels_ms": {kk: v / max(n, 1) for kk, v in parts.items()},
+                      "fp64_sweep_ms": ms64, "fp64_updates_per_s": info.n_updates / (ms64 / 1e3),
+                      "fp32_vs_fp64_first_step": multistep.precision_errors(first, ref, wl.c),
+                      "fp32_sweep_depth": info.fp32_sweep_depth, "device_status": P.device_status()}), flush=True)
+    P.close()
+
+
 def main():
     args = parse()
     if args.kernel_only:
         run_kernel_only(args)
+    elif args.workload == "paper40":
+        run_paper_layout(args)
     elif args.workload == "refine":
         run_refine(args)
     elif args.workload == "batch64":

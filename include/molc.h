@@ -180,7 +180,9 @@ molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa
  *  - There is ONE array per device, shared by every plan and stream in the process: calls that can overlap in
  *    time on the same device (different streams, or different host threads) race on it and give wrong
  *    results.  Serialise them, e.g. issue them all on one stream.
- *  - Sweep-kernel timing (molc_kernel_timing) does not record this call. */
+ *  - Sweep-kernel timing (molc_kernel_timing) does not record this call.
+ *  - A FP32 plan with cells crossed by more than 256 characteristic segments (very fine ray spacing) also sums
+ *    per-part partials in a buffer of its own, allocated by molc_create, as molc_sweep does. */
 molc_status molc_sweep_static_scratch(molc_plan *plan, molc_precision prec, const double *kappa,
                                       const double *B, double c, double dt, void *I, const double *bnd,
                                       const molc_moments *out, molc_stream stream);

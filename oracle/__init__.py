@@ -21,7 +21,7 @@ _SRC = os.path.join(_HERE, "molc_oracle.cpp")
 _OUT = os.path.join(_HERE, "_build", "libmolc_oracle.so")
 _lib = None
 
-MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy", "Nzz", "absFx", "absFy", "absNxy")
+MOMENTS = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy", "Nzz", "absFx", "absFy", "absNxy", "absBNxy", "absBFx", "absBFy")
 PREC = {"double": 0, "quad": 1}
 
 

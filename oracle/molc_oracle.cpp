@@ -320,7 +320,8 @@ template <class R> static void canonical_offsets(const oracle_geom &g, const Geo
 
 // Moments accumulated per block of directions (fixed blocks, merged in block order: results do not depend
 // on the number of threads).
-enum { MOM_D = 0, MOM_FX, MOM_FY, MOM_NXX, MOM_NXY, MOM_NYY, MOM_NZZ, MOM_AFX, MOM_AFY, MOM_ANXY, N_MOM };
+enum { MOM_D = 0, MOM_FX, MOM_FY, MOM_NXX, MOM_NXY, MOM_NYY, MOM_NZZ, MOM_AFX, MOM_AFY, MOM_ANXY, MOM_BNXY, MOM_BFX,
+       MOM_BFY, N_MOM };
 
 template <class R>
 static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
@@ -377,6 +378,9 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
       a[MOM_AFX * ncell + i] += wA * rabs(Ox) * dev;
       a[MOM_AFY * ncell + i] += wA * rabs(Oy) * dev;
       a[MOM_ANXY * ncell + i] += wA * rabs(Ox * Oy) * dev;
+      a[MOM_BNXY * ncell + i] += wA * rabs(Ox * Oy) * B_i;
+      a[MOM_BFX * ncell + i] += wA * rabs(Ox) * B_i;
+      a[MOM_BFY * ncell + i] += wA * rabs(Oy) * B_i;
       if (I_new) I_new[seg * Gsub + gi] = store_dev ? (double)(Ibar - B_i) : (double)Ibar;
       I = Iout;
     }
@@ -515,8 +519,10 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 //                                with prev_dev != 0 their deviations from this step's B of the segment's cell
 //                                (I^{n-1} = B + I_prev formed in the oracle's precision)
 //   groups     [ngroups]         subset of groups to sweep, or NULL for all (Gsub = G)
-//   out        [10][Gsub][ncell] E, Fx, Fy, Nxx, Nxy, Nyy, Nzz, then the conditioning magnitudes
-//                                (1/V) sum omega A |Omega_x| |Ibar - B|, same with |Omega_y|, |Omega_x Omega_y|
+//   out        [13][Gsub][ncell] E, Fx, Fy, Nxx, Nxy, Nyy, Nzz, then the conditioning magnitudes
+//                                (1/V) sum omega A |Omega_x| |Ibar - B|, same with |Omega_y|, |Omega_x Omega_y|,
+//                                and the Planck parts (1/V) sum omega A |Omega_x Omega_y| B, same with |Omega_x|,
+//                                |Omega_y|
 //   I_new      [nseg][Gsub]      canonical segment averages Ibar (may be NULL); with store_dev != 0 the
 //                                deviations Ibar - B of the segment's cell, formed in the oracle's precision
 //   I_exit     [nrays][Gsub]     intensity leaving each characteristic (may be NULL)

@@ -96,6 +96,9 @@ struct molc_plan {
   int4 *d_gent = nullptr;
   int64_t *d_boff = nullptr;
   int2 *d_seg_face = nullptr;
+  int2 *d_munit = nullptr;
+  int4 *d_mmulti = nullptr;
+  double *d_mscratch = nullptr;
   double *d_facc = nullptr;
   size_t facc_elems = 0;
   int *d_block_order = nullptr;
@@ -307,7 +310,8 @@ void free_device(molc_plan *p) {
   free_events(p);
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
                   p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
-                  p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order, p->d_seg_face, p->d_facc};
+                  p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order, p->d_seg_face, p->d_facc,
+                  p->d_munit, p->d_mmulti, p->d_mscratch};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -797,6 +801,20 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         gent[e].z = 0;   // zero area
       }
   }
+  // Work units of the moment gather: each cell's entry list in parts of at most kPartEntries entries, so that a
+  // cell crossed by very many characteristics (fine ray spacing) is summed by several threads; the parts of a
+  // split cell are added in order by a second kernel (deterministic).
+  std::vector<int2> munit;
+  std::vector<int4> mmulti;
+  if (nch32) {
+    static_assert(kPartEntries % kGatherPad == 0, "parts must hold whole gather batches");
+    for (int i = 0; i < ncell; ++i) {
+      const int64_t n = cell_off[i + 1] - cell_off[i];
+      const int parts = (int)std::max<int64_t>(1, (n + kPartEntries - 1) / kPartEntries);
+      if (parts > 1) mmulti.push_back(make_int4(i, (int)munit.size(), parts, 0));
+      for (int k = 0; k < parts; ++k) munit.push_back(make_int2(i, k));
+    }
+  }
 
   PlanView &v = p->view;
   v.nx = g.nx;
@@ -866,6 +884,10 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_gent, gent.data(), gent.size(), "cell entries")
   UP(d_boff, boff.data(), boff.size(), "state bundles")
   UP(d_seg_face, seg_face.data(), seg_face.size(), "segment faces")
+  UP(d_munit, munit.data(), munit.size(), "moment units")
+  UP(d_mmulti, mmulti.data(), mmulti.size(), "split cells")
+  UP(d_mscratch, (const double *)nullptr, mmulti.empty() ? 0 : (size_t)nch32 * munit.size() * kOutputs * gc32,
+     "moment partials")
   UP(d_facc, (const double *)nullptr, p->facc_elems, "face accumulators")
   UP(d_block_order, block_order.data(), block_order.size(), "block order")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
@@ -898,6 +920,11 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.block_order = p->d_block_order;
   v.seg_face = p->d_seg_face;
   v.facc = p->d_facc;
+  v.munit = p->d_munit;
+  v.n_munits = (int64_t)munit.size();
+  v.mmulti = p->d_mmulti;
+  v.n_mmulti = (int)mmulti.size();
+  v.mscratch = p->d_mscratch;
   if ((flags & MOLC_AUTOTUNE) && nch32) {
     st = autotune(p);
     if (st != MOLC_OK) {
@@ -1136,6 +1163,8 @@ struct molc_batch {
   std::vector<MomentClass> moments;
   int2 *d_closure = nullptr;
   int n_closure = 0;
+  int4 *d_combine = nullptr;
+  int n_combine = 0;
   bool bound = false;
   bool want_closure = false;
 };
@@ -1146,6 +1175,7 @@ void batch_free(molc_batch *b) {
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_prep) cudaFree(b->d_prep);
   if (b->d_closure) cudaFree(b->d_closure);
+  if (b->d_combine) cudaFree(b->d_combine);
   for (auto &c : b->sweeps)
     if (c.d_map) cudaFree(c.d_map);
   for (auto &c : b->moments)
@@ -1191,6 +1221,7 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
   std::map<int, std::vector<int4>> mo;
   std::map<int, size_t> mo_smem;
   std::vector<int2> clo;
+  std::vector<int4> comb;
   for (int i = 0; i < n; ++i) {
     const molc_plan *p = plans[i];
     const PlanView &v = p->view;
@@ -1210,8 +1241,10 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
     auto &m = mo[p->n_polar];
     for (int ch = 0; ch < L.n_chunks; ++ch) {
       const int gcount = std::min(L.gc, v.G - ch * L.gc);
-      const int64_t nb = ((int64_t)v.ncell * gcount + 127) / 128;
+      const int64_t nb = (v.n_munits * gcount + 127) / 128;
       for (int64_t k = 0; k < nb; ++k) m.push_back(make_int4(i, ch, (int)k, 0));
+      const int64_t nc = ((int64_t)v.n_mmulti * gcount + 127) / 128;
+      for (int64_t k = 0; k < nc; ++k) comb.push_back(make_int4(i, ch, (int)k, 0));
     }
     mo_smem[p->n_polar] = std::max(mo_smem[p->n_polar], (size_t)v.n_pairs * (3 * v.n_polar + 2) * sizeof(float));
     for (int k = 0; k < (v.ncell + 255) / 256; ++k) clo.push_back(make_int2(i, k));
@@ -1221,6 +1254,8 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
   b->n_prep = (int)prep.size();
   if (e == cudaSuccess) e = upload_vec(&b->d_closure, clo);
   b->n_closure = (int)clo.size();
+  if (e == cudaSuccess) e = upload_vec(&b->d_combine, comb);
+  b->n_combine = (int)comb.size();
   for (auto &kv : sw) {
     if (e != cudaSuccess) break;
     auto &lst = kv.second;
@@ -1313,6 +1348,8 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
     e = launch_moments_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: moments");
   }
+  e = launch_moments_combine_batch(b->d_inst, b->d_combine, b->n_combine, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: moments (split cells)");
   if (b->want_closure) {
     e = launch_closure_batch(b->d_inst, b->d_closure, b->n_closure, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: closure");

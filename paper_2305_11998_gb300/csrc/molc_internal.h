@@ -11,6 +11,7 @@ namespace molc {
 constexpr int kMaxPolarFP32 = 8;     // FP32 sweep: polar cosines per azimuth handled by one half-warp
 constexpr int kOutputs = 6;          // D, Fx, Fy, Nxx, Nxy, Nyy accumulators per (cell, group)
 constexpr int kGatherPad = 4;        // FP32 moments: each cell's entry list is padded to a multiple of this
+constexpr int kPartEntries = 256;    // FP32 moments: entries one thread sums (longer cell lists are split)
 constexpr int kSweepBlock = 128;     // FP32 sweep: work items (threads) per block = width of a state bundle
 constexpr size_t kMaxGatherSmem = 200 * 1024;  // FP32 moments: per-pair coefficient table in shared memory
 
@@ -63,6 +64,12 @@ struct PlanView {
   int gc32;                     // FP32 sweep: groups per chunk
   const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into gent
   const int4 *gent;             // FP32 moments: per cell, {item position, step, A/V f32 bits, 2 pair + sense}
+  const int2 *munit;            // FP32 moments: work units {cell, part}, cell-major; part k sums the cell's entries
+                                //   [kPartEntries k, kPartEntries (k + 1))
+  int64_t n_munits;
+  const int4 *mmulti;           // FP32 moments: cells split in more than one part: {cell, first unit, parts, 0}
+  int n_mmulti;
+  double *mscratch;             // FP32 moments: [chunk][unit][6][gc] partial sums of split cells (or null)
   const int64_t *boff;          // FP32 state: [n_blocks + 1] first step slot of each bundle
   const int *block_order;       // FP32 sweep: bundle swept by each block of the launch (longest first)
   int sweep_depth;              // FP32 sweep: staging depth D (one of kSweepDepths; autotuned or 4)
@@ -163,6 +170,8 @@ cudaError_t launch_sweep_fp32_batch(const BatchInst *inst, const int2 *map, int 
                                     cudaStream_t st);
 cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, int blocks, int n_polar,
                                       size_t smem, cudaStream_t st);
+// combine step of split cells: map int4 {instance, chunk, block, 0} over the instance's split cells
+cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
 cudaError_t launch_closure_batch(const BatchInst *inst, const int2 *map, int blocks, cudaStream_t st);
 
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.

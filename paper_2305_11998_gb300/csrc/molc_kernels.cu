@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_batch_kernel(const Bat
 // (NP contiguous values per segment; the lanes of a cell read one contiguous block) weighted by
 // omega (A/V) (1, Omega, Omega Omega).  A cell's entries come grouped by azimuth pair: within a pair the
 // polar folds S0 = sum_p w_p dev_p, S1 = sum_p w_p sin(zeta_p) dev_p (signed by the sense),
-// S2 = sum_p w_p sin^2(zeta_p) dev_p are summed in FP32 (a few same-pair segments); across pairs the six sums
+// S2 = sum_p w_p sin^2(zeta_p) dev_p are summed in FP32 (runs of at most kPairRun segments); across runs the six sums
 // are carried as unevaluated pairs of FP32 words (hi + lo, TwoSum: a 48-bit significand), then assembled in FP64:
 //   E = (B geo0 + D)/c, F = D_F, N_ab = B geo_ab + D_ab, and B_ref := B.
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
@@ -535,8 +535,29 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
 // Entries are taken kGatherBatch at a time so that their state loads are in flight together (each cell's entry
 // list is padded to a multiple of kGatherPad with zero-area entries of its last pair, so the batch must equal it).
 constexpr int kGatherBatch = kGatherPad;
+// An FP32 partial sum takes at most kPairRun entries (one azimuth pair) before it is added to the two-word sums:
+// a cell crossed by many characteristics of one pair (fine ray spacing) keeps the FP32 error of a few terms.
+constexpr int kPairRun = 8;
 
-// One block: threads t0 .. t0+127 of chunk ch ((cell, group) pairs, groups fastest).
+// Assembly of one (cell, group) from its six deviation sums D (state units; is = 1/scale):
+//   E = (B geo0 + D0 is)/c, F = D_F is, N_ab = B geo_ab + D_ab is, and B_ref := B.
+__device__ __forceinline__ void assemble_cell(const PlanView &v, const SweepArgs &a, int cell, int g,
+                                              const double (&D)[kOutputs]) {
+  const double is = a.scale[1];   // the deviations are in the state's scaled units (exact power of two)
+  const int64_t idx = (int64_t)g * v.ncell + cell;
+  const double B = a.B[idx];
+  a.out.E[idx] = (B * v.geo[cell] + D[0] * is) * a.inv_c;
+  a.out.Fx[idx] = D[1] * is;
+  a.out.Fy[idx] = D[2] * is;
+  a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + D[3] * is;
+  a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + D[4] * is;
+  a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + D[5] * is;
+  a.Bref[idx] = B;   // the new deviations refer to this step's B
+}
+
+// One block: threads t0 .. t0+127 of chunk ch ((unit, group) pairs, groups fastest; a unit is one part of a
+// cell's entry list).  A cell in one part is assembled here; the parts of a split cell go to the scratch
+// partials, summed in order by moments_combine.
 template <int NP>
 __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int ch,
                                                   int64_t t0) {
@@ -558,16 +579,22 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   const int gcount = min(L.gc, v.G - g0);
   const int64_t t = t0 + threadIdx.x;
   if (ch == 0 && t == 0) const_cast<double *>(a.scale)[3] = 1.0;   // the state is in this step's scale now
-  if (t >= (int64_t)v.ncell * gcount) return;
-  const int cell = (int)(t / gcount), gi = (int)(t - (int64_t)cell * gcount);
+  if (t >= v.n_munits * gcount) return;
+  const int64_t unit = t / gcount;
+  const int gi = (int)(t - unit * gcount);
+  const int2 um = v.n_mmulti ? v.munit[unit] : make_int2((int)unit, 0);   // no split cell: unit = cell
+  const int cell = um.x;
   const int g = g0 + gi;
   const int64_t item0 = (int64_t)ch * 2 * v.n_tracks * L.gc + gi;   // item of (position 0, this group)
   const float *I = (const float *)a.I;
   float hi[kOutputs], lo[kOutputs];
 #pragma unroll
   for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
-  const int64_t e0 = v.cell_off[cell], e1 = v.cell_off[cell + 1];
+  const int64_t ce0 = v.cell_off[cell], ce1 = v.cell_off[cell + 1];
+  const int64_t e0 = ce0 + (int64_t)um.y * kPartEntries, e1 = min(ce1, e0 + kPartEntries);
+  const bool split = ce1 - ce0 > kPartEntries;
   int cur = e1 > e0 ? (__ldg(&v.gent[e0].w) >> 1) : 0;
+  int run = 0;   // entries in the current FP32 partial sums
   float P0 = 0.f, P1 = 0.f, P2 = 0.f;
   auto flush = [&]() {
     const float cf = csn[2 * cur], sf = csn[2 * cur + 1];
@@ -589,11 +616,13 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) {
       const int pr = en[b].w >> 1;
-      if (pr != cur) {
+      if (pr != cur || run == kPairRun) {
         flush();
         cur = pr;
+        run = 0;
         P0 = P1 = P2 = 0.f;
       }
+      ++run;
       const float *c0 = coef + pr * 3 * NP;
       float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
@@ -613,26 +642,52 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   double D[kOutputs];
 #pragma unroll
   for (int k = 0; k < kOutputs; ++k) D[k] = f32_to_f64(hi[k]) + f32_to_f64(lo[k]);
-  const double is = a.scale[1];   // the deviations are in the state's scaled units (exact power of two)
-  const int64_t idx = (int64_t)g * v.ncell + cell;
-  const double B = a.B[idx];
-  a.out.E[idx] = (B * v.geo[cell] + D[0] * is) * a.inv_c;
-  a.out.Fx[idx] = D[1] * is;
-  a.out.Fy[idx] = D[2] * is;
-  a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + D[3] * is;
-  a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + D[4] * is;
-  a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + D[5] * is;
-  a.Bref[idx] = B;   // the new deviations refer to this step's B
+  if (!split) {
+    assemble_cell(v, a, cell, g, D);
+  } else {
+    double *ps = v.mscratch + (((int64_t)ch * v.n_munits + unit) * kOutputs) * L.gc + gi;
+#pragma unroll
+    for (int k = 0; k < kOutputs; ++k) ps[k * L.gc] = D[k];
+  }
+}
+
+// Split cells: the parts' partial sums added in part order (FP64), then assembled.  One thread per (split
+// cell, group) of chunk ch, threads t0 ...
+__device__ __forceinline__ void moments_combine_body(const PlanView &v, const SweepArgs &a, const Layout &L, int ch,
+                                                     int64_t t0) {
+  const int g0 = ch * L.gc;
+  const int gcount = min(L.gc, v.G - g0);
+  const int64_t t = t0 + threadIdx.x;
+  if (t >= (int64_t)v.n_mmulti * gcount) return;
+  const int m = (int)(t / gcount), gi = (int)(t - (int64_t)m * gcount);
+  const int4 mc = v.mmulti[m];
+  double D[kOutputs] = {0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < mc.z; ++k) {
+    const double *ps = v.mscratch + (((int64_t)ch * v.n_munits + mc.y + k) * kOutputs) * L.gc + gi;
+#pragma unroll
+    for (int o = 0; o < kOutputs; ++o) D[o] += ps[o * L.gc];
+  }
+  assemble_cell(v, a, mc.x, g0 + gi, D);
+}
+
+__global__ void __launch_bounds__(128) moments_combine_kernel(PlanView v, SweepArgs a, Layout L) {
+  moments_combine_body(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
+}
+
+__global__ void __launch_bounds__(128) moments_combine_batch_kernel(const BatchInst *inst, const int4 *map) {
+  const int4 m = map[blockIdx.x];
+  const BatchInst &b = inst[m.x];
+  moments_combine_body(b.v, b.a, b.L, m.y, (int64_t)m.z * blockDim.x);
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+__global__ void __launch_bounds__(128, NP <= 4 ? 7 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
   moments_fp32_body<NP>(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
 }
 
 // Batched: block j handles threads 128 map[j].z .. of chunk map[j].y of instance map[j].x.
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
+__global__ void __launch_bounds__(128, NP <= 4 ? 7 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
                                                                                  const int4 *map) {
   const int4 m = map[blockIdx.x];
   const BatchInst &b = inst[m.x];
@@ -966,7 +1021,7 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
     finalize_kernel<<<grid_for(v.ncell, 128), 128, 0, st>>>(v, a, L);
     return cudaGetLastError();
   }
-  const int64_t blocks = ((int64_t)v.ncell * L.gc + 127) / 128;
+  const int64_t blocks = (v.n_munits * L.gc + 127) / 128;
   if (blocks > 0x7fffffff || L.n_chunks > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)blocks, (unsigned)L.n_chunks);
   const size_t smem = (size_t)v.n_pairs * (3 * v.n_polar + 2) * sizeof(float);
@@ -992,6 +1047,10 @@ cudaError_t launch_finalize(const PlanView &v, molc_precision prec, const SweepA
 #undef MOLC_MOMENTS
     default: return cudaErrorInvalidValue;
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || v.n_mmulti == 0) return e;
+  const dim3 cgrid((unsigned)(((int64_t)v.n_mmulti * L.gc + 127) / 128), (unsigned)L.n_chunks);
+  moments_combine_kernel<<<cgrid, 128, 0, st>>>(v, a, L);
   return cudaGetLastError();
 }
 
@@ -1107,6 +1166,12 @@ cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, in
 #undef MOLC_MOMENTS_B
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  moments_combine_batch_kernel<<<blocks, 128, 0, st>>>(inst, map);
   return cudaGetLastError();
 }
 
