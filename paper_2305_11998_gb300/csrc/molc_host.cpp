@@ -800,6 +800,30 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         gent[e] = gent[pos[i] - 1];
         gent[e].z = 0;   // zero area
       }
+    // Per chunk, the (item position, step) of each entry becomes the state slot of the chunk's group 0 plus the
+    // bundle length and lane (gather_slot); chunks 1.. are written from the chunk-0 list first, chunk 0 last,
+    // in place.
+    const int64_t n_ent = cell_off[ncell];
+    gent.resize((size_t)(n_ent * nch32));
+    for (int ch = nch32 - 1; ch >= 0; --ch) {
+      const int gcount = std::min(gc32, p->G - ch * gc32);
+      const int64_t item_base = (int64_t)ch * 2 * T * gc32;
+      for (int64_t e = 0; e < n_ent; ++e) {
+        int4 r = gent[e];
+        const int64_t item = item_base + (int64_t)r.x * gcount;
+        const int64_t b = item / kSweepBlock;
+        const int lane = (int)(item % kSweepBlock);
+        const int64_t slot = (boff[b] + r.y) * kSweepBlock + lane;
+        const int64_t blen = boff[b + 1] - boff[b];
+        if ((slot >> (32 + (32 - kGatherSlotHiShift))) != 0 || blen > (int64_t)kGatherBlenMask) {
+          delete p;
+          return fail(MOLC_ERR_INVALID_ARG, "create: FP32 state too large for the moment-gather entries");
+        }
+        r.x = (int)(uint32_t)(slot & 0xffffffffLL);
+        r.y = (int)(((uint32_t)(slot >> 32) << kGatherSlotHiShift) | ((uint32_t)blen << 7) | (uint32_t)lane);
+        gent[(size_t)(ch * n_ent + e)] = r;
+      }
+    }
   }
   // Work units of the moment gather: each cell's entry list in parts of at most kPartEntries entries, so that a
   // cell crossed by very many characteristics (fine ray spacing) is summed by several threads; the parts of a
@@ -916,6 +940,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.status = p->d_status;
   v.cell_off = p->d_cell_off;
   v.gent = p->d_gent;
+  v.gent_chunk = nch32 ? cell_off[ncell] : 0;
   v.boff = p->d_boff;
   v.block_order = p->d_block_order;
   v.seg_face = p->d_seg_face;

@@ -62,8 +62,10 @@ struct PlanView {
   const int64_t *dir_seg_off;   // canonical segment offset of each direction
   int *status;
   int gc32;                     // FP32 sweep: groups per chunk
-  const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into gent
-  const int4 *gent;             // FP32 moments: per cell, {item position, step, A/V f32 bits, 2 pair + sense}
+  const int64_t *cell_off;      // FP32 moments: [ncell + 1] offsets into one chunk's gent entries
+  const int4 *gent;             // FP32 moments: [chunk][entry] {state slot bits 0-31, slot bits 32-36 << 27 |
+                                //   bundle length << 7 | lane, A/V f32 bits, 2 pair + sense} (gather_slot)
+  int64_t gent_chunk;           // FP32 moments: entries per chunk (cell_off[ncell])
   const int2 *munit;            // FP32 moments: work units {cell, part}, cell-major; part k sums the cell's entries
                                 //   [kPartEntries k, kPartEntries (k + 1))
   int64_t n_munits;
@@ -89,6 +91,20 @@ constexpr int kSweepDepths[] = {3, 4, 6};   // compiled staging depths of the FP
 // item = chunk * 2 T gc + pos[sense] * gcount + g_local, pos = TrackDev::pos (pair, then sense, then track).
 __host__ __device__ inline int64_t bundle_index(const int64_t *boff, int64_t item, int s, int NP) {
   return ((boff[item / kSweepBlock] + s) * kSweepBlock + item % kSweepBlock) * NP;
+}
+
+// A moment-gather entry addresses the state slot of group 0 of its chunk directly: slot = (boff[b] + step) 128
+// + lane for the item of group 0 at lane `lane` of bundle b.  Group gi of the same (track, sense) is item + gi:
+// the same bundle while lane + gi < 128, else lane + gi - 128 of bundle b + 1, which starts blen(b) slots of
+// 128 later.  Packing limits (checked by the planner): slot < 2^37, bundle length < 2^20.
+constexpr int kGatherSlotHiShift = 27;
+constexpr unsigned kGatherBlenMask = 0xFFFFFu;
+__host__ __device__ inline int64_t gather_slot(int ex, int ey, int gi) {
+  const unsigned y = (unsigned)ey;
+  int64_t slot = (int64_t)(((uint64_t)(y >> kGatherSlotHiShift) << 32) | (unsigned)ex) + gi;
+  if ((int)(y & (kSweepBlock - 1)) + gi >= kSweepBlock)
+    slot += ((int64_t)((y >> 7) & kGatherBlenMask) - 1) * kSweepBlock;
+  return slot;
 }
 
 // Group tiling of the opaque intensity state: groups are tiled in chunks of `gc` groups.  FP64 state: within a

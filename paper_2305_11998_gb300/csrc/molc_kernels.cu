@@ -585,7 +585,7 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   const int2 um = v.n_mmulti ? v.munit[unit] : make_int2((int)unit, 0);   // no split cell: unit = cell
   const int cell = um.x;
   const int g = g0 + gi;
-  const int64_t item0 = (int64_t)ch * 2 * v.n_tracks * L.gc + gi;   // item of (position 0, this group)
+  const int4 *gent = v.gent + ch * v.gent_chunk;
   const float *I = (const float *)a.I;
   float hi[kOutputs], lo[kOutputs];
 #pragma unroll
@@ -593,7 +593,7 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   const int64_t ce0 = v.cell_off[cell], ce1 = v.cell_off[cell + 1];
   const int64_t e0 = ce0 + (int64_t)um.y * kPartEntries, e1 = min(ce1, e0 + kPartEntries);
   const bool split = ce1 - ce0 > kPartEntries;
-  int cur = e1 > e0 ? (__ldg(&v.gent[e0].w) >> 1) : 0;
+  int cur = e1 > e0 ? (__ldg(&gent[e0].w) >> 1) : 0;
   int run = 0;   // entries in the current FP32 partial sums
   float P0 = 0.f, P1 = 0.f, P2 = 0.f;
   auto flush = [&]() {
@@ -608,11 +608,10 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   for (int64_t e = e0; e < e1; e += kGatherBatch) {
     int4 en[kGatherBatch];
 #pragma unroll
-    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(v.gent + e + b);
+    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(gent + e + b);
     float dv[kGatherBatch][NP];
 #pragma unroll
-    for (int b = 0; b < kGatherBatch; ++b)
-      load_dev_cg<NP>(I + bundle_index(v.boff, item0 + (int64_t)en[b].x * gcount, en[b].y, NP), dv[b]);
+    for (int b = 0; b < kGatherBatch; ++b) load_dev_cg<NP>(I + gather_slot(en[b].x, en[b].y, gi) * NP, dv[b]);
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) {
       const int pr = en[b].w >> 1;
