@@ -591,9 +591,11 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
 #pragma unroll
   for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
   const int64_t ce0 = v.cell_off[cell], ce1 = v.cell_off[cell + 1];
-  const int64_t e0 = ce0 + (int64_t)um.y * kPartEntries, e1 = min(ce1, e0 + kPartEntries);
+  const int64_t e0 = ce0 + (int64_t)um.y * kPartEntries;
+  const int ne = (int)min(ce1 - e0, (int64_t)kPartEntries);   // entries of this part (a multiple of kGatherBatch)
   const bool split = ce1 - ce0 > kPartEntries;
-  int cur = e1 > e0 ? (__ldg(&gent[e0].w) >> 1) : 0;
+  const int4 *ep = gent + e0;
+  int cur = ne > 0 ? (__ldg(&ep->w) >> 1) : 0;
   int run = 0;   // entries in the current FP32 partial sums
   float P0 = 0.f, P1 = 0.f, P2 = 0.f;
   auto flush = [&]() {
@@ -605,10 +607,10 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
     two_sum_add(hi[4], lo[4], (cf * sf) * P2);
     two_sum_add(hi[5], lo[5], (sf * sf) * P2);
   };
-  for (int64_t e = e0; e < e1; e += kGatherBatch) {
+  for (int e = 0; e < ne; e += kGatherBatch) {
     int4 en[kGatherBatch];
 #pragma unroll
-    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(gent + e + b);
+    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + b);
     float dv[kGatherBatch][NP];
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) load_dev_cg<NP>(I + gather_slot(en[b].x, en[b].y, gi) * NP, dv[b]);
@@ -636,7 +638,7 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
       P2 = fmaf(af, S2, P2);
     }
   }
-  if (e1 > e0) flush();
+  if (ne > 0) flush();
   // FP64 work here is per (cell, group), not per update: conversions by integer operations, one add per sum
   double D[kOutputs];
 #pragma unroll
@@ -680,13 +682,13 @@ __global__ void __launch_bounds__(128) moments_combine_batch_kernel(const BatchI
 }
 
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 7 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
   moments_fp32_body<NP>(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
 }
 
 // Batched: block j handles threads 128 map[j].z .. of chunk map[j].y of instance map[j].x.
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 7 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
+__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
                                                                                  const int4 *map) {
   const int4 m = map[blockIdx.x];
   const BatchInst &b = inst[m.x];

@@ -126,6 +126,11 @@ def _check(rc: int):
         raise MolcError(rc, load().molc_last_error().decode())
 
 
+def _check_f64(t, n: int, name: str):
+    if t.dtype != torch.float64 or t.numel() != n:
+        raise ValueError(f"{name}: expected {n} float64 elements")
+
+
 def _dp(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -263,9 +268,14 @@ class Plan:
                                                    _ptr(I), _ptr(bnd), C.byref(m), _stream(stream)))
         return out
 
-    def closure(self, moments, c, grey=False, stream=None):
-        f = {k: torch.empty((self.G, self.ncell), dtype=torch.float64, device=moments["E"].device)
-             for k in ("fxx", "fxy", "fyy")}
+    def closure(self, moments, c, grey=False, stream=None, out=None):
+        """molc_closure: {fxx, fxy, fyy} ([G][ncell] each, written into `out` when given) and, with grey, the
+        E-weighted spectral averages [3][ncell]."""
+        f = out if out is not None else {
+            k: torch.empty((self.G, self.ncell), dtype=torch.float64, device=moments["E"].device)
+            for k in ("fxx", "fxy", "fyy")}
+        for k in ("fxx", "fxy", "fyy"):
+            _check_f64(f[k], self.G * self.ncell, k)
         fg = torch.empty((3, self.ncell), dtype=torch.float64, device=moments["E"].device) if grey else None
         m = _Moments(*[moments[k].data_ptr() for k in MOMENTS])
         _check(self._lib.molc_closure(self._h, C.byref(m), float(c), _ptr(f["fxx"]), _ptr(f["fxy"]),
