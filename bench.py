@@ -493,6 +493,7 @@ def run_refine(args):
     t_seq = time.perf_counter() - t0
     Pref.close()
     rows = []
+    E_last = {"fp64": [], "fp32": []}   # grey E (sum over groups) after the last step, per spacing
     for div in (2, 4, 8, 16):
         P = molc.Plan.from_workload(wl, spacing=wl.h / div, autotune=True)
         n_upd = P.info.n_updates
@@ -500,6 +501,8 @@ def run_refine(args):
         m64 = multistep.run_sequence(P, wl, Ts, "fp64", on_step=lambda n, m, ms: t64.append(ms))
         torch.cuda.empty_cache()
         m32 = multistep.run_sequence(P, wl, Ts, "fp32", on_step=lambda n, m, ms: t32.append(ms))
+        E_last["fp64"].append(m64[-1]["E"].sum(axis=0))
+        E_last["fp32"].append(m32[-1]["E"].sum(axis=0))
         worst = {}
         for a, b in zip(m32, m64):
             for k, v in multistep.precision_errors(a, b, wl.c).items():
@@ -512,6 +515,11 @@ def run_refine(args):
                      "device_status": P.device_status()})
         P.close()
         torch.cuda.empty_cache()
+    # the paper's refinement norms of the grey E after the last step: ||dE_h|| = ||E_h - E_2h||_L2, rho_h
+    vol = (wl.L / wl.nx) * (wl.L / wl.ny)
+    for prec in ("fp64", "fp32"):
+        for r, nr in zip(rows, multistep.refinement_norms(E_last[prec], vol)):
+            r[f"refinement_E_{prec}"] = nr
     T = Ts[-1]
     print(json.dumps({"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, {wl.n_polar}x{wl.n_azim} "
                                   f"directions, cold start, left edge at 1 keV, {steps} steps",

@@ -78,3 +78,18 @@ def precision_errors(m32, m64, c):
         f64 = np.where(ok, m64[n] / (c * np.where(ok, E, 1.0)), 0.0)
         out[k] = float(np.max(np.abs(f32 - f64)))
     return out
+
+
+def refinement_norms(ys, cell_volume):
+    """Mesh-refinement norms in the paper's convention (Sec. 5): for solutions y_h on successively halved
+    spacings (ys[0] coarsest), ||dy_h|| = ||y_h - y_{2h}||_{L2} (cell sums weighted by the cell volume) for every
+    spacing after the first, and the estimated convergence rate rho_h = ||dy_{2h}|| / ||dy_h|| for every spacing
+    after the second.  Returns [{"norm": ..., "rho": ...}] aligned with ys (None where undefined)."""
+    out = [{"norm": None, "rho": None}]
+    for i in range(1, len(ys)):
+        d = np.asarray(ys[i], dtype=np.float64) - np.asarray(ys[i - 1], dtype=np.float64)
+        out.append({"norm": float(np.sqrt(cell_volume * np.sum(d * d))), "rho": None})
+    for i in range(2, len(ys)):
+        if out[i]["norm"] > 0:
+            out[i]["rho"] = out[i - 1]["norm"] / out[i]["norm"]
+    return out
