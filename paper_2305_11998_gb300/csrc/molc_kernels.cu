@@ -189,19 +189,27 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
 // afterwards from the swept state (moments_fp32_kernel).
 // ---------------------------------------------------------------------------------------------------------
 
-// (1 - e^-tau)/tau and e^-tau in FP32.  With h = e^(-tau/2) (ex2.approx):
-//   tau < 1/2:  E1 = h sinh(tau/2) / (tau/2), the even Taylor series in y = tau^2/4 to y^3 (truncation
-//               < 5e-11 relative), free of cancellation;
+// 2^x (ex2.approx.ftz.f32: the SFU's base-2 exponential).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// (1 - e^-tau)/tau and e^-tau in FP32, from a = tau/2.  With h = e^-a = 2^(-a log2 e):
+//   tau < 1/2:  E1 = h sinh(a) / a, the even Taylor series in y = a^2 to y^3 (truncation < 5e-11 relative),
+//               free of cancellation;
 //   tau >= 1/2: E1 = (1 - e^-tau) / tau (1 - e^-tau > 0.39, no cancellation).
 // e^-tau = h^2.  inv_tau is 1/tau.
-__device__ __forceinline__ void attenuation(float tau, float inv_tau, float &E1, float &ex) {
-  const float h = __expf(-0.5f * tau);
+__device__ __forceinline__ void attenuation(float a, float inv_tau, float &E1, float &ex) {
+  constexpr float kMinusLog2e = -1.4426950408889634f;
+  const float h = ex2_approx(a * kMinusLog2e);
   ex = h * h;
-  const float y = 0.25f * tau * tau;
+  const float y = a * a;
   float p = fmaf(y, 1.f / 5040.f, 1.f / 120.f);
   p = fmaf(p, y, 1.f / 6.f);
   p = fmaf(p, y, 1.f);
-  E1 = tau < 0.5f ? h * p : (1.f - ex) * inv_tau;
+  E1 = a < 0.25f ? h * p : (1.f - ex) * inv_tau;
 }
 
 // FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU): exponent rebiased by
@@ -382,11 +390,11 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   const float4 *cd = a.cdat + cbase;
   const float *cdB = a.cdB + cbase;
 
-  float inv_sinz[NP], sinz[NP], wf[FACES ? NP : 1];
+  float half_inv_sinz[NP], sinz[NP], wf[FACES ? NP : 1];   // 1/(2 sin zeta): tau/2 = kappa~ l half_inv_sinz
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const PolarDev pd = v.polar[tr.pair * NP + p];
-    inv_sinz[p] = pd.inv_sinzf;
+    half_inv_sinz[p] = 0.5f * pd.inv_sinzf;
     sinz[p] = pd.sinzf;
     if constexpr (FACES) wf[p] = pd.wf;
   }
@@ -448,9 +456,8 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
           for (int p = 0; p < NP; ++p) dv[p] = sdev[u][tid * NP + p];
         }
-#pragma unroll
-        for (int p = 0; p < NP; ++p) dv[p] *= rescale;
         const float4 q = stab[u][tid];
+        const float qy = q.y * rescale;   // rescale (a power of two) brings the stored deviations to this scale
         const float dB = sdB[u][tid];
         // step s
         const float len = __int_as_float(recs[u].y);
@@ -486,8 +493,8 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           float E1, ex;
-          attenuation(kl * inv_sinz[p], sinz[p] * rkl, E1, ex);
-          const float d = fmaf(dv[p], q.y, dB);
+          attenuation(kl * half_inv_sinz[p], sinz[p] * rkl, E1, ex);
+          const float d = fmaf(dv[p], qy, dB);
           const float x = psi[p] - d;
           dv[p] = fmaf(x, E1, d);
           psi[p] = fmaf(x, ex, d);
