@@ -191,9 +191,12 @@ def run_ours(args):
     P.intensity_init("fp32", I, B_d)
     mom = P.new_moments(dev)
 
+    fac = {k: torch.empty((G, ncell), dtype=torch.float64, device=dev) for k in ("fxx", "fxy", "fyy")}
+    # kernels of one FP32 step: state scale, cell table, sweep, moment gather (+ the combine of split cells)
+    launches_per_step = 4 + (1 if info.n_split_cells else 0)
+
     def step():
-        P.sweep("fp32", k_d, B_d, wl.c, wl.dt, I, bnd_d, out=mom)
-        return P.closure(mom, wl.c)
+        return P.sweep_closure("fp32", k_d, B_d, wl.c, wl.dt, I, bnd_d, out=mom, f=fac)[1]
 
     def barrier():
         if ws > 1:
@@ -291,8 +294,7 @@ def run_ours(args):
                 if n >= 2:
                     cs.wait_event(ev_out[j])
                 k_, B_, bnd_ = ins_d[j]
-                P.sweep("fp32", k_, B_, wl.c, wl.dt, I, bnd_, out=moms[j], stream=cs)
-                P.closure(moms[j], wl.c, out=fes[j], stream=cs)
+                P.sweep_closure("fp32", k_, B_, wl.c, wl.dt, I, bnd_, out=moms[j], f=fes[j], stream=cs)
                 ev_done[j].record(cs)
                 with torch.cuda.stream(s_out):
                     s_out.wait_event(ev_done[j])
@@ -328,8 +330,7 @@ def run_ours(args):
         n64 = 2
         e0.record()
         for _ in range(n64):
-            P.sweep("fp64", k_d, B_d, wl.c, wl.dt, I64, bnd_d, out=mom)
-            P.closure(mom, wl.c)
+            P.sweep_closure("fp64", k_d, B_d, wl.c, wl.dt, I64, bnd_d, out=mom, f=fac)
         e1.record()
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / n64
@@ -349,9 +350,9 @@ def run_ours(args):
                                        f"directions, spacing h/{wl.spacing_div}, three fronts; one instance per GPU",
                            "updates_per_step_per_gpu": info.n_updates,
                            "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
-                           "step": "molc_sweep (FP32) + molc_closure"},
+                           "step": "molc_sweep_closure (FP32 sweep, moments and Eddington factors in one call)"},
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 5 * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
         print(json.dumps(line), flush=True)
     P.close()
     if ws > 1:

@@ -107,6 +107,8 @@ typedef struct {
   size_t device_bytes;      /* device memory the plan holds */
   int fp32_sweep_depth;     /* staging depth of the FP32 sweep (steps of look-ahead; MOLC_AUTOTUNE picks it) */
   int n_faces;              /* MOLC_FACES: (nx + 1) ny x-faces then nx (ny + 1) y-faces; else 0 */
+  int n_split_cells;        /* FP32 moments: cells crossed by more than 256 segment entries, summed in parts and
+                               combined by one more kernel launch per sweep (0: no such launch) */
 } molc_plan_info;
 
 /* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,
@@ -227,6 +229,15 @@ void molc_batch_destroy(molc_batch *batch);
  * A cell with E = 0 gets f = 0. */
 molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c, double *fxx, double *fxy,
                          double *fyy, double *f_grey, molc_stream stream);
+
+/* One backward-Euler step and the Eddington factors of its moments in one call (Eqs. 7, 11-15): the same as
+ * molc_sweep followed by molc_closure(plan, out, c, fxx, fxy, fyy, NULL, stream), bit for bit, with the factors
+ * formed where each cell's moments are assembled (no second pass over the moments).  fxx, fxy, fyy: device
+ * [G][cell], caller-owned, all non-NULL (else MOLC_ERR_INVALID_ARG).  Other arguments, errors and
+ * asynchrony as molc_sweep; the grey average is not formed (molc_closure gives it). */
+molc_status molc_sweep_closure(molc_plan *plan, molc_precision prec, const double *kappa, const double *B, double c,
+                               double dt, void *I, const double *bnd, const molc_moments *out, double *fxx,
+                               double *fxy, double *fyy, molc_stream stream);
 
 /* Face-average moments of the last molc_sweep in precision prec (plans created with MOLC_FACES), the
  * quantities of the face Eddington tensor (Eq. 16): for every face f and group, with I_{k,s} the intensity at

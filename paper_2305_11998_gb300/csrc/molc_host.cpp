@@ -36,6 +36,10 @@ molc_status cuda_fail(cudaError_t e, const char *what) {
   return fail(e == cudaErrorMemoryAllocation ? MOLC_ERR_OUT_OF_MEMORY : MOLC_ERR_CUDA, "%s: %s", what,
               cudaGetErrorString(e));
 }
+molc_status cuda_fail(cudaError_t e, const char *who, const char *what) {
+  return fail(e == cudaErrorMemoryAllocation ? MOLC_ERR_OUT_OF_MEMORY : MOLC_ERR_CUDA, "%s: %s: %s", who, what,
+              cudaGetErrorString(e));
+}
 
 // Compensated (double-double) accumulator for the per-cell geometric moments.
 struct Acc2 {
@@ -67,6 +71,7 @@ struct molc_plan {
   molc_layout layout = MOLC_RAYS_UNIFORM;
   unsigned flags = 0;
   bool host_only = false;
+  int n_split_cells = 0;      // FP32 moments: cells whose entry list is summed in parts (known to host-only plans too)
   double hx = 0, hy = 0, V = 0;
   // host copies of the characteristic grid
   std::vector<PairDev> pairs;
@@ -839,6 +844,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       for (int k = 0; k < parts; ++k) munit.push_back(make_int2(i, k));
     }
   }
+  p->n_split_cells = (int)mmulti.size();
 
   PlanView &v = p->view;
   v.nx = g.nx;
@@ -978,6 +984,7 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->device_bytes = p->device_bytes;
   info->fp32_sweep_depth = p->view.sweep_depth;
   info->n_faces = p->view.n_faces;
+  info->n_split_cells = p->n_split_cells;
   return MOLC_OK;
 }
 
@@ -1039,13 +1046,15 @@ molc_status molc_intensity_init(molc_plan *p, molc_precision prec, void *I, cons
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "intensity_init");
 }
 
-molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, const double *B, double c,
-                       double dt, void *I, const double *bnd, const molc_moments *out, molc_stream stream) {
-  if (!p || !kappa || !B || !I || !bnd || !out) return fail(MOLC_ERR_INVALID_ARG, "sweep: NULL argument");
+// molc_sweep, and with factor outputs molc_sweep_closure (`who` names the entry point in error messages).
+static molc_status sweep_step(molc_plan *p, molc_precision prec, const double *kappa, const double *B, double c,
+                              double dt, void *I, const double *bnd, const molc_moments *out, double *fxx,
+                              double *fxy, double *fyy, molc_stream stream, const char *who) {
+  if (!p || !kappa || !B || !I || !bnd || !out) return fail(MOLC_ERR_INVALID_ARG, "%s: NULL argument", who);
   if (!out->E || !out->Fx || !out->Fy || !out->Nxx || !out->Nxy || !out->Nyy)
-    return fail(MOLC_ERR_INVALID_ARG, "sweep: NULL moment array");
-  if (!finite_pos(c) || !finite_pos(dt)) return fail(MOLC_ERR_INVALID_ARG, "sweep: need c > 0 and dt > 0");
-  molc_status s = check_prec(p, prec, "sweep");
+    return fail(MOLC_ERR_INVALID_ARG, "%s: NULL moment array", who);
+  if (!finite_pos(c) || !finite_pos(dt)) return fail(MOLC_ERR_INVALID_ARG, "%s: need c > 0 and dt > 0", who);
+  molc_status s = check_prec(p, prec, who);
   if (s) return s;
   DeviceGuard dg(p->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1066,34 +1075,49 @@ molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, c
   a.acc = p->d_acc;
   a.items = p->d_items32;
   a.n_items = p->n_items32;
+  a.fxx = fxx;
+  a.fxy = fxy;
+  a.fyy = fyy;
   cudaError_t e = cudaSuccess;
   if (p->d_facc) {
     e = cudaMemsetAsync(p->d_facc, 0, p->facc_elems * sizeof(double), st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep: clear face accumulators");
+    if (e != cudaSuccess) return cuda_fail(e, who, "clear face accumulators");
   }
   if (prec == MOLC_FP64) {   // the FP32 path gathers its moments and has no accumulators
     e = cudaMemsetAsync(p->d_acc, 0, (size_t)p->G * p->view.ncell * kOutputs * sizeof(double), st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep: clear accumulators");
+    if (e != cudaSuccess) return cuda_fail(e, who, "clear accumulators");
   } else {
     e = launch_update_scale(p->view, B, bnd, header_of(p, prec, I), st);
-    if (e != cudaSuccess) return cuda_fail(e, "sweep: scale");
+    if (e != cudaSuccess) return cuda_fail(e, who, "scale");
   }
   const bool timed = p->timing && p->n_timed < kMaxTimed;
   cudaEvent_t *ev = timed ? &p->ev[4 * (size_t)p->n_timed] : nullptr;
   if (timed) cudaEventRecord(ev[0], st);
   e = launch_prep(p->view, prec, a, st);
-  if (e != cudaSuccess) return cuda_fail(e, "sweep: prep");
+  if (e != cudaSuccess) return cuda_fail(e, who, "prep");
   if (timed) cudaEventRecord(ev[1], st);
   e = prec == MOLC_FP64 ? launch_sweep_fp64(p->view, a, st) : launch_sweep_fp32(p->view, a, st);
-  if (e != cudaSuccess) return cuda_fail(e, "sweep: sweep kernel");
+  if (e != cudaSuccess) return cuda_fail(e, who, "sweep kernel");
   if (timed) cudaEventRecord(ev[2], st);
   e = launch_finalize(p->view, prec, a, st);
-  if (e != cudaSuccess) return cuda_fail(e, "sweep: finalize");
+  if (e != cudaSuccess) return cuda_fail(e, who, "finalize");
   if (timed) {
     cudaEventRecord(ev[3], st);
     ++p->n_timed;
   }
   return MOLC_OK;
+}
+
+molc_status molc_sweep(molc_plan *p, molc_precision prec, const double *kappa, const double *B, double c,
+                       double dt, void *I, const double *bnd, const molc_moments *out, molc_stream stream) {
+  return sweep_step(p, prec, kappa, B, c, dt, I, bnd, out, nullptr, nullptr, nullptr, stream, "sweep");
+}
+
+molc_status molc_sweep_closure(molc_plan *p, molc_precision prec, const double *kappa, const double *B, double c,
+                               double dt, void *I, const double *bnd, const molc_moments *out, double *fxx,
+                               double *fxy, double *fyy, molc_stream stream) {
+  if (!fxx || !fxy || !fyy) return fail(MOLC_ERR_INVALID_ARG, "sweep_closure: NULL factor array");
+  return sweep_step(p, prec, kappa, B, c, dt, I, bnd, out, fxx, fxy, fyy, stream, "sweep_closure");
 }
 
 molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const double *kappa, const double *B,
@@ -1186,12 +1210,9 @@ struct molc_batch {
   };
   std::vector<SweepClass> sweeps;
   std::vector<MomentClass> moments;
-  int2 *d_closure = nullptr;
-  int n_closure = 0;
   int4 *d_combine = nullptr;
   int n_combine = 0;
   bool bound = false;
-  bool want_closure = false;
 };
 
 namespace {
@@ -1199,7 +1220,6 @@ void batch_free(molc_batch *b) {
   DeviceGuard dg(b->device);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_prep) cudaFree(b->d_prep);
-  if (b->d_closure) cudaFree(b->d_closure);
   if (b->d_combine) cudaFree(b->d_combine);
   for (auto &c : b->sweeps)
     if (c.d_map) cudaFree(c.d_map);
@@ -1245,7 +1265,6 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
   std::map<std::pair<int, int>, std::vector<std::pair<int, int2>>> sw;   // (np, depth) -> (length, block)
   std::map<int, std::vector<int4>> mo;
   std::map<int, size_t> mo_smem;
-  std::vector<int2> clo;
   std::vector<int4> comb;
   for (int i = 0; i < n; ++i) {
     const molc_plan *p = plans[i];
@@ -1272,13 +1291,10 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
       for (int64_t k = 0; k < nc; ++k) comb.push_back(make_int4(i, ch, (int)k, 0));
     }
     mo_smem[p->n_polar] = std::max(mo_smem[p->n_polar], (size_t)v.n_pairs * (3 * v.n_polar + 2) * sizeof(float));
-    for (int k = 0; k < (v.ncell + 255) / 256; ++k) clo.push_back(make_int2(i, k));
   }
   cudaError_t e = cudaMalloc((void **)&b->d_inst, n * sizeof(BatchInst));
   if (e == cudaSuccess) e = upload_vec(&b->d_prep, prep);
   b->n_prep = (int)prep.size();
-  if (e == cudaSuccess) e = upload_vec(&b->d_closure, clo);
-  b->n_closure = (int)clo.size();
   if (e == cudaSuccess) e = upload_vec(&b->d_combine, comb);
   b->n_combine = (int)comb.size();
   for (auto &kv : sw) {
@@ -1309,7 +1325,6 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
 
 molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
   if (!b || !args) return fail(MOLC_ERR_INVALID_ARG, "batch_bind: NULL argument");
-  bool any_f = false;
   for (size_t i = 0; i < b->plans.size(); ++i) {
     const molc_sweep_args &x = args[i];
     const molc_plan *p = b->plans[i];
@@ -1321,7 +1336,6 @@ molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
     const bool f = x.fxx || x.fxy || x.fyy;
     if (f && !(x.fxx && x.fxy && x.fyy))
       return fail(MOLC_ERR_INVALID_ARG, "batch_bind: instance %zu: give all of fxx, fxy, fyy or none", i);
-    any_f |= f;
     BatchInst &h = b->h_inst[i];
     h.v = p->view;
     h.L = layout_for(p->view, MOLC_FP32);
@@ -1343,16 +1357,15 @@ molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
     a.acc = nullptr;
     a.items = p->d_items32;
     a.n_items = p->n_items32;
-    h.fxx = x.fxx;
-    h.fxy = x.fxy;
-    h.fyy = x.fyy;
+    a.fxx = x.fxx;   // factors formed where the moments are assembled
+    a.fxy = x.fxy;
+    a.fyy = x.fyy;
   }
   DeviceGuard dg(b->device);
   cudaError_t e = cudaMemcpy(b->d_inst, b->h_inst.data(), b->h_inst.size() * sizeof(BatchInst),
                              cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "batch_bind");
   b->bound = true;
-  b->want_closure = any_f;
   return MOLC_OK;
 }
 
@@ -1375,10 +1388,6 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
   }
   e = launch_moments_combine_batch(b->d_inst, b->d_combine, b->n_combine, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: moments (split cells)");
-  if (b->want_closure) {
-    e = launch_closure_batch(b->d_inst, b->d_closure, b->n_closure, st);
-    if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: closure");
-  }
   return MOLC_OK;
 }
 

@@ -147,6 +147,7 @@ struct SweepArgs {
   const int2 *items;  // FP32: one per thread, {track, sense | g_local << 1 | chunk << 16}; chunk-major,
                       // longest track first, then sense, then group
   int64_t n_items;
+  double *fxx, *fxy, *fyy;   // Eddington factors [G][cell], written where the moments are assembled, or all null
 };
 
 // One instance of a batched FP32 sweep, as the batched kernels read it (device memory).
@@ -154,7 +155,6 @@ struct BatchInst {
   PlanView v;
   SweepArgs a;
   Layout L;
-  double *fxx, *fxy, *fyy;   // Eddington factors, or all null
 };
 
 // Kernel launchers (molc_kernels.cu).  Return cudaSuccess or the launch error.
@@ -188,7 +188,6 @@ cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, in
                                       size_t smem, cudaStream_t st);
 // combine step of split cells: map int4 {instance, chunk, block, 0} over the instance's split cells
 cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
-cudaError_t launch_closure_batch(const BatchInst *inst, const int2 *map, int blocks, cudaStream_t st);
 
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;

@@ -546,6 +546,17 @@ constexpr int kGatherBatch = kGatherPad;
 // a cell crossed by many characteristics of one pair (fine ray spacing) keeps the FP32 error of a few terms.
 constexpr int kPairRun = 8;
 
+// Eddington factors of one (cell, group) from the moments just assembled (Eq. 7 with the cell averages of
+// Eq. 15): f = N / (c E), 0 where E = 0.  The same operations as closure_cells, so molc_sweep_closure and
+// molc_sweep + molc_closure give the same bits.
+__device__ __forceinline__ void eddington_factors(const SweepArgs &a, int64_t idx, double E, double nxx, double nxy,
+                                                  double nyy) {
+  const double inv = E > 0 ? 1.0 / (a.c * E) : 0.0;
+  a.fxx[idx] = nxx * inv;
+  a.fxy[idx] = nxy * inv;
+  a.fyy[idx] = nyy * inv;
+}
+
 // Assembly of one (cell, group) from its six deviation sums D (state units; is = 1/scale):
 //   E = (B geo0 + D0 is)/c, F = D_F is, N_ab = B geo_ab + D_ab is, and B_ref := B.
 __device__ __forceinline__ void assemble_cell(const PlanView &v, const SweepArgs &a, int cell, int g,
@@ -553,13 +564,18 @@ __device__ __forceinline__ void assemble_cell(const PlanView &v, const SweepArgs
   const double is = a.scale[1];   // the deviations are in the state's scaled units (exact power of two)
   const int64_t idx = (int64_t)g * v.ncell + cell;
   const double B = a.B[idx];
-  a.out.E[idx] = (B * v.geo[cell] + D[0] * is) * a.inv_c;
+  const double E = (B * v.geo[cell] + D[0] * is) * a.inv_c;
+  const double nxx = B * v.geo[v.ncell + cell] + D[3] * is;
+  const double nxy = B * v.geo[2 * (int64_t)v.ncell + cell] + D[4] * is;
+  const double nyy = B * v.geo[3 * (int64_t)v.ncell + cell] + D[5] * is;
+  a.out.E[idx] = E;
   a.out.Fx[idx] = D[1] * is;
   a.out.Fy[idx] = D[2] * is;
-  a.out.Nxx[idx] = B * v.geo[v.ncell + cell] + D[3] * is;
-  a.out.Nxy[idx] = B * v.geo[2 * (int64_t)v.ncell + cell] + D[4] * is;
-  a.out.Nyy[idx] = B * v.geo[3 * (int64_t)v.ncell + cell] + D[5] * is;
+  a.out.Nxx[idx] = nxx;
+  a.out.Nxy[idx] = nxy;
+  a.out.Nyy[idx] = nyy;
   a.Bref[idx] = B;   // the new deviations refer to this step's B
+  if (a.fxx) eddington_factors(a, idx, E, nxx, nxy, nyy);
 }
 
 // One block: threads t0 .. t0+127 of chunk ch ((unit, group) pairs, groups fastest; a unit is one part of a
@@ -720,13 +736,18 @@ __global__ void finalize_kernel(PlanView v, SweepArgs a, Layout L) {
       const int g0 = g / L.gc * L.gc, gc = L.gc;   // [chunk][cell][6][gc], as the sweeps accumulate
       const double *ac = a.acc + (int64_t)kOutputs * g0 * v.ncell + (int64_t)cell * kOutputs * gc + (g - g0);
       const double B = a.B[idx];
-      a.out.E[idx] = (B * g0v + __ldg(ac + 0 * gc) * is) * inv_c;
+      const double E = (B * g0v + __ldg(ac + 0 * gc) * is) * inv_c;
+      const double nxx = B * gxx + __ldg(ac + 3 * gc) * is;
+      const double nxy = B * gxy + __ldg(ac + 4 * gc) * is;
+      const double nyy = B * gyy + __ldg(ac + 5 * gc) * is;
+      a.out.E[idx] = E;
       a.out.Fx[idx] = __ldg(ac + 1 * gc) * is;
       a.out.Fy[idx] = __ldg(ac + 2 * gc) * is;
-      a.out.Nxx[idx] = B * gxx + __ldg(ac + 3 * gc) * is;
-      a.out.Nxy[idx] = B * gxy + __ldg(ac + 4 * gc) * is;
-      a.out.Nyy[idx] = B * gyy + __ldg(ac + 5 * gc) * is;
+      a.out.Nxx[idx] = nxx;
+      a.out.Nxy[idx] = nxy;
+      a.out.Nyy[idx] = nyy;
       a.Bref[idx] = B;   // the new deviations refer to this step's B
+      if (a.fxx) eddington_factors(a, idx, E, nxx, nxy, nyy);
     }
   }
 }
@@ -797,13 +818,6 @@ __global__ void closure_kernel(PlanView v, molc_moments m, double c, double *fxx
   closure_cells(v, m, c, fxx, fxy, fyy, fgrey, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
-// Batched: block j closes cells 256 map[j].y .. of instance map[j].x (instances with closure outputs only).
-__global__ void __launch_bounds__(256) closure_batch_kernel(const BatchInst *inst, const int2 *map) {
-  const int2 m = map[blockIdx.x];
-  const BatchInst &b = inst[m.x];
-  if (!b.fxx) return;
-  closure_cells(b.v, b.a.out, b.a.c, b.fxx, b.fxy, b.fyy, nullptr, m.y * blockDim.x + threadIdx.x, 1 << 30);
-}
 
 // Canonical segment averages <-> deviation state: one thread per row (track, sense, step) of the layout,
 // looping over polar cosines and the selected groups.  Ibar = B_ref(cell) + delta.
@@ -1183,11 +1197,6 @@ cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map,
   return cudaGetLastError();
 }
 
-cudaError_t launch_closure_batch(const BatchInst *inst, const int2 *map, int blocks, cudaStream_t st) {
-  if (blocks <= 0) return cudaSuccess;
-  closure_batch_kernel<<<blocks, 256, 0, st>>>(inst, map);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
                                   const double *scale, int g_begin, int g_count, double *canon, bool to_canon,

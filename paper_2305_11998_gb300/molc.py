@@ -32,7 +32,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
-            "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments")
+            "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure")
 
 
 class MolcError(RuntimeError):
@@ -63,7 +63,8 @@ class _Info(C.Structure):
     _fields_ = [("G", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("n_dir", C.c_int), ("n_azim_pairs", C.c_int),
                 ("n_polar", C.c_int), ("n_tracks", C.c_int64), ("n_track_segments", C.c_int64),
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
-                ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int)]
+                ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int),
+                ("n_split_cells", C.c_int)]
 
 
 class _SweepArgs(C.Structure):
@@ -97,6 +98,8 @@ def load(build_if_needed: bool = True):
         "molc_sweep_static_scratch": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp,
                                                 C.POINTER(_Moments), vp]),
         "molc_closure": (C.c_int, [vp, C.POINTER(_Moments), C.c_double, vp, vp, vp, vp, vp]),
+        "molc_sweep_closure": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp, C.POINTER(_Moments),
+                                         vp, vp, vp, vp]),
         "molc_grey_coefficients": (C.c_int, [vp, C.POINTER(_Moments), vp, vp, vp, vp]),
         "molc_face_moments": (C.c_int, [vp, C.c_int, vp, C.c_double, C.POINTER(_Moments), vp]),
         "molc_intensity_export": (C.c_int, [vp, C.c_int, vp, C.c_int, C.c_int, vp, vp]),
@@ -174,6 +177,7 @@ class PlanInfo:
     device_bytes: int
     fp32_sweep_depth: int
     n_faces: int
+    n_split_cells: int
 
 
 class Plan:
@@ -256,6 +260,20 @@ class Plan:
         _check(self._lib.molc_sweep(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt), _ptr(I),
                                     _ptr(bnd), C.byref(m), _stream(stream)))
         return out
+
+    def sweep_closure(self, prec, kappa, B, c, dt, I, bnd, out=None, f=None, stream=None):
+        """molc_sweep_closure: one step and its Eddington factors in one call; returns (moments, factors), the
+        factors {fxx, fxy, fyy} ([G][ncell] each, written into `f` when given)."""
+        out = out if out is not None else self.new_moments(kappa.device)
+        f = f if f is not None else {k: torch.empty((self.G, self.ncell), dtype=torch.float64, device=kappa.device)
+                                     for k in ("fxx", "fxy", "fyy")}
+        for k in ("fxx", "fxy", "fyy"):
+            _check_f64(f[k], self.G * self.ncell, k)
+        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        _check(self._lib.molc_sweep_closure(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt), _ptr(I),
+                                            _ptr(bnd), C.byref(m), _ptr(f["fxx"]), _ptr(f["fxy"]), _ptr(f["fyy"]),
+                                            _stream(stream)))
+        return out, f
 
     def sweep_static_scratch(self, prec, kappa, B, c, dt, I, bnd, out=None, stream=None):
         """molc_sweep_static_scratch: as sweep(), with the workspace taken from the library's fixed device array

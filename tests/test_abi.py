@@ -85,3 +85,20 @@ def test_invalid_arguments_are_rejected():
     assert lib.molc_sweep(P._h, 7, None, None, 1.0, 1.0, None, None, None, None) == 1
     assert b"NULL" in lib.molc_last_error() or len(lib.molc_last_error()) > 0
     P.close()
+
+
+@pytest.mark.parametrize("fine", [False, True])
+def test_split_cell_count_follows_the_entry_lists(fine):
+    # a cell's gather list holds one entry per (track segment, sense) crossing it, padded to a multiple of 4;
+    # lists longer than 256 entries are summed in parts (n_split_cells)
+    wl = synth.Workload("paper8", 8, 8, 6.0, 17, 0.001, 100.0, 2, 16, 40, 1)
+    q = wl.quadrature()
+    h = 0.02 if fine else 0.5
+    P = molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, h, "paper", False,
+                  host_only=True)
+    cells = P.tracks()["cell"]
+    entries = np.bincount(cells, minlength=wl.ncell) // wl.n_polar   # export: every polar cosine and sense
+    padded = (entries + 3) // 4 * 4
+    assert P.info.n_split_cells == int(np.sum(padded > 256))
+    assert (P.info.n_split_cells > 0) == fine
+    P.close()
