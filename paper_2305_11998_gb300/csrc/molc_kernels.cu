@@ -27,7 +27,28 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ bool bad_input(double x) { return !(x >= 0.0) || !isfinite(x); }
+// Not (x >= 0 and finite), decided on the bits (integer pipe; the FP64 pipe is narrow): +0, -0 and the positive
+// finite numbers pass.
+__device__ __forceinline__ bool bad_input(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return !(u < 0x7FF0000000000000ull || u == 0x8000000000000000ull);
+}
+
+// FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU): exponent rebiased by
+// 1023 - 127 and mantissa shifted into place, exact for normal numbers.  Zeros and subnormals (|x| < 2^-126)
+// map to a value of the same sign and magnitude below 2^-126; the FP32 sweep works in units where max B is
+// ~2^100, so that is below 1e-68 of max B.
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned hi = (u & 0x80000000u) | (((u >> 3) & 0x0fffffffu) + 0x38000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// Exact FP32 -> FP64 for every finite x: the integer route for normal numbers, the conversion instruction for
+// zeros and subnormals.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) ? f32_to_f64(x) : (double)x;
+}
 
 // Track holding row r of the intensity layout (rows are (track, sense, step); a track owns 2 nseg rows).
 __device__ __forceinline__ int64_t find_track(const TrackDev *tr, int64_t T, int64_t row) {
@@ -76,9 +97,10 @@ __device__ __forceinline__ void prep_tiles(const PlanView &v, const SweepArgs &a
         const float kt = (float)(kap + a.inv_cdt);
         const float r = __fdiv_rn(inv_cdt_f, kt);
         const double Bs = B * sc;
-        range |= !(Bs < kScaledMax);
+        // !(Bs < kScaledMax) on the bits: signed order is value order for non-negative doubles and -0
+        range |= __double_as_longlong(Bs) >= __double_as_longlong(kScaledMax);
         const float bhi = (float)Bs;
-        const float blo = (float)(Bs - (double)bhi);
+        const float blo = (float)(Bs - f32_to_f64_exact(bhi));
         t4[c * gcount + gl] = make_float4(kt, r, bhi, blo);
         t1[c * gcount + gl] = (float)((a.Bref[idx] - B) * sc) * r;
       }
@@ -210,16 +232,6 @@ __device__ __forceinline__ void attenuation(float a, float inv_tau, float &E1, f
   p = fmaf(p, y, 1.f / 6.f);
   p = fmaf(p, y, 1.f);
   E1 = a < 0.25f ? h * p : (1.f - ex) * inv_tau;
-}
-
-// FP32 -> FP64 by integer operations (the FP64 conversion pipe is narrow on this GPU): exponent rebiased by
-// 1023 - 127 and mantissa shifted into place, exact for normal numbers.  Zeros and subnormals (|x| < 2^-126)
-// map to a value of the same sign and magnitude below 2^-126; the FP32 sweep works in units where max B is
-// ~2^100, so that is below 1e-68 of max B.
-__device__ __forceinline__ double f32_to_f64(float x) {
-  const unsigned u = __float_as_uint(x);
-  const unsigned hi = (u & 0x80000000u) | (((u >> 3) & 0x0fffffffu) + 0x38000000u);
-  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 // L2 eviction policy (sm_80+ createpolicy) for the streamed state, which each pass touches once: evict-first,
