@@ -63,6 +63,9 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 #define MOLC_AUTOTUNE 4u    /* time the FP32 sweep's compiled staging depths on this plan during molc_create
                                (temporary device memory of about one FP32 state) and keep the fastest; the
                                choice changes no result, only speed (molc_plan_info.fp32_sweep_depth) */
+#define MOLC_BALANCE 16u    /* also evaluate the per-ray discrete balance of every sweep in FP64 (a check, not part
+                               of the result; FP64 work per update, so sweeps are slower); read the largest
+                               relative residual with molc_ray_balance.  Not with MOLC_FACES. */
 
 typedef struct {
   int nx, ny;               /* material cells (>= 1) */
@@ -229,6 +232,22 @@ void molc_batch_destroy(molc_batch *batch);
  * A cell with E = 0 gets f = 0. */
 molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c, double *fxx, double *fxy,
                          double *fyy, double *f_grey, molc_stream stream);
+
+/* Per-ray discrete balance of the sweeps of a plan created with MOLC_BALANCE (Eqs. 11-13: the transport equation
+ * integrated along each characteristic, which the exact attenuation of Eq. 12 satisfies segment by segment).
+ * For every characteristic k, direction and group of the sweep,
+ *   R = I_in - I_out + sum_s (Q_s - kappa~_s Ibar_s) l_s / sin zeta
+ * is formed in FP64 from the values the sweep itself computed (in the sweep's working precision), and divided by
+ * S, the sum of the magnitudes of its terms written segment by segment in the variables the sweep rounds
+ * (|I_in,s|, |I_out,s|, their deviations from the cell's B, |Q_s| l_s / sin zeta, kappa~_s |Ibar_s| l_s / sin zeta,
+ * and the cell-to-cell steps of B that the deviation form adds at each crossing): a few units of the working
+ * precision's rounding (FP64 ~1e-16, FP32 ~1e-7) when the sweep's arithmetic is consistent.  Rays with S below
+ * 1e-30 of max(B, boundary) of the sweep carry no radiation at the working precision and are left out.
+ * *max_rel_residual
+ * := the largest |R| / S over all characteristics, directions and groups of the molc_sweep or molc_sweep_closure
+ * calls since the last molc_sweep or molc_sweep_closure began (0 before any).  Synchronises with the device.
+ * MOLC_ERR_INVALID_ARG for a plan created without MOLC_BALANCE. */
+molc_status molc_ray_balance(const molc_plan *plan, double *max_rel_residual);
 
 /* One backward-Euler step and the Eddington factors of its moments in one call (Eqs. 7, 11-15): the same as
  * molc_sweep followed by molc_closure(plan, out, c, fxx, fxy, fyy, NULL, stream), bit for bit, with the factors

@@ -101,6 +101,7 @@ struct molc_plan {
   int4 *d_gent = nullptr;
   int64_t *d_boff = nullptr;
   int2 *d_seg_face = nullptr;
+  unsigned long long *d_balance = nullptr;   // MOLC_BALANCE: largest per-ray relative residual (double bits)
   int2 *d_munit = nullptr;
   int4 *d_mmulti = nullptr;
   double *d_mscratch = nullptr;
@@ -316,7 +317,7 @@ void free_device(molc_plan *p) {
   void *ptrs[] = {p->d_tracks, p->d_seg32, p->d_seg_cell, p->d_seg_len, p->d_seg_afrac, p->d_pairs, p->d_polar,
                   p->d_geo, p->d_dir_seg_off, p->d_status, p->d_cdat, p->d_cdB, p->d_acc, p->d_items32,
                   p->d_cell_off, p->d_gent, p->d_boff, p->d_block_order, p->d_seg_face, p->d_facc,
-                  p->d_munit, p->d_mmulti, p->d_mscratch};
+                  p->d_munit, p->d_mmulti, p->d_mscratch, p->d_balance};
   for (void *q : ptrs)
     if (q) cudaFree(q);
 }
@@ -480,8 +481,10 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   if (groups->G < 1 || groups->G > 4096) return fail(MOLC_ERR_INVALID_ARG, "create: need 1 <= G <= 4096");
   if (!finite_pos(ray_spacing)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing must be > 0");
   if (layout != MOLC_RAYS_UNIFORM && layout != MOLC_RAYS_PAPER) return fail(MOLC_ERR_INVALID_ARG, "create: layout");
-  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE | MOLC_FACES))
+  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE | MOLC_FACES | MOLC_BALANCE))
     return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
+  if ((flags & MOLC_BALANCE) && (flags & MOLC_FACES))
+    return fail(MOLC_ERR_INVALID_ARG, "create: MOLC_BALANCE and MOLC_FACES cannot be combined");
   const int n = quad->n;
   if (n < 2 || !quad->mu || !quad->cos_phi || !quad->sin_phi || !quad->w)
     return fail(MOLC_ERR_INVALID_ARG, "create: bad quadrature");
@@ -919,6 +922,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   UP(d_mscratch, (const double *)nullptr, mmulti.empty() ? 0 : (size_t)nch32 * munit.size() * kOutputs * gc32,
      "moment partials")
   UP(d_facc, (const double *)nullptr, p->facc_elems, "face accumulators")
+  UP(d_balance, (const unsigned long long *)nullptr, (flags & MOLC_BALANCE) ? 2 : 0, "balance residual")
   UP(d_block_order, block_order.data(), block_order.size(), "block order")
   UP(d_cdat, (const float4 *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
   UP(d_cdB, (const float *)nullptr, (size_t)nch32 * gc32 * ncell, "cell table")
@@ -964,6 +968,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       return st;
     }
   }
+  v.balance = p->d_balance;   // after the autotuner, which times the plain sweep
+
   *out = p;
   return MOLC_OK;
 }
@@ -1082,6 +1088,11 @@ static molc_status sweep_step(molc_plan *p, molc_precision prec, const double *k
   if (p->d_facc) {
     e = cudaMemsetAsync(p->d_facc, 0, p->facc_elems * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, who, "clear face accumulators");
+  }
+  if (p->d_balance) {
+    e = cudaMemsetAsync(p->d_balance, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_balance_scale(p->view, B, bnd, st);
+    if (e != cudaSuccess) return cuda_fail(e, who, "balance check set-up");
   }
   if (prec == MOLC_FP64) {   // the FP32 path gathers its moments and has no accumulators
     e = cudaMemsetAsync(p->d_acc, 0, (size_t)p->G * p->view.ncell * kOutputs * sizeof(double), st);
@@ -1252,6 +1263,9 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
       return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d has no FP32 sweep (more than %d polar cosines)", i,
                   kMaxPolarFP32);
     if (plans[i]->device != dev) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is on another device", i);
+    if (plans[i]->d_balance)
+      return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d was created with MOLC_BALANCE (the check runs in "
+                                        "molc_sweep only)", i);
     if (plans[i]->d_facc)
       return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d was created with MOLC_FACES (face moments come from "
                                         "molc_sweep only)", i);
@@ -1393,6 +1407,17 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
 
 void molc_batch_destroy(molc_batch *b) {
   if (b) batch_free(b);
+}
+
+molc_status molc_ray_balance(const molc_plan *p, double *max_rel_residual) {
+  if (!p || !max_rel_residual) return fail(MOLC_ERR_INVALID_ARG, "ray_balance: NULL argument");
+  if (!p->d_balance) return fail(MOLC_ERR_INVALID_ARG, "ray_balance: the plan was created without MOLC_BALANCE");
+  DeviceGuard dg(p->device);
+  unsigned long long bits = 0;
+  cudaError_t e = cudaMemcpy(&bits, p->d_balance, sizeof bits, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "ray_balance");
+  std::memcpy(max_rel_residual, &bits, sizeof bits);
+  return MOLC_OK;
 }
 
 molc_status molc_closure(const molc_plan *p, const molc_moments *m, double c, double *fxx, double *fxy,

@@ -78,6 +78,8 @@ struct PlanView {
   // face moments (Eq. 16), plans created with MOLC_FACES only (else null / 0)
   const int2 *seg_face;         // per track segment: upwind face of the + sense, of the - sense
   double *facc;                 // [chunk][face][6][gc] FP64 sums of omega w I (1, Omega, Omega Omega)
+  unsigned long long *balance;  // MOLC_BALANCE: [0] bits of the largest per-ray relative balance residual, [1] bits
+                                //   of max(B, boundary) of the sweep (else null)
   int n_faces;                  // x-faces (nx + 1) ny, then y-faces nx (ny + 1)
   double hx, hy;                // cell sizes (face lengths)
 };
@@ -171,6 +173,7 @@ cudaError_t launch_grey(const PlanView &v, const molc_moments &m, const double *
 cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *I, const double *Bref,
                                   const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
                                   cudaStream_t st);
+cudaError_t launch_balance_scale(const PlanView &v, const double *B, const double *bnd, cudaStream_t st);
 cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const double *B, double *header,
                              cudaStream_t st);
 // Batched FP32 kernels: one launch each over the blocks of all instances listed in a block map

@@ -140,7 +140,26 @@ __global__ void __launch_bounds__(128) prep_batch_kernel(const BatchInst *inst, 
 // ---------------------------------------------------------------------------------------------------------
 // FP64 plain sweep: one thread per (track, sense, group, polar cosine), all arithmetic in FP64, one FP64
 // atomic per output and update into the [cell][6][G] accumulators.
+// Per-ray balance (MOLC_BALANCE): R = I_in - I_out + sum_s tau_s (d_s - psibar_s), which is the integral of the
+// transport equation along the characteristic, I_in - I_out + sum_s (Q_s - kappa~_s Ibar_s) l_s / sin zeta, in the
+// deviation variables (Q - kappa~ Ibar = kappa~ (d - psibar)).  Segment by segment it reads
+// I_in,s - I_out,s + tau_s (d_s - psibar_s) = 0, and the crossings add I_out,s - I_in,s+1 = 0 (the steps of B the
+// deviation form takes there); S is the sum of the magnitudes of all these terms in the variables the sweep
+// rounds (|I_in,s|, |I_out,s| and their deviations |psi_in,s|, |psi_out,s| from the cell's B, tau_s |B_s + d_s| =
+// |Q_s| l_s / sin zeta, tau_s |B_s + psibar_s| = kappa~_s |Ibar_s| l_s / sin zeta, the B steps), so that |R| / S
+// is a few units of the working precision's rounding when the arithmetic is consistent.  The largest |R| / S goes
+// into *word by an integer atomicMax (non-negative doubles order like their bits).
+// Rays whose terms sum to less than kBalanceFloor of max(B, boundary) (word[1], in the units of R and S after the
+// factor `units`) carry no radiation at the working precision and are left out.
+constexpr double kBalanceFloor = 1e-30;
+__device__ __forceinline__ void ray_balance_max(unsigned long long *word, double R, double S, double units) {
+  const double floor = kBalanceFloor * __longlong_as_double((long long)word[1]) * units;
+  if (!(S > floor) || !(S > 0.0)) return;
+  atomicMax(word, (unsigned long long)__double_as_longlong(fabs(R) / S));
+}
+
 // ---------------------------------------------------------------------------------------------------------
+template <bool BAL>   // BAL: with the per-ray balance check (MOLC_BALANCE)
 __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a) {
   const int NP = v.n_polar, Q = v.G * NP;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,13 +182,16 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
   const int nseg = tr.nseg;
   const double Iin = a.bnd[(sense ? tr.entry_minus : tr.entry_plus) * v.G + g];
   double psi = 0.0, Bprev = 0.0;
+  double rb = 0.0, sb = 0.0;   // MOLC_BALANCE: sum of tau (d - psibar) and the magnitudes of the terms
   for (int s = 0; s < nseg; ++s) {
     const int64_t sgi = sense ? tr.seg_off + nseg - 1 - s : tr.seg_off + s;
     const int cell = v.seg_cell[sgi];
     const double len = v.seg_len[sgi], af = v.seg_afrac[sgi];
     const double Bc = Bg[cell];
     const double kt = kap[cell] + inv_cdt;
-    psi = s == 0 ? Iin - Bc : psi + (Bprev - Bc);
+    const double jump = s == 0 ? Iin - Bc : Bprev - Bc;
+    psi = s == 0 ? jump : psi + jump;
+    if constexpr (BAL) sb += fabs(jump);
     if (v.facc) {   // Eq. (16): omega w times the intensity at the segment's upwind face
       const int2 fc = v.seg_face[sgi];
       double *fa = v.facc + (int64_t)(sense ? fc.y : fc.x) * kOutputs * v.G + g;
@@ -186,10 +208,17 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
     const double one_m_e = -expm1(-tau);
     const double ex = exp(-tau);
     const double E1 = one_m_e / tau;
-    const double x = psi - d;
+    const double pin = psi;
+    const double x = pin - d;
     const double pb = fma(x, E1, d);
-    psi = fma(x, ex, d);
+    // thin: psi_in - (psi_in - d)(1 - e^-tau), the change to the accuracy of expm1; thick: d + (psi_in - d) e^-tau,
+    // the transmitted part to the accuracy of exp
+    psi = tau < 0.5 ? fma(-x, one_m_e, pin) : fma(x, ex, d);
     I[(int64_t)s * Q] = pb;
+    if constexpr (BAL) {
+      rb += tau * (d - pb);
+      sb += fabs(Bc + pin) + fabs(Bc + psi) + fabs(pin) + fabs(psi) + tau * (fabs(Bc + d) + fabs(Bc + pb));
+    }
     const double wv = pd.w * af * pb;
     double *acc = a.acc + (int64_t)cell * kOutputs * v.G + g;
     atomicAdd(acc + 0 * v.G, wv);
@@ -199,6 +228,10 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(PlanView v, SweepArgs a
     atomicAdd(acc + 4 * v.G, wv * Ox * Oy);
     atomicAdd(acc + 5 * v.G, wv * Oy * Oy);
     Bprev = Bc;
+  }
+  if (BAL && nseg > 0) {
+    const double Iout = psi + Bprev;
+    ray_balance_max(v.balance, Iin - Iout + rb, sb, 1.0);
   }
 }
 
@@ -218,12 +251,16 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return r;
 }
 
-// (1 - e^-tau)/tau and e^-tau in FP32, from a = tau/2.  With h = e^-a = 2^(-a log2 e):
+// E1 = (1 - e^-tau)/tau, e^-tau and, for tau < 1/2, om = 1 - e^-tau in FP32, from a = tau/2.  With
+// h = e^-a = 2^(-a log2 e):
 //   tau < 1/2:  E1 = h sinh(a) / a, the even Taylor series in y = a^2 to y^3 (truncation < 5e-11 relative),
-//               free of cancellation;
+//               free of cancellation, and om = tau E1 (= 2 h sinh(a));
 //   tau >= 1/2: E1 = (1 - e^-tau) / tau (1 - e^-tau > 0.39, no cancellation).
-// e^-tau = h^2.  inv_tau is 1/tau.
-__device__ __forceinline__ void attenuation(float a, float inv_tau, float &E1, float &ex) {
+// e^-tau = h^2.  inv_tau is 1/tau.  The outgoing intensity is taken as psi_in - (psi_in - d) om below tau = 1/2
+// and as d + (psi_in - d) e^-tau above: equal in exact arithmetic, but across a thin segment the first keeps the
+// change to the relative accuracy of om where the second would carry the rounding of e^-tau on all of psi_in - d,
+// and across a thick one the second keeps the small transmitted part to the relative accuracy of e^-tau.
+__device__ __forceinline__ void attenuation(float a, float inv_tau, float &E1, float &om, float &ex, bool &thin) {
   constexpr float kMinusLog2e = -1.4426950408889634f;
   const float h = ex2_approx(a * kMinusLog2e);
   ex = h * h;
@@ -231,7 +268,10 @@ __device__ __forceinline__ void attenuation(float a, float inv_tau, float &E1, f
   float p = fmaf(y, 1.f / 5040.f, 1.f / 120.f);
   p = fmaf(p, y, 1.f / 6.f);
   p = fmaf(p, y, 1.f);
-  E1 = a < 0.25f ? h * p : (1.f - ex) * inv_tau;
+  const float hp = h * p;
+  thin = a < 0.25f;
+  E1 = thin ? hp : (1.f - ex) * inv_tau;
+  om = (a + a) * hp;
 }
 
 // L2 eviction policy (sm_80+ createpolicy) for the streamed state, which each pass touches once: evict-first,
@@ -368,9 +408,14 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
 // Group accounting: the prologue commits D-1 groups (deviations of steps 0..D-2, table entries of steps
 // 0..D-3) and step s commits one; step s's deviations are in group s and its table entry in group s+1 (group s
 // for s <= D-3), so waiting until at most D-2 groups are pending is enough.
-template <int NP, int D, bool FACES = false>
+// What an FP32 sweep adds to the segment update: nothing, the face reductions of Eq. 16 (MOLC_FACES), or the
+// per-ray balance check (MOLC_BALANCE).
+enum SweepExtra { kSweepPlain = 0, kSweepFaces = 1, kSweepBalance = 2 };
+
+template <int NP, int D, int EXTRA = kSweepPlain>
 __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle) {
   static_assert(D >= 3, "the staging depth needs D >= 3");
+  constexpr bool FACES = EXTRA == kSweepFaces, BAL = EXTRA == kSweepBalance;
   constexpr int kSteps = D;
   __shared__ __align__(16) float sdev[kSteps][kSweepBlock * NP];
   __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
@@ -439,6 +484,13 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
   for (int p = 0; p < NP; ++p) psi[p] = 0.f;
   float bhi_prev = in_hi, blo_prev = in_lo;   // the boundary acts as the "previous cell" of step 0
+  // MOLC_BALANCE, in FP64 from this sweep's FP32 values: per polar cosine the sum of tau (d - psibar) and of the
+  // magnitudes of the terms; the crossing steps are common to the polar cosines; B of the last cell
+  double rb[BAL ? NP : 1], sb[BAL ? NP : 1], jsum = 0.0, blast = 0.0;
+  if constexpr (BAL) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) rb[p] = sb[p] = 0.0;
+  }
   for (int s0 = 0; s0 < nmax; s0 += kSteps) {
 #pragma unroll
     for (int u = 0; u < kSteps; ++u) {
@@ -478,6 +530,12 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
         const float rkl = rcp_approx(kl);
 #pragma unroll
         for (int p = 0; p < NP; ++p) psi[p] += jump;
+        double bcell = 0.0;
+        if constexpr (BAL) {
+          jsum += fabs(f32_to_f64_exact(jump));
+          bcell = f32_to_f64_exact(q.z) + f32_to_f64_exact(q.w);
+          blast = bcell;
+        }
         if constexpr (FACES) {
           // the intensity entering the segment, in scaled units: psi (relative to this cell) + B of this cell
           const float Bc = q.z + q.w;
@@ -504,12 +562,23 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
         }
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          float E1, ex;
-          attenuation(kl * half_inv_sinz[p], sinz[p] * rkl, E1, ex);
+          float E1, om, ex;
+          bool thin;
+          const float ahalf = kl * half_inv_sinz[p];   // tau / 2
+          attenuation(ahalf, sinz[p] * rkl, E1, om, ex, thin);
           const float d = fmaf(dv[p], qy, dB);
-          const float x = psi[p] - d;
+          const float pin = psi[p];
+          const float x = pin - d;
           dv[p] = fmaf(x, E1, d);
-          psi[p] = fmaf(x, ex, d);
+          psi[p] = thin ? fmaf(-x, om, pin) : fmaf(x, ex, d);
+          if constexpr (BAL) {
+            const double tau = 2.0 * f32_to_f64_exact(ahalf), dd = f32_to_f64_exact(d),
+                         pb = f32_to_f64_exact(dv[p]);
+            rb[p] += tau * (dd - pb);
+            const double pi = f32_to_f64_exact(pin), po = f32_to_f64_exact(psi[p]);
+            sb[p] += fabs(bcell + pi) + fabs(bcell + po) + fabs(pi) + fabs(po) +
+                     tau * (fabs(bcell + dd) + fabs(bcell + pb));
+          }
         }
         store_dev<NP>(I, dv, pol_stream);
         bhi_prev = q.z;
@@ -520,11 +589,29 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
     }
   }
   cp_async_wait<0>();
+  if constexpr (BAL) {
+    if (nseg > 0) {
+      const double Iin = f32_to_f64_exact(in_hi) + f32_to_f64_exact(in_lo);
+      double R = 0.0, S = 0.0, worst = -1.0;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {   // the polar cosine with the largest relative residual
+        const double Iout = f32_to_f64_exact(psi[p]) + blast;
+        const double r = Iin - Iout + rb[p], sm = sb[p] + jsum;
+        const double rel = sm > 0.0 ? fabs(r) / sm : 0.0;
+        if (rel > worst) {
+          worst = rel;
+          R = r;
+          S = sm;
+        }
+      }
+      ray_balance_max(v.balance, R, S, a.scale[0]);   // R, S in the state's scaled units
+    }
+  }
 }
 
-template <int NP, int D, bool FACES = false>
+template <int NP, int D, int EXTRA = kSweepPlain>
 __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
-  sweep_fp32_body<NP, D, FACES>(v, a, L, v.block_order[blockIdx.x]);
+  sweep_fp32_body<NP, D, EXTRA>(v, a, L, v.block_order[blockIdx.x]);
 }
 
 // Batched: block j sweeps bundle map[j].y of instance map[j].x (blocks of all instances, longest first).
@@ -1001,7 +1088,10 @@ cudaError_t launch_sweep_fp64(const PlanView &v, const SweepArgs &a, cudaStream_
   const int64_t threads = v.n_tracks * 2 * (int64_t)v.G * v.n_polar;
   const int64_t blocks = (threads + 127) / 128;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-  sweep_fp64_kernel<<<(unsigned)blocks, 128, 0, st>>>(v, a);
+  if (v.balance)
+    sweep_fp64_kernel<true><<<(unsigned)blocks, 128, 0, st>>>(v, a);
+  else
+    sweep_fp64_kernel<false><<<(unsigned)blocks, 128, 0, st>>>(v, a);
   return cudaGetLastError();
 }
 
@@ -1022,25 +1112,29 @@ static cudaError_t sweep_fp32_depth(const PlanView &v, const SweepArgs &a, const
   return cudaGetLastError();
 }
 
+template <int EXTRA>
+cudaError_t sweep_fp32_extra(const PlanView &v, const SweepArgs &a, const Layout &L, dim3 grid, cudaStream_t st) {
+  switch (v.n_polar) {
+    case 1: sweep_fp32_kernel<1, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 2: sweep_fp32_kernel<2, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 3: sweep_fp32_kernel<3, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 4: sweep_fp32_kernel<4, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 5: sweep_fp32_kernel<5, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 6: sweep_fp32_kernel<6, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 7: sweep_fp32_kernel<7, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    case 8: sweep_fp32_kernel<8, 4, EXTRA><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_fp32(const PlanView &v, const SweepArgs &a, cudaStream_t st) {
   const Layout L = layout_for(v, MOLC_FP32);
   const int64_t blocks = (a.n_items + kSweepBlock - 1) / kSweepBlock;
   if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)blocks);
-  if (v.facc) {   // face moments requested: the variant with face reductions (staging depth 4)
-    switch (v.n_polar) {
-      case 1: sweep_fp32_kernel<1, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 2: sweep_fp32_kernel<2, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 3: sweep_fp32_kernel<3, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 4: sweep_fp32_kernel<4, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 5: sweep_fp32_kernel<5, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 6: sweep_fp32_kernel<6, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 7: sweep_fp32_kernel<7, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      case 8: sweep_fp32_kernel<8, 4, true><<<grid, kSweepBlock, 0, st>>>(v, a, L); break;
-      default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-  }
+  if (v.facc) return sweep_fp32_extra<kSweepFaces>(v, a, L, grid, st);       // face reductions, depth 4
+  if (v.balance) return sweep_fp32_extra<kSweepBalance>(v, a, L, grid, st);  // per-ray balance check, depth 4
   switch (v.sweep_depth) {
     case 3: return sweep_fp32_depth<3>(v, a, L, grid, st);
     case 4: return sweep_fp32_depth<4>(v, a, L, grid, st);
@@ -1220,6 +1314,13 @@ cudaError_t launch_intensity_copy(const PlanView &v, molc_precision prec, void *
   else
     intensity_copy_kernel<float><<<grid_for(L.rows, 128), 128, 0, st>>>(v, L, (float *)I, Bref, scale, g_begin,
                                                                        g_count, canon, to_canon, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_balance_scale(const PlanView &v, const double *B, const double *bnd, cudaStream_t st) {
+  unsigned long long *mx = v.balance + 1;
+  max_bits_kernel<<<grid_for((int64_t)v.G * v.ncell, 256), 256, 0, st>>>(B, (int64_t)v.G * v.ncell, mx);
+  max_bits_kernel<<<1, 256, 0, st>>>(bnd, 4 * (int64_t)v.G, mx);
   return cudaGetLastError();
 }
 

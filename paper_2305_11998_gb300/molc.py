@@ -20,6 +20,7 @@ AREA_RENORM = 1
 HOST_ONLY = 2
 AUTOTUNE = 4
 FACES = 8
+BALANCE = 16
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 LAYOUT = {"uniform": RAYS_UNIFORM, "paper": RAYS_PAPER, RAYS_UNIFORM: RAYS_UNIFORM, RAYS_PAPER: RAYS_PAPER}
 STATUS = {0: "MOLC_OK", 1: "MOLC_ERR_INVALID_ARG", 2: "MOLC_ERR_OUT_OF_MEMORY", 3: "MOLC_ERR_CUDA",
@@ -32,7 +33,8 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_intensity_import", "molc_tracks_export", "molc_kernel_timing", "molc_kernel_time",
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
-            "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure")
+            "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure",
+            "molc_ray_balance")
 
 
 class MolcError(RuntimeError):
@@ -98,6 +100,7 @@ def load(build_if_needed: bool = True):
         "molc_sweep_static_scratch": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp,
                                                 C.POINTER(_Moments), vp]),
         "molc_closure": (C.c_int, [vp, C.POINTER(_Moments), C.c_double, vp, vp, vp, vp, vp]),
+        "molc_ray_balance": (C.c_int, [vp, dp]),
         "molc_sweep_closure": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_double, vp, vp, C.POINTER(_Moments),
                                          vp, vp, vp, vp]),
         "molc_grey_coefficients": (C.c_int, [vp, C.POINTER(_Moments), vp, vp, vp, vp]),
@@ -184,7 +187,7 @@ class Plan:
     """molc_create / molc_sweep / molc_closure on torch tensors (float64, CUDA, contiguous)."""
 
     def __init__(self, nx, ny, lx, ly, mu, cos_phi, sin_phi, w, G, spacing, layout="uniform", renorm=True,
-                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False, faces=False):
+                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False, faces=False, balance=False):
         lib = load()
         self._lib = lib
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, cos_phi, sin_phi, w)]
@@ -195,7 +198,8 @@ class Plan:
         h = C.c_void_p()
         _check(lib.molc_create(C.byref(grid), C.byref(quad), C.byref(groups), float(spacing), LAYOUT[layout],
                                (AREA_RENORM if renorm else 0) | (HOST_ONLY if host_only else 0) |
-                               (AUTOTUNE if autotune else 0) | (FACES if faces else 0), C.byref(h)))
+                               (AUTOTUNE if autotune else 0) | (FACES if faces else 0) |
+                               (BALANCE if balance else 0), C.byref(h)))
         self._h = h
         inf = _Info()
         _check(lib.molc_plan_get_info(h, C.byref(inf)))
@@ -205,11 +209,11 @@ class Plan:
 
     @classmethod
     def from_workload(cls, wl, quad=None, spacing=None, layout="uniform", renorm=True, host_only=False,
-                      autotune=False, faces=False):
+                      autotune=False, faces=False, balance=False):
         q = quad if quad is not None else wl.quadrature()
         return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G,
                    wl.spacing if spacing is None else spacing, layout, renorm, edges=wl.edges(), host_only=host_only,
-                   autotune=autotune, faces=faces)
+                   autotune=autotune, faces=faces, balance=balance)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -319,6 +323,13 @@ class Plan:
         _check(self._lib.molc_grey_coefficients(self._h, C.byref(m), _ptr(kappa), _ptr(B), _ptr(out),
                                                 _stream(stream)))
         return dict(zip(self.GREY, out))
+
+    def ray_balance(self) -> float:
+        """molc_ray_balance: the largest per-ray relative balance residual of the last sweep (plans created with
+        balance=True; synchronises)."""
+        r = C.c_double()
+        _check(self._lib.molc_ray_balance(self._h, C.byref(r)))
+        return r.value
 
     def kernel_timing(self, enable: bool = True):
         _check(self._lib.molc_kernel_timing(self._h, int(enable)))

@@ -102,3 +102,11 @@ def test_split_cell_count_follows_the_entry_lists(fine):
     assert P.info.n_split_cells == int(np.sum(padded > 256))
     assert (P.info.n_split_cells > 0) == fine
     P.close()
+
+
+def test_balance_check_does_not_combine_with_face_moments():
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    with pytest.raises(molc.MolcError):
+        molc.Plan.from_workload(wl, host_only=True, faces=True, balance=True)
+    P = molc.Plan.from_workload(wl, host_only=True, balance=True)
+    P.close()

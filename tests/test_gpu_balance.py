@@ -1,0 +1,97 @@
+"""GPU: the per-ray discrete balance check (MOLC_BALANCE, molc_ray_balance) of both sweeps.
+
+Integrated along a characteristic, the transport equation gives I_in - I_out + sum_s (Q_s - kappa~_s Ibar_s)
+l_s / sin zeta = 0, which the exact attenuation of Eq. 12 satisfies segment by segment.  The sweeps evaluate it in
+FP64 from their own values; S sums the magnitudes of the terms in the variables the sweep rounds, so the largest
+|R| / S over all rays is a few units of the working precision's rounding: FP64 below 1e-13 (n u for n ~ 1e3
+terms), FP32 below 4e-6 (64 u; the FP32 update keeps tau E1 and 1 - e^-tau consistent by construction).  The
+check changes nothing in the results: moments and state equal those of a plan without it.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def molc():
+    import paper_2305_11998_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+CASES = [("fc16_g4_d32", "uniform"), ("fc16_g4_d32", "paper"), ("fc64_g17_d128", "uniform")]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 4e-6)])
+@pytest.mark.parametrize("name,layout", CASES)
+def test_ray_balance_holds_and_changes_nothing(molc, prec, tol, name, layout):
+    wl = synth.WORKLOADS[name]
+    spacing = wl.spacing if layout == "uniform" else wl.h / 1.5
+    kw = dict(spacing=spacing, layout=layout, renorm=(layout == "uniform"))
+    P = molc.Plan.from_workload(wl, balance=True, **kw)
+    R = molc.Plan.from_workload(wl, **kw)
+    d = wl.inputs(1)
+    k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
+    I_p, I_r = P.new_intensity(prec).zero_(), R.new_intensity(prec).zero_()
+    P.intensity_init(prec, I_p, B)
+    R.intensity_init(prec, I_r, B)
+    assert P.ray_balance() == 0.0
+    for step in range(3):
+        got = P.sweep(prec, k, B, d["c"], d["dt"], I_p, bnd)
+        ref = R.sweep(prec, k, B, d["c"], d["dt"], I_r, bnd)
+        torch.cuda.synchronize()
+        rel = P.ray_balance()
+        assert 0.0 <= rel <= tol, (step, rel)
+        if prec == "fp32":
+            assert rel > 0.0   # the FP32 update leaves rounding to see: the check did run
+            for kk in got:
+                assert torch.equal(got[kk], ref[kk]), kk
+        else:
+            cE = d["c"] * np.abs(ref["E"].cpu().numpy())
+            for kk in got:
+                a, b = got[kk].cpu().numpy(), ref[kk].cpu().numpy()
+                den = np.maximum(np.abs(b), 1e-30 * np.abs(b).max()) if kk in ("E", "Nxx", "Nyy") else \
+                    np.maximum(cE, 1e-30 * cE.max())
+                assert np.max(np.abs(a - b) / den) <= 1e-12, kk
+        assert torch.equal(I_p, I_r)
+    assert P.device_status() == 0
+    P.close()
+    R.close()
+
+
+def test_ray_balance_needs_the_flag_and_stays_out_of_batches(molc):
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    P = molc.Plan.from_workload(wl)
+    with pytest.raises(molc.MolcError):
+        P.ray_balance()
+    Q = molc.Plan.from_workload(wl, balance=True)
+    with pytest.raises(molc.MolcError):
+        molc.Batch([P, Q])
+    P.close()
+    Q.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 4e-6)])
+def test_ray_balance_at_full_size(molc, prec, tol):
+    # 512^2 x 17 groups, 128 directions, the benchmark's workload: every ray of one step
+    wl = synth.WORKLOADS["fc512_g17_d128"]
+    P = molc.Plan.from_workload(wl, balance=True)
+    d = wl.inputs(0)
+    k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
+    I = P.new_intensity(prec)
+    P.intensity_init(prec, I, B)
+    P.sweep(prec, k, B, d["c"], d["dt"], I, bnd)
+    rel = P.ray_balance()
+    assert 0.0 < rel <= tol, rel
+    assert P.device_status() == 0
+    del I
+    P.close()
+    torch.cuda.empty_cache()
