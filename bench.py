@@ -34,7 +34,7 @@ METRIC = "segment×group updates/s"
 # ncu dram bytes (read + write) per update of sweep_fp32_kernel, from the capture summarised in
 # profiles/sweep_moments_fp32_fc384_g17.md (384x384 cells, same kernel configuration), scaled by the updates of
 # the launch; None once the kernel changes after that capture.
-SWEEP_FP32_DRAM_BYTES_PER_UPDATE = 8.66
+SWEEP_FP32_DRAM_BYTES_PER_UPDATE = 8.63
 
 
 def parse():
