@@ -211,15 +211,17 @@ typedef struct {
   double *fxx, *fxy, *fyy;      /* device [G][cell] (f = N / (c E), as molc_closure), or all NULL */
 } molc_sweep_args;
 
-/* plans: host array of n (>= 1) plans created on the current device (not MOLC_HOST_ONLY, at most 8 polar
- * cosines); the batch keeps pointers to them (destroy the batch first).  Builds the block maps (device). */
+/* plans: host array of n (>= 1) plans created on the current device (not MOLC_HOST_ONLY, MOLC_FACES or
+ * MOLC_BALANCE, at most 8 polar cosines; MOLC_ERR_INVALID_ARG otherwise); the batch keeps pointers to them
+ * (destroy the batch first).  Builds the block maps (device). */
 molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out);
 
 /* Record the per-instance arguments (host array of n, copied to the device synchronously).  Call again whenever
  * a buffer changes; molc_batch_sweep uses the last recorded arguments. */
 molc_status molc_batch_bind(molc_batch *batch, const molc_sweep_args *args);
 
-/* One backward-Euler step of every instance (molc_sweep in FP32, then the factors where requested).
+/* One backward-Euler step of every instance: molc_sweep_closure in FP32 for the instances bound with factor
+ * outputs, molc_sweep for the others.
  * Asynchronous on `stream`; no allocation and no host synchronisation, so a step (or several) can be captured
  * in a CUDA graph and replayed.  Device status words are per plan (molc_device_status). */
 molc_status molc_batch_sweep(molc_batch *batch, molc_stream stream);

@@ -890,9 +890,8 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
         seg_face[q].y = j == t.nseg - 1 ? edge_face(t.entry_minus, c) : between(p->seg_cell[q + 1], c);
       }
     }
-    const int gcf = std::max(gc32, p->G);   // accumulators shared by both precisions: [chunk][face][6][gc]
+    // accumulators shared by both precisions: [chunk][face][6][gc] (FP32 chunks of gc32 groups, FP64 one chunk of G)
     p->facc_elems = (size_t)v.n_faces * kOutputs * std::max<int64_t>((int64_t)nch32 * gc32, p->G);
-    (void)gcf;
   }
   if (p->host_only) {
     *out = p;
