@@ -247,7 +247,8 @@ molc_status molc_closure(const molc_plan *plan, const molc_moments *m, double c,
  * 1e-30 of max(B, boundary) of the sweep carry no radiation at the working precision and are left out.
  * *max_rel_residual
  * := the largest |R| / S over all characteristics, directions and groups of the molc_sweep or molc_sweep_closure
- * calls since the last molc_sweep or molc_sweep_closure began (0 before any).  Synchronises with the device.
+ * calls since the last molc_sweep or molc_sweep_closure began (0 before any; molc_sweep_static_scratch on such a
+ * plan adds its rays without starting a new record).  Synchronises with the device.
  * MOLC_ERR_INVALID_ARG for a plan created without MOLC_BALANCE. */
 molc_status molc_ray_balance(const molc_plan *plan, double *max_rel_residual);
 

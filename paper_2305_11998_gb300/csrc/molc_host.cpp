@@ -930,6 +930,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
 #undef UP
   if (st == MOLC_OK) {
     cudaError_t e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e == cudaSuccess && p->d_balance) e = cudaMemset(p->d_balance, 0, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) st = cuda_fail(e, "status");
   }
   if (st != MOLC_OK) {
