@@ -238,6 +238,8 @@ class Plan:
         return torch.empty(self.intensity_bytes(prec), dtype=torch.uint8, device=device)
 
     def intensity_init(self, prec, I, B, stream=None):
+        self._state(prec, I)
+        self._fields(B=B)
         _check(self._lib.molc_intensity_init(self._h, PREC[prec], _ptr(I), _ptr(B), _stream(stream)))
 
     def intensity_export(self, prec, I, g_begin=0, g_count=None, out=None, stream=None):
@@ -245,14 +247,40 @@ class Plan:
         ns = self.info.n_segments
         if out is None:
             out = torch.empty((ns, g_count), dtype=torch.float64, device=I.device)
+        self._state(prec, I)
+        _check_f64(out, ns * g_count, "out")
         _check(self._lib.molc_intensity_export(self._h, PREC[prec], _ptr(I), g_begin, g_count, _ptr(out),
                                                _stream(stream)))
         return out
 
     def intensity_import(self, prec, I, canon, B, g_begin=0, stream=None):
         g_count = canon.shape[1]
+        self._state(prec, I)
+        self._fields(B=B)
+        _check_f64(canon, self.info.n_segments * g_count, "canon")
         _check(self._lib.molc_intensity_import(self._h, PREC[prec], _ptr(I), g_begin, g_count, _ptr(canon),
                                                _ptr(B), _stream(stream)))
+
+    # ---- argument checks (sizes and types of the tensors whose raw pointers cross the C ABI; a mismatch is
+    # rejected here, before any kernel could read or write past a buffer)
+    def _fields(self, kappa=None, B=None, bnd=None):
+        n = self.G * self.ncell
+        if kappa is not None:
+            _check_f64(kappa, n, "kappa")
+        if B is not None:
+            _check_f64(B, n, "B")
+        if bnd is not None:
+            _check_f64(bnd, 4 * self.G, "bnd")
+
+    def _state(self, prec, I):
+        if I.numel() * I.element_size() < self.intensity_bytes(prec):
+            raise ValueError(f"I: needs {self.intensity_bytes(prec)} bytes for {prec}")
+
+    def _moments(self, m, per=None):
+        n = self.G * (self.ncell if per is None else per)
+        for k in MOMENTS:
+            _check_f64(m[k], n, k)
+        return _Moments(*[_ptr(m[k]).value for k in MOMENTS])
 
     # ---- the sweep
     def new_moments(self, device="cuda"):
@@ -260,7 +288,9 @@ class Plan:
 
     def sweep(self, prec, kappa, B, c, dt, I, bnd, out=None, stream=None):
         out = out if out is not None else self.new_moments(kappa.device)
-        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        self._fields(kappa, B, bnd)
+        self._state(prec, I)
+        m = self._moments(out)
         _check(self._lib.molc_sweep(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt), _ptr(I),
                                     _ptr(bnd), C.byref(m), _stream(stream)))
         return out
@@ -273,7 +303,9 @@ class Plan:
                                      for k in ("fxx", "fxy", "fyy")}
         for k in ("fxx", "fxy", "fyy"):
             _check_f64(f[k], self.G * self.ncell, k)
-        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        self._fields(kappa, B, bnd)
+        self._state(prec, I)
+        m = self._moments(out)
         _check(self._lib.molc_sweep_closure(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt), _ptr(I),
                                             _ptr(bnd), C.byref(m), _ptr(f["fxx"]), _ptr(f["fxy"]), _ptr(f["fyy"]),
                                             _stream(stream)))
@@ -285,7 +317,9 @@ class Plan:
         one device race).  `out` is allocated here by torch when not given: pass it for a call that allocates
         nothing at all."""
         out = out if out is not None else self.new_moments(kappa.device)
-        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        self._fields(kappa, B, bnd)
+        self._state(prec, I)
+        m = self._moments(out)
         _check(self._lib.molc_sweep_static_scratch(self._h, PREC[prec], _ptr(kappa), _ptr(B), float(c), float(dt),
                                                    _ptr(I), _ptr(bnd), C.byref(m), _stream(stream)))
         return out
@@ -299,7 +333,7 @@ class Plan:
         for k in ("fxx", "fxy", "fyy"):
             _check_f64(f[k], self.G * self.ncell, k)
         fg = torch.empty((3, self.ncell), dtype=torch.float64, device=moments["E"].device) if grey else None
-        m = _Moments(*[moments[k].data_ptr() for k in MOMENTS])
+        m = self._moments(moments)
         _check(self._lib.molc_closure(self._h, C.byref(m), float(c), _ptr(f["fxx"]), _ptr(f["fxy"]),
                                       _ptr(f["fyy"]), _ptr(fg), _stream(stream)))
         if grey:
@@ -310,7 +344,8 @@ class Plan:
         """molc_face_moments: {E, Fx, Fy, Nxx, Nxy, Nyy} of the faces, each [G][n_faces], of the last sweep."""
         nf = self.info.n_faces
         out = {k: torch.empty((self.G, nf), dtype=torch.float64, device=I.device) for k in MOMENTS}
-        m = _Moments(*[out[k].data_ptr() for k in MOMENTS])
+        self._state(prec, I)
+        m = self._moments(out, per=nf)
         _check(self._lib.molc_face_moments(self._h, PREC[prec], _ptr(I), float(c), C.byref(m), _stream(stream)))
         return out
 
@@ -319,7 +354,8 @@ class Plan:
     def grey_coefficients(self, moments, kappa, B, stream=None):
         """molc_grey_coefficients: {name: [cell] tensor} for kappa_E, kappa_B, KRx, KRy, eta_x, eta_y."""
         out = torch.empty((6, self.ncell), dtype=torch.float64, device=kappa.device)
-        m = _Moments(*[moments[k].data_ptr() for k in MOMENTS])
+        self._fields(kappa, B)
+        m = self._moments(moments)
         _check(self._lib.molc_grey_coefficients(self._h, C.byref(m), _ptr(kappa), _ptr(B), _ptr(out),
                                                 _stream(stream)))
         return dict(zip(self.GREY, out))
@@ -384,10 +420,18 @@ class Batch:
         """args: one dict per instance with kappa, B, c, dt, I, bnd, out (moments dict) and optionally f
         (dict fxx, fxy, fyy)."""
         arr = (_SweepArgs * len(self.plans))()
-        for i, a in enumerate(args):
+        if len(args) != len(self.plans):
+            raise ValueError(f"bind: need {len(self.plans)} argument sets")
+        for i, (a, P) in enumerate(zip(args, self.plans)):
             f = a.get("f")
+            P._fields(a["kappa"], a["B"], a["bnd"])
+            P._state("fp32", a["I"])
+            m = P._moments(a["out"])
+            if f:
+                for k in ("fxx", "fxy", "fyy"):
+                    _check_f64(f[k], P.G * P.ncell, k)
             arr[i] = _SweepArgs(_ptr(a["kappa"]), _ptr(a["B"]), float(a["c"]), float(a["dt"]), _ptr(a["I"]),
-                                _ptr(a["bnd"]), _Moments(*[a["out"][k].data_ptr() for k in MOMENTS]),
+                                _ptr(a["bnd"]), m,
                                 *([_ptr(f["fxx"]), _ptr(f["fxy"]), _ptr(f["fyy"])] if f else [None] * 3))
         _check(self._lib.molc_batch_bind(self._h, arr))
         self._args = args     # keep the tensors alive while bound

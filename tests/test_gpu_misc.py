@@ -264,3 +264,28 @@ def test_kernel_timing_hook(molc):
     P.sweep("fp32", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"]))
     assert P.kernel_time() == (0.0, 0)
     P.close()
+
+
+def test_binding_rejects_tensors_of_the_wrong_size_or_type(molc):
+    # checked on the host before any launch: no kernel ever sees a buffer shorter than the plan needs
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
+    I = P.new_intensity("fp32")
+    P.intensity_init("fp32", I, B)
+    with pytest.raises(ValueError):
+        P.sweep("fp32", k[:-1], B, d["c"], d["dt"], I, bnd)                   # kappa one group short
+    with pytest.raises(ValueError):
+        P.sweep("fp32", k.float(), B, d["c"], d["dt"], I, bnd)               # FP32 inputs
+    with pytest.raises(ValueError):
+        P.sweep("fp32", k, B, d["c"], d["dt"], I, bnd[:, :1])                # boundary of one group
+    with pytest.raises(ValueError):
+        P.sweep("fp64", k, B, d["c"], d["dt"], I, bnd)                       # an FP32 state as FP64
+    out = P.new_moments()
+    out["Fy"] = out["Fy"][:1]
+    with pytest.raises(ValueError):
+        P.sweep("fp32", k, B, d["c"], d["dt"], I, bnd, out=out)              # a short moment array
+    torch.cuda.synchronize()
+    assert P.device_status() == 0
+    P.close()
