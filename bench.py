@@ -235,8 +235,10 @@ def run_ours(args):
     alg_bytes = (8.0 * info.n_updates                       # deviation state: 4 B read + 4 B written per update
                  + 16.0 * info.n_track_segments * n_chunks  # segment records, once per group chunk
                  + 20.0 * ncell * G)                        # cell table {kappa~, r, B_hi, B_lo, dB}, read once
-    # the cell-moment gather: the swept state read once more, the cell entry lists, B in, 6 moments + B_ref out
-    mom_bytes = (4.0 * info.n_updates + 16.0 * 2 * info.n_track_segments * n_chunks + (8.0 + 56.0) * ncell * G)
+    # the cell-moment gather: the swept state read once more, the cell entry lists, B in, 6 moments + B_ref out,
+    # and the 3 Eddington factors molc_sweep_closure forms there
+    mom_bytes = (4.0 * info.n_updates + 16.0 * 2 * info.n_track_segments * n_chunks
+                 + (8.0 + 56.0 + 24.0) * ncell * G)
     nk = max(kern_n, 1)
     kern_avg = kern_ms / nk
     peak, peak_kind = measured_peaks()
