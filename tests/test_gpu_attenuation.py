@@ -58,3 +58,42 @@ def test_segment_average_is_E1_over_twelve_decades_of_tau(molc, prec, tol):
     err = np.abs(got - ref) / ref
     assert err.max() <= tol, (float(err.max()), float(tau.flat[np.argmax(err)]))
     P.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 8e-6), ("fp64", 1e-14)])
+def test_hand_worked_characteristic(molc, prec, tol):
+    # the characteristic of tests/golden/single_ray_3x3.txt (cells and lengths worked out by hand): the library's
+    # grid reproduces it and, with Q = 0, its segment averages are I_in,s (1 - e^-tau_s) / tau_s
+    import math
+    import os
+    rows = [ln.split() for ln in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                                   "single_ray_3x3.txt")) if ln.strip() and not ln.startswith("#")]
+    direction, ray, edge = (int(x) for x in rows[0])
+    cells = [int(r[0]) for r in rows[1:]]
+    lens = [float(r[1]) * math.sqrt(2.0) for r in rows[1:]]
+    mu, cphi, sphi, w = molc.quadrature_product(1, 4)
+    P = molc.Plan(3, 3, 3.0, 3.0, mu, cphi, sphi, w, 1, 3.0 * math.sqrt(2.0) / 4.0)
+    tr = P.tracks()
+    rg = tr["dir_ray_off"][direction] + ray
+    s0, s1 = tr["ray_seg_off"][rg], tr["ray_seg_off"][rg + 1]
+    assert tr["entry"][rg] == edge and tr["cell"][s0:s1].tolist() == cells
+    assert np.allclose(tr["len"][s0:s1], lens, rtol=0, atol=1e-14)
+    dev = dict(device="cuda", dtype=torch.float64)
+    kappa = 0.3 + 0.7 * np.arange(9, dtype=float)
+    k = torch.tensor(kappa[None, :], **dev)
+    B = torch.zeros((1, 9), **dev)
+    bnd = torch.zeros((4, 1), **dev)
+    bnd[edge] = 1.0
+    I = P.new_intensity(prec)
+    P.intensity_init(prec, I, B)
+    P.sweep(prec, k, B, C_LIGHT, DT, I, bnd)
+    got = P.intensity_export(prec, I).cpu().numpy()[s0:s1, 0]
+    sinz = math.sqrt(3.0) / 2.0
+    Iin = 1.0
+    for j, (cell, ln) in enumerate(zip(cells, lens)):
+        tau = (kappa[cell] + 1.0 / (C_LIGHT * DT)) * ln / sinz
+        ref = Iin * (-math.expm1(-tau)) / tau
+        assert abs(got[j] - ref) <= tol * ref, (j, got[j], ref)
+        Iin *= math.exp(-tau)
+    assert P.device_status() == 0
+    P.close()
