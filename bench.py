@@ -40,7 +40,7 @@ SWEEP_FP32_DRAM_BYTES_PER_UPDATE = 8.63
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -62,25 +62,34 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms around the timed region; mark() brackets the
+    region so that the summary keeps the samples taken inside it (one interval of slack on each side)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.2
 
     def __init__(self):
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
-                                         stderr=subprocess.DEVNULL)
+                                          "-lms", str(int(self.PERIOD_S * 1000)), "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def stop(self):
         if not self.proc:
@@ -90,22 +99,50 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         try:
-            for line in open(self.path):
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+            lines = open(self.path).read().splitlines()
+        except Exception:
+            lines = []
         finally:
-            os.unlink(self.path)
-        if not rows:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return summarize_clocks(lines, self.t0, self.t1, self.PERIOD_S)
+
+
+def summarize_clocks(lines, t0=None, t1=None, period=0.2):
+    """Median SM clock, max clock and active throttle reasons of nvidia-smi CSV rows (the FIELDS of
+    ClockSampler); rows stamped within [t0 - period, t1 + period] (the timed region) when any are, else all."""
+    import datetime
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        rows.append((ts, parts[1:]))
+    if not rows:
+        return None
+    inside = [r for ts, r in rows
+              if ts is not None and t0 is not None and t1 is not None and t0 - period <= ts <= t1 + period]
+    use = inside if inside else [r for _, r in rows]
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+
+    sm = [v for v in (num(r[1]) for r in use) if v is not None]
+    mx = [v for v in (num(p[2]) for _, p in rows) if v is not None]
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    reasons = sorted({n for r in use for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows), "samples_in_timed_region": len(inside)}
 
 
 def cpu_oracle_sample(wl, d, max_seconds=12.0):
@@ -214,11 +251,15 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.mark(True)
     e0.record()
     for _ in range(args.steps):
         f = step()
     e1.record()
     torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(False)
     barrier()
     ms = pdist.max_over_ranks(e0.elapsed_time(e1), dev)
     parts, kern_n = P.kernel_time_parts()
@@ -424,10 +465,12 @@ def run_batch(args):
     sampler.start()
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
     e0.record()
     g.replay()
     e1.record()
     torch.cuda.synchronize()
+    sampler.mark(False)
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     status = max(P.device_status() for P in plans)
