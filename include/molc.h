@@ -130,21 +130,21 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
 
 molc_status molc_plan_get_info(const molc_plan *plan, molc_plan_info *info);
 
-/* The opaque intensity state I^{n-1} of one precision: one element per (segment, direction, group) (FP64: 8
- * bytes, FP32: 4, laid out for the sweep kernel with a little padding) holding the deviation of the segment
- * average from the cell's Planck intensity, followed by that reference Planck intensity per (group, cell) in
- * FP64 and a small header.  The FP32 state works in units scaled by a power of two that maps max(B, boundary)
- * near 2^100 (set by molc_intensity_init from B, and reset by any sweep whose max(B, boundary) has moved by more
- * than ~2^8 from it, the stored deviations being rescaled exactly as they are read), which keeps intensities down
- * to ~1e-68 of that maximum in the normal FP32 range.  molc_intensity_count gives the elements,
- * molc_intensity_bytes the bytes to allocate (256-byte aligned device memory).  The layout is private to the
- * library; use export/import to read or write segment averages. */
+/* The opaque intensity state I^{n-1} of one precision (the previous step's segment averages in the source Q of Eq.
+ * 11): one element per (segment, direction, group) (FP64: 8 bytes, FP32: 4, laid out for the sweep kernel with a
+ * little padding) holding the deviation of the segment average from the cell's Planck intensity, followed by that
+ * reference Planck intensity per (group, cell) in FP64 and a small header. The FP32 state works in units scaled by
+ * a power of two that maps max(B, boundary) near 2^100 (set by molc_intensity_init from B, and reset by any sweep
+ * whose max(B, boundary) has moved by more than ~2^8 from it, the stored deviations being rescaled exactly as they
+ * are read), which keeps intensities down to ~1e-68 of that maximum in the normal FP32 range. molc_intensity_count
+ * gives the elements, molc_intensity_bytes the bytes to allocate (256-byte aligned device memory). The layout is
+ * private to the library; use export/import to read or write segment averages. */
 int64_t molc_intensity_count(const molc_plan *plan);
 size_t molc_intensity_bytes(const molc_plan *plan, molc_precision prec);
 
-/* I^{n-1} := B_g of the segment's cell on every segment, direction and group (the state before the first
- * step), and the state's scale.  I: device, molc_intensity_bytes(prec).  B: device [G][cell], finite and
- * >= 0.  Allocation-free (memsets, a copy and two small kernels). */
+/* I^{n-1} := B_g of the segment's cell on every segment, direction and group (the state before the first step: Eq.
+ * 11's I^{n-1} for a medium starting in equilibrium), and the state's scale. I: device, molc_intensity_bytes(prec).
+ * B: device [G][cell], finite and >= 0. Allocation-free (memsets, a copy and two small kernels). */
 molc_status molc_intensity_init(molc_plan *plan, molc_precision prec, void *I, const double *B,
                                 molc_stream stream);
 
@@ -192,13 +192,12 @@ molc_status molc_sweep_static_scratch(molc_plan *plan, molc_precision prec, cons
                                       const double *B, double c, double dt, void *I, const double *bnd,
                                       const molc_moments *out, molc_stream stream);
 
-/* ---- Batched FP32 sweep of many independent instances (plans of any sizes, group counts and quadratures on
- * one device): every step runs as one launch of each kernel over the work of all instances (one sweep launch
- * per distinct (polar count, staging depth) and one moment launch per polar count), with the sweep blocks of
- * all instances scheduled longest first.  Built for many uneven problems in one time-stepping loop, where
- * per-instance launches would leave most of the GPU idle.  The paper sweeps one problem; this is the
- * production packaging of the same per-instance sweep (results are bit-identical to molc_sweep + molc_closure
- * per instance). */
+/* ---- Batched FP32 sweep of many independent instances (Eqs. 7, 11-15 for each; plans of any sizes, group counts
+ * and quadratures on one device): every step runs as one launch of each kernel over the work of all instances (one
+ * sweep launch per distinct (polar count, staging depth) and one moment launch per polar count), with the sweep
+ * blocks of all instances scheduled longest first. Built for many uneven problems in one time-stepping loop, where
+ * per-instance launches would leave most of the GPU idle. The paper sweeps one problem; this is the production
+ * packaging of the same per-instance sweep (results are bit-identical to molc_sweep + molc_closure per instance). */
 typedef struct molc_batch molc_batch;
 
 /* Per-instance arguments, as for molc_sweep (device pointers) plus optional Eddington factors. */
@@ -211,21 +210,23 @@ typedef struct {
   double *fxx, *fxy, *fyy;      /* device [G][cell] (f = N / (c E), as molc_closure), or all NULL */
 } molc_sweep_args;
 
-/* plans: host array of n (>= 1) plans created on the current device (not MOLC_HOST_ONLY, MOLC_FACES or
- * MOLC_BALANCE, at most 8 polar cosines; MOLC_ERR_INVALID_ARG otherwise); the batch keeps pointers to them
- * (destroy the batch first).  Builds the block maps (device). */
+/* Builds a batch (no counterpart in the paper: block maps over the instances). plans: host array of n (>= 1) plans
+ * created on the current device (not MOLC_HOST_ONLY, MOLC_FACES or MOLC_BALANCE, at most 8 polar cosines;
+ * MOLC_ERR_INVALID_ARG otherwise); the batch keeps pointers to them (destroy the batch first). Builds the block
+ * maps (device). */
 molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out);
 
-/* Record the per-instance arguments (host array of n, copied to the device synchronously).  Call again whenever
- * a buffer changes; molc_batch_sweep uses the last recorded arguments. */
+/* Record the per-instance arguments of Eqs. 11-15 (and 7) (host array of n, copied to the device synchronously).
+ * Call again whenever a buffer changes; molc_batch_sweep uses the last recorded arguments. */
 molc_status molc_batch_bind(molc_batch *batch, const molc_sweep_args *args);
 
-/* One backward-Euler step of every instance: molc_sweep_closure in FP32 for the instances bound with factor
- * outputs, molc_sweep for the others.
- * Asynchronous on `stream`; no allocation and no host synchronisation, so a step (or several) can be captured
- * in a CUDA graph and replayed.  Device status words are per plan (molc_device_status). */
+/* One backward-Euler step (Eqs. 11-15) of every instance: molc_sweep_closure in FP32 for the instances bound with
+ * factor outputs, molc_sweep for the others. Asynchronous on `stream`; no allocation and no host synchronisation,
+ * so a step (or several) can be captured in a CUDA graph and replayed. Device status words are per plan
+ * (molc_device_status). */
 molc_status molc_batch_sweep(molc_batch *batch, molc_stream stream);
 
+/* Frees the batch (no counterpart in the paper). */
 void molc_batch_destroy(molc_batch *batch);
 
 /* Eddington factors of each cell and group, f = N / (c E) (Eq. 7 with the cell averages of Eq. 15):
@@ -284,38 +285,39 @@ molc_status molc_face_moments(const molc_plan *plan, molc_precision prec, const 
 molc_status molc_grey_coefficients(const molc_plan *plan, const molc_moments *m, const double *kappa,
                                    const double *B, double *out, molc_stream stream);
 
-/* Canonical intensity layout: [n_segments][g_count] FP64 segment averages, direction-major in quadrature
- * order; within a direction, characteristics by increasing offset along (-sin phi, cos phi) and segments in
- * traversal order.  export: canon := I (groups g_begin .. g_begin+g_count-1).  import: I := canon for the same
- * groups, with B (device [G][cell]) as the new reference Planck intensity of those groups.  Device memory. */
+/* Canonical intensity layout: [n_segments][g_count] FP64 segment averages (Ibar of Eq. 12), direction-major in
+ * quadrature order; within a direction, characteristics by increasing offset along (-sin phi, cos phi) and segments
+ * in traversal order. export: canon := I (groups g_begin .. g_begin+g_count-1). import: I := canon for the same
+ * groups, with B (device [G][cell]) as the new reference Planck intensity of those groups. Device memory. */
 molc_status molc_intensity_export(const molc_plan *plan, molc_precision prec, const void *I, int g_begin,
                                   int g_count, double *canon, molc_stream stream);
 molc_status molc_intensity_import(molc_plan *plan, molc_precision prec, void *I, int g_begin, int g_count,
                                   const double *canon, const double *B, molc_stream stream);
 
-/* The characteristic grid in the canonical order (host arrays): dir_ray_off[n_dir+1], ray_seg_off[rays+1],
- * width[rays], entry[rays] (edge 0..3), cell[n_segments], len[n_segments] (in-plane l), area[n_segments]
- * (A after renormalisation).  rays = 2 n_polar n_tracks. */
+/* The characteristic grid of Sec. 3 in the canonical order (host arrays): dir_ray_off[n_dir+1],
+ * ray_seg_off[rays+1], width[rays], entry[rays] (edge 0..3), cell[n_segments], len[n_segments] (in-plane l),
+ * area[n_segments] (A after renormalisation). rays = 2 n_polar n_tracks. */
 molc_status molc_tracks_export(const molc_plan *plan, int64_t *dir_ray_off, int64_t *ray_seg_off, double *width,
                                int *entry, int *cell, double *len, double *area);
 
-/* Kernel timing for benchmarks: while enabled, every molc_sweep records CUDA events around its three kernels
- * (input preparation, the sweep itself, the cell moments; at most 4096 calls are kept).  molc_kernel_time
- * synchronises with the last recorded event, returns the summed elapsed milliseconds of the sweep kernel and
- * the number of timed calls, and clears the record; molc_kernel_time_parts does the same with
- * parts_ms[3] = {preparation, sweep, moments}.  Disabled by default; enabling creates the events (no device
- * memory allocation). */
+/* Kernel timing for benchmarks (no counterpart in the paper): while enabled, every molc_sweep records CUDA events
+ * around its three kernels (input preparation, the sweep itself, the cell moments; at most 4096 calls are kept).
+ * molc_kernel_time synchronises with the last recorded event, returns the summed elapsed milliseconds of the sweep
+ * kernel and the number of timed calls, and clears the record; molc_kernel_time_parts does the same with
+ * parts_ms[3] = {preparation, sweep, moments}. Disabled by default; enabling creates the events (no device memory
+ * allocation). */
 molc_status molc_kernel_timing(molc_plan *plan, int enable);
 molc_status molc_kernel_time(molc_plan *plan, double *total_ms, int *launches);
 molc_status molc_kernel_time_parts(molc_plan *plan, double *parts_ms, int *launches);
 
-/* Read and clear the plan's device status word (synchronises with the device).  *code = MOLC_OK or the first
- * error the kernels recorded. */
+/* Read and clear the plan's device status word (error reporting, no counterpart in the paper; synchronises with the
+ * device). *code = MOLC_OK or the first error the kernels recorded. */
 molc_status molc_device_status(molc_plan *plan, int *code);
 
-/* Message of the last failure on the calling thread ("" if none). */
+/* Message of the last failure on the calling thread ("" if none; no counterpart in the paper). */
 const char *molc_last_error(void);
 
+/* Frees the plan and its device memory (no counterpart in the paper). */
 void molc_destroy(molc_plan *plan);
 
 #ifdef __cplusplus
