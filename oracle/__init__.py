@@ -72,7 +72,7 @@ def _dp(a):
 
 @dataclass
 class Geometry:
-    """Material grid, angular quadrature and characteristic-grid rule."""
+    """Material grid, angular quadrature and characteristic-grid rule (Sec. 3; readings c4, c9)."""
     nx: int
     ny: int
     lx: float
@@ -105,7 +105,7 @@ class Geometry:
 
 
 def counts(geom: Geometry):
-    """(characteristics, segments), both summed over directions."""
+    """(characteristics, segments) of the characteristic grid of Sec. 3, both summed over directions."""
     lib = _load()
     g = geom._c()
     out = np.zeros(2, dtype=np.int64)
@@ -116,7 +116,7 @@ def counts(geom: Geometry):
 
 
 def tracks(geom: Geometry, precision: str = "quad") -> dict:
-    """The characteristic grid in canonical order (direction, characteristic by offset, segment)."""
+    """The characteristic grid of Sec. 3 in canonical order (direction, characteristic by offset, segment)."""
     lib = _load()
     nr, ns = counts(geom)
     g = geom._c()
@@ -137,16 +137,19 @@ FACE_MOMENTS = ("face_E", "face_Fx", "face_Fy", "face_Nxx", "face_Nxy", "face_Ny
 
 
 def n_faces(geom: Geometry) -> int:
-    """x-faces (nx + 1) ny, then y-faces nx (ny + 1)."""
+    """Faces of the material grid that carry the face moments of Eq. 16: x-faces (nx + 1) ny, then y-faces
+    nx (ny + 1)."""
     return (geom.nx + 1) * geom.ny + geom.nx * (geom.ny + 1)
 
 
 def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
           want_I=True, want_exit=False, threads=None, I_as_deviation=False, I_prev_is_deviation=False,
           want_faces=False) -> dict:
-    """One backward-Euler sweep.  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
+    """One backward-Euler sweep (Sec. 3: Eqs. 11-13 along every characteristic, Eqs. 14-15 and the Sec. 2
+    moment definitions per cell).  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
     (I^{n-1} = B of the segment's cell); with I_prev_is_deviation, I_prev holds deviations from B of the
-    segment's cell (so a state carried between steps as deviations keeps its precision).  Returns the cell moments as [Gsub][ncell] arrays keyed by name,
+    segment's cell (so a state carried between steps as deviations keeps its precision).  Returns the cell
+    moments as [Gsub][ncell] arrays keyed by name,
     plus 'I' (canonical [nseg][Gsub] segment averages, or their deviations from the cell's B formed in the
     oracle's precision when I_as_deviation) and 'I_exit' ([nrays][Gsub]) when asked."""
     lib = _load()
@@ -195,6 +198,7 @@ def closure(E, Nxx, Nxy, Nyy, c):
 
 
 def real_bits(precision: str) -> int:
+    """Bits of the oracle's real type for a precision name (bookkeeping)."""
     return _load().oracle_real_bits(PREC[precision])
 
 

@@ -104,7 +104,8 @@ template <class R> struct Dir {
   std::vector<Ray<R>> rays;   // ordered by increasing offset along n = (-dy, dx)
 };
 
-// Offsets t (along the normal n) and widths of the characteristics of one direction.
+// Offsets t (along the normal n) and widths of the characteristics of one direction (Sec. 3, construction of
+// the characteristic grid; uniform spacing or the vertex bands halved to h_moc, reading c4).
 // (evaluated in double: part of the definition of the characteristic grid)
 static void characteristic_offsets(const oracle_geom &g, double dx, double dy, std::vector<double> &t,
                                    std::vector<double> &w) {
@@ -231,6 +232,7 @@ static bool trace(const oracle_geom &g, R dx, R dy, R t, R width, Ray<R> &ray) {
   return !ray.cell.empty();
 }
 
+// Unit in-plane direction (cos phi, sin phi) of direction m (Sec. 3; quadrature of reading c9).
 // (evaluated in double: part of the definition of the characteristic grid)
 static void unit_dir(const oracle_geom &g, int m, double &dx, double &dy) {
   const double c = g.cos_phi[m], s = g.sin_phi[m];
@@ -239,6 +241,8 @@ static void unit_dir(const oracle_geom &g, int m, double &dx, double &dy) {
   dy = s / n;
 }
 
+// The characteristics of one in-plane direction with their segments (cells, in-plane lengths l, areas A = l w of
+// Eq. 14, entry edges), Sec. 3.
 template <class R> static int build_dir(const oracle_geom &g, int m, Dir<R> &d) {
   double dxd, dyd;
   unit_dir(g, m, dxd, dyd);
@@ -277,6 +281,7 @@ template <class R> static int build_dir(const oracle_geom &g, int m, Dir<R> &d) 
   return 0;
 }
 
+// Argument checks of the geometry (no counterpart in the paper).
 static int check_geom(const oracle_geom *g) {
   if (!g || g->nx < 1 || g->ny < 1 || !(g->lx > 0) || !(g->ly > 0) || g->ndir < 1 || !(g->spacing > 0)) return -1;
   if (!g->mu || !g->cos_phi || !g->sin_phi || !g->w) return -1;
@@ -307,7 +312,7 @@ template <class R> struct Geometry {
 };
 
 // Segment counts per direction (canonical order: direction m, then its characteristics by increasing
-// offset along n = (-dy, dx), then segments in traversal order).
+// offset along n = (-dy, dx), then segments in traversal order); bookkeeping, no counterpart in the paper.
 template <class R> static void canonical_offsets(const oracle_geom &g, const Geometry<R> &geo,
                                                  std::vector<int64_t> &seg_dir_off) {
   seg_dir_off.assign(g.ndir + 1, 0);
@@ -463,6 +468,7 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
   return 0;
 }
 
+// The characteristic grid of Sec. 3 (every direction's characteristics and segments) in canonical order.
 template <class R>
 static int run_tracks(const oracle_geom *g, int64_t *counts, int64_t *dir_ray_off, int64_t *ray_seg_off,
                       double *width, int *entry, int *cell, double *len, double *area, int *face) {
@@ -497,13 +503,13 @@ static int run_tracks(const oracle_geom *g, int64_t *counts, int64_t *dir_ray_of
 
 extern "C" {
 
-// Sizes of the characteristic grid: counts[0] = characteristics summed over directions, counts[1] = segments
+// Sizes of the characteristic grid (Sec. 3): counts[0] = characteristics summed over directions, counts[1] = segments
 // summed over directions (the length of the canonical per-group intensity array).  Returns 0 on success.
 int oracle_count(const oracle_geom *g, int64_t *counts) {
   return run_tracks<double>(g, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
 }
 
-// The characteristic grid in canonical order.  precision: 0 = double, 1 = binary128 (values rounded to double).
+// The characteristic grid of Sec. 3 in canonical order.  precision: 0 = double, 1 = binary128 (values rounded to double).
 int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int64_t *ray_seg_off,
                   double *width, int *entry, int *cell, double *len, double *area, int *face) {
   if (!dir_ray_off || !ray_seg_off || !width || !entry || !cell || !len || !area) return -1;
@@ -538,6 +544,7 @@ int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa
                                        nthreads, store_dev, prev_dev, face_out);
 }
 
+// Bits of the oracle's real type (bookkeeping, no counterpart in the paper).
 int oracle_real_bits(int precision) { return precision ? (int)(sizeof(real128) * 8) : 64; }
 
 }  // extern "C"
