@@ -1,9 +1,9 @@
 #!/usr/bin/env python
 """Benchmark of the MOLC high-order sweep (Sec. 3) on one or more GB300 GPUs.
 
-One step = one backward-Euler sweep of every direction, characteristic and group (FP32 production path,
-molc_sweep) followed by the Eddington closure (molc_closure), on the 512 x 512-cell, 17-group, 4 x 32-direction,
-h/2-spacing synthetic Fleck-Cummings-shaped workload with three tanh fronts.  The intensity state (5.8 GB) is
+One step = one call of molc_sweep_closure in FP32: the backward-Euler sweep of every direction, characteristic and
+group, the cell moments and the Eddington factors, on the 512 x 512-cell, 17-group, 4 x 32-direction, h/2-spacing
+synthetic Fleck-Cummings-shaped workload with three tanh fronts.  The intensity state (5.8 GB) is
 far larger than L2, so no cache flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead (double precision, all host
@@ -31,10 +31,25 @@ from paper_2305_11998_gb300 import dist as pdist  # noqa: E402
 
 WORKLOAD = "fc512_g17_d128"
 METRIC = "segment×group updates/s"
-# ncu dram bytes (read + write) per update of sweep_fp32_kernel, from the capture summarised in
-# profiles/sweep_moments_fp32_fc384_g17.md (384x384 cells, same kernel configuration), scaled by the updates of
-# the launch; None once the kernel changes after that capture.
-SWEEP_FP32_DRAM_BYTES_PER_UPDATE = 8.63
+# ncu dram bytes (read + write) per update of the dominant FP32 kernel, from an ncu capture of a smaller case of the
+# same generators, scaled by the updates of the launch.  The figure is keyed to the SHA-256 of the kernel source it
+# was taken on: once the source changes, the bench line reports traffic as null until a new capture is recorded.
+SWEEP_FP32_TRAFFIC = {"kernel_source_sha256": None, "dram_bytes_per_update": None}
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2305_11998_gb300", "csrc", "molc_kernels.cu")
+
+
+def traffic_per_update():
+    """The recorded ncu bytes per update, or None when the kernel source differs from the captured one."""
+    import hashlib
+    rec = SWEEP_FP32_TRAFFIC
+    if rec["kernel_source_sha256"] is None or rec["dram_bytes_per_update"] is None:
+        return None
+    try:
+        with open(KERNEL_SOURCE, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return rec["dram_bytes_per_update"] if h == rec["kernel_source_sha256"] else None
 
 
 def parse():
@@ -50,7 +65,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
-                    help="only the FP32 sweeps (warmup + steps), for profiler captures")
+                    help="only the sweeps (warmup + steps) in --precision, for profiler captures")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the --kernel-only sweeps (fp64: also the device's FP64 FMA rate)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 20 if args.impl == "reference" else 100
@@ -290,13 +307,21 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kern_avg / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": (None if SWEEP_FP32_DRAM_BYTES_PER_UPDATE is None
-                            else SWEEP_FP32_DRAM_BYTES_PER_UPDATE * info.n_updates),
+                "traffic": (None if traffic_per_update() is None else traffic_per_update() * info.n_updates),
                 "kernel": "sweep_fp32_kernel", "kernel_ms": kern_avg,
                 "alg_bytes_per_launch": alg_bytes, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
     kernels = {"prep_ms": parts["prep"] / nk, "sweep_ms": kern_avg, "moments_ms": parts["moments"] / nk,
                "moments_gbs": mom_bytes / (parts["moments"] / nk / 1e3) / 1e9 if parts["moments"] > 0 else None,
                "moments_alg_bytes": mom_bytes}
+    # the whole step (every kernel of molc_sweep_closure) against the algorithmic bytes of the path: the FP32
+    # state read and written (8 B per update), the segment records walked by both senses (8 B per track segment
+    # per sense), kappa and B read once (16 B per cell-group), six FP64 moments and three Eddington factors
+    # written once (72 B per cell-group)
+    step_bytes = 8.0 * info.n_updates + 16.0 * info.n_track_segments + (16.0 + 72.0) * ncell * G
+    step_gbs = step_bytes / (ms_step / 1e3) / 1e9
+    roofline_step = {"bound": "hbm", "achieved": step_gbs, "peak": peak, "unit": "GB/s", "frac": step_gbs / peak,
+                     "alg_bytes_per_step": step_bytes, "ms_per_step": ms_step,
+                     "what": "all kernels of one molc_sweep_closure call (device events around the K steps)"}
 
     # end to end through the public API: every step copies its kappa, B and boundary in from pinned host
     # memory and its moments and Eddington factors out to pinned host memory.  The copies are pipelined
@@ -399,7 +424,7 @@ def run_ours(args):
                            "updates_per_step_per_gpu": info.n_updates,
                            "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
                            "step": "molc_sweep_closure (FP32 sweep, moments and Eddington factors in one call)"},
-                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "roofline_step": roofline_step, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
         print(json.dumps(line), flush=True)
     P.close()
@@ -408,26 +433,31 @@ def run_ours(args):
 
 
 def run_kernel_only(args):
-    """FP32 sweeps only (no closure, e2e, FP64 or CPU legs): the command profiler captures use."""
+    """Sweeps only, in --precision (no closure, e2e or CPU legs): the command profiler captures use.  With
+    fp64 it also reports the device's FP64 FMA rate (molc_fp64_fma_rate), the bound of the plain FP64 sweep."""
     import torch
     import paper_2305_11998_gb300 as molc
     wl = synth.WORKLOADS[args.workload]
     d = wl.inputs(seed=0)
     P = molc.Plan.from_workload(wl)
     dev = torch.device("cuda")
+    prec = args.precision
     k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
-    I = P.new_intensity("fp32", dev)
-    P.intensity_init("fp32", I, B)
+    I = P.new_intensity(prec, dev)
+    P.intensity_init(prec, I, B)
     out = P.new_moments(dev)
     for _ in range(args.warmup):
-        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=out)
+        P.sweep(prec, k, B, wl.c, wl.dt, I, bnd, out=out)
     P.kernel_timing(True)
     for _ in range(args.steps):
-        P.sweep("fp32", k, B, wl.c, wl.dt, I, bnd, out=out)
-    ms, n = P.kernel_time()
-    print(json.dumps({"workload": wl.name, "kernel": "sweep_fp32_kernel", "launches": n,
-                      "kernel_ms": ms / max(n, 1), "updates": P.info.n_updates,
-                      "device_status": P.device_status()}), flush=True)
+        P.sweep(prec, k, B, wl.c, wl.dt, I, bnd, out=out)
+    parts, n = P.kernel_time_parts()
+    line = {"workload": wl.name, "precision": prec, "launches": n,
+            "kernel_ms": {k_: v / max(n, 1) for k_, v in parts.items()}, "updates": P.info.n_updates,
+            "device_status": P.device_status()}
+    if prec == "fp64":
+        line["fp64_fma_flops"] = molc.fp64_fma_rate()
+    print(json.dumps(line), flush=True)
     P.close()
 
 

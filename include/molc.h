@@ -310,6 +310,12 @@ molc_status molc_kernel_timing(molc_plan *plan, int enable);
 molc_status molc_kernel_time(molc_plan *plan, double *total_ms, int *launches);
 molc_status molc_kernel_time_parts(molc_plan *plan, double *parts_ms, int *launches);
 
+/* FP64 fused multiply-add throughput of the current device, in FLOP/s (2 per FMA): the bound of the plain FP64
+ * sweep's arithmetic (no counterpart in the paper; a measurement for the roofline).  Runs a kernel of independent
+ * FMA chains on every SM four times (the first as warm-up) on the legacy default stream, timed with CUDA events;
+ * synchronises with the device.  No device memory is allocated. */
+molc_status molc_fp64_fma_rate(double *flops_per_s);
+
 /* Read and clear the plan's device status word (error reporting, no counterpart in the paper; synchronises with the
  * device). *code = MOLC_OK or the first error the kernels recorded. */
 molc_status molc_device_status(molc_plan *plan, int *code);

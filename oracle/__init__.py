@@ -47,6 +47,11 @@ class _Geom(C.Structure):
                 ("spacing", C.c_double), ("layout", C.c_int), ("renorm", C.c_int)]
 
 
+class _ErrModel(C.Structure):
+    _fields_ = [("path", C.c_int), ("u", C.c_double), ("e_exp", C.c_double), ("e_rcp", C.c_double),
+                ("k_sum", C.c_double), ("abs_unit", C.c_double), ("Bref", C.POINTER(C.c_double))]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -57,7 +62,8 @@ def _load():
         lib.oracle_count.argtypes = [C.POINTER(_Geom), i64p]
         lib.oracle_tracks.argtypes = [C.POINTER(_Geom), C.c_int, i64p, i64p, dp, ip, ip, dp, dp, ip]
         lib.oracle_sweep.argtypes = [C.POINTER(_Geom), C.c_int, C.c_int, dp, dp, C.c_double, C.c_double, dp, dp,
-                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int, dp]
+                                     ip, C.c_int, dp, dp, dp, C.c_int, C.c_int, C.c_int, dp, C.POINTER(_ErrModel),
+                                     dp, dp, dp]
         for f in (lib.oracle_count, lib.oracle_tracks, lib.oracle_sweep):
             f.restype = C.c_int
         lib.oracle_real_bits.argtypes = [C.c_int]
@@ -142,16 +148,26 @@ def n_faces(geom: Geometry) -> int:
     return (geom.nx + 1) * geom.ny + geom.nx * (geom.ny + 1)
 
 
+BOUND_NAMES = ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")
+
+
 def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precision: str = "quad",
           want_I=True, want_exit=False, threads=None, I_as_deviation=False, I_prev_is_deviation=False,
-          want_faces=False) -> dict:
+          want_faces=False, errmodel=None, I_err=None) -> dict:
     """One backward-Euler sweep (Sec. 3: Eqs. 11-13 along every characteristic, Eqs. 14-15 and the Sec. 2
     moment definitions per cell).  kappa, B: [G][ncell]; bnd: [4][G]; I_prev: canonical [nseg][Gsub] or None
     (I^{n-1} = B of the segment's cell); with I_prev_is_deviation, I_prev holds deviations from B of the
     segment's cell (so a state carried between steps as deviations keeps its precision).  Returns the cell
     moments as [Gsub][ncell] arrays keyed by name,
     plus 'I' (canonical [nseg][Gsub] segment averages, or their deviations from the cell's B formed in the
-    oracle's precision when I_as_deviation) and 'I_exit' ([nrays][Gsub]) when asked."""
+    oracle's precision when I_as_deviation) and 'I_exit' ([nrays][Gsub]) when asked.
+
+    errmodel: {path: 0 (all operations in one precision) or 1 (FP32 with approximate 2^x and 1/x), u, e_exp,
+    e_rcp, k_sum, abs_unit, Bref (optional [G][ncell])} describes the arithmetic of a path that evaluates Eq. 12 in the
+    deviation form; the sweep then also returns 'bound' (the first-order bound of that path's error in E, Fx, Fy,
+    Nxx, Nxy, Nyy, [Gsub][ncell] each), 'dev' and 'plk' (the magnitudes of their deviation and Planck terms) and
+    'I_err' (the bound of the path's stored deviations, canonical [nseg][Gsub]).  I_err: the bound of the stored
+    deviations entering this step (from the previous step's 'I_err'), or None for an exact state."""
     lib = _load()
     kappa = np.ascontiguousarray(kappa, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
@@ -170,15 +186,35 @@ def sweep(geom: Geometry, kappa, B, c, dt, bnd, I_prev=None, groups=None, precis
     I_new = np.zeros((ns, Gsub)) if want_I else None
     I_exit = np.zeros((nr, Gsub)) if want_exit else None
     fout = np.zeros((6, Gsub, n_faces(geom))) if want_faces else None
+    em = err_out = Ierr_new = Bref = None
+    if errmodel is not None:
+        if errmodel.get("Bref") is not None:
+            Bref = np.ascontiguousarray(errmodel["Bref"], dtype=np.float64)
+            assert Bref.shape == B.shape
+        em = _ErrModel(int(errmodel["path"]), float(errmodel["u"]), float(errmodel["e_exp"]),
+                       float(errmodel.get("e_rcp", 0.0)), float(errmodel.get("k_sum", 0.0)),
+                       float(errmodel.get("abs_unit", 0.0)), _dp(Bref))
+        err_out = np.zeros((18, Gsub, geom.ncell))
+        Ierr_new = np.zeros((ns, Gsub))
+        if I_err is not None:
+            I_err = np.ascontiguousarray(I_err, dtype=np.float64)
+            assert I_err.shape == (ns, Gsub)
     g = geom._c()
     nthreads = threads or max(1, min(os.cpu_count() or 1, 64))
     rc = lib.oracle_sweep(C.byref(g), PREC[precision], G, _dp(kappa), _dp(B), float(c), float(dt), _dp(bnd),
                           _dp(I_prev), gl.ctypes.data_as(C.POINTER(C.c_int)) if gl is not None else None,
                           0 if gl is None else int(gl.size), _dp(out), _dp(I_new), _dp(I_exit), int(nthreads),
-                          int(bool(I_as_deviation)), int(bool(I_prev_is_deviation)), _dp(fout))
+                          int(bool(I_as_deviation)), int(bool(I_prev_is_deviation)), _dp(fout),
+                          C.byref(em) if em is not None else None, _dp(I_err if em is not None else None),
+                          _dp(Ierr_new), _dp(err_out))
     if rc:
         raise RuntimeError(f"oracle_sweep failed ({rc})")
     res = {k: out[i] for i, k in enumerate(MOMENTS)}
+    if em is not None:
+        res["bound"] = {k: err_out[i] for i, k in enumerate(BOUND_NAMES)}
+        res["dev"] = {k: err_out[6 + i] for i, k in enumerate(BOUND_NAMES)}
+        res["plk"] = {k: err_out[12 + i] for i, k in enumerate(BOUND_NAMES)}
+        res["I_err"] = Ierr_new
     if want_I:
         res["I"] = I_new
     if want_exit:
@@ -195,6 +231,20 @@ def closure(E, Nxx, Nxy, Nyy, c):
     fxy = np.asarray(Nxy) / cE
     fyy = np.asarray(Nyy) / cE
     return fxx, fxy, fyy
+
+
+def grey_eddington(E, Nxx, Nxy, Nyy, c):
+    """The E-weighted spectral average of the Eddington factors, <f>_E = sum_g f_g E_g / sum_g E_g (Sec. 2, Eq. 8
+    with u = f), from [G][ncell] arrays; f_g = N_g / (c E_g) per group (0 where E_g = 0), and the average is 0
+    where sum_g E_g = 0.  Returns (xx, xy, yy), each [ncell]."""
+    E = np.asarray(E, dtype=np.float64)
+    pos = E > 0
+    se = E.sum(0)
+    out = []
+    for N in (Nxx, Nxy, Nyy):
+        f = np.where(pos, np.asarray(N, dtype=np.float64) / np.where(pos, c * E, 1.0), 0.0)
+        out.append(np.where(se > 0, (f * E).sum(0) / np.where(se > 0, se, 1.0), 0.0))
+    return tuple(out)
 
 
 def real_bits(precision: str) -> int:

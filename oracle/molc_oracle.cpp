@@ -85,6 +85,22 @@ typedef struct {
   int layout;                 // 0: uniform parallel rays, 1: paper's vertex-band construction
   int renorm;                 // 1: scale areas so that sum_{C(i,m)} A = V_i
 } oracle_geom;
+
+// Rounding-error model of a sweep that carries the deviation psi = I - B_cell along each characteristic (the
+// form the GPU paths compute Eq. 12 in), for a first-order running error bound (test infrastructure: it bounds the
+// arithmetic of a path, it is not part of the method).  path 0: every operation in a precision of unit roundoff u
+// with exp and expm1 of relative error <= e_exp; path 1: FP32 operations (unit roundoff u) with the exponential
+// formed as 2^x by an approximation of relative error <= e_exp and 1/x of relative error <= e_rcp, the average
+// E1 = (1 - e^-tau)/tau below tau = 1/2 taken as e^-tau/2 sinh(tau/2)/(tau/2) by its series to the (tau/2)^6 term.
+// k_sum: roundings of relative u a moment term passes through on its way into the cell sums, beyond those of its
+// segment average (path 1; path 0 sums terms one by one in any order, bounded by gamma_{n-1} per cell).
+// abs_unit: the absolute error of one operation whose result falls below the path's normal range (FP32 in scaled
+// units: 2^-126 divided by the state's scale), added for every operation of a segment.
+typedef struct {
+  int path;
+  double u, e_exp, e_rcp, k_sum, abs_unit;
+  const double *Bref;         // [G][ncell] Planck intensity the path's stored deviations refer to, or NULL (= B)
+} oracle_errmodel;
 }
 
 enum { EDGE_L = 0, EDGE_R = 1, EDGE_B = 2, EDGE_T = 3 };
@@ -327,12 +343,60 @@ template <class R> static void canonical_offsets(const oracle_geom &g, const Geo
 // on the number of threads).
 enum { MOM_D = 0, MOM_FX, MOM_FY, MOM_NXX, MOM_NXY, MOM_NYY, MOM_NZZ, MOM_AFX, MOM_AFY, MOM_ANXY, MOM_BNXY, MOM_BFX,
        MOM_BFY, N_MOM };
+// With an error model: per cell, for each of the six outputs k (D, Fx, Fy, Nxx, Nxy, Nyy) the sum of
+// omega A |factor_k| times the bound of the term's segment average (ERR), the magnitude of the deviation terms
+// omega A |factor_k| |Ibar - B| (DEV) and of the Planck terms omega A |factor_k| B (PLK), and the term count.
+enum { ERR0 = 0, DEV0 = 6, PLK0 = 12, ECNT = 18, N_ERR = 19 };
+
+// First-order bound of the errors of one segment's computed segment-average deviation (bar) and outgoing
+// deviation (out) under an error model, from the magnitudes of the exact values: tau, e = e^-tau, om = 1 - e^-tau,
+// E1 = om / tau, x = psi_in - d, pbar = Ibar - B, pout = I_out - B, the bounds eps_in of psi_in and eps_d of
+// d = S - B, and mu = cos(zeta).  The path computes pbar = d + x E1, and pout = psi_in - x om below tau = 1/2 and
+// d + x e above (each a fused multiply-add): pbar carries E1 eps_in + (1 - E1) eps_d, pout e eps_in + om eps_d,
+// plus the roundings of x, of the product's factor (relative bound r*) and of the result.  Near tau = 1/2 the path
+// may take either form; the larger bound is kept.
+struct SegBound {
+  double bar, out;
+};
+static SegBound segment_bound(const oracle_errmodel &em, double tau, double e, double om, double E1, double x,
+                              double pbar, double pout, double eps_in, double eps_d, double mu) {
+  const double u = em.u;
+  const bool may_thin = tau < 0.5 * (1 + 1e-4), may_thick = tau >= 0.5 * (1 - 1e-4);
+  double rE1 = 0, rom = 0, re = 0;
+  if (em.path == 1) {
+    // a = tau/2 from four FP32 roundings of its factors and two products: 5u; 2^(-a log2 e) with the argument
+    // rounded twice more: relative error 7u a + e_exp; e^-tau = h^2
+    const double rh = 3.5 * u * tau + em.e_exp;
+    re = 2 * rh + u;
+    const double rhp = rh + 4 * u + u + 5e-11;   // series in FP32 FMAs (4u), product h p (u), truncation
+    const double r1me = u + (om > 0 ? e / om : 0.0) * re;
+    const double ritau = 5 * u + em.e_rcp;        // 1/tau = sin(zeta) rcp(kappa~ l): 3u + e_rcp + 2u
+    const double rE1_thin = rhp, rE1_thick = r1me + ritau + u;
+    rE1 = std::max(may_thin ? rE1_thin : 0.0, may_thick ? rE1_thick : 0.0);
+    rom = 5 * u + rhp + u;                        // om = (a + a) h p
+  } else {
+    // tau = kappa~ l / sin(zeta): kappa~ 3u, l u, 1/sin(zeta) from sqrt(1 - mu^2) in the path's precision
+    const double rtau = (9.0 + mu * mu / (1.0 - mu * mu)) * u;
+    rom = rtau + em.e_exp;                        // -expm1(-tau): argument sensitivity <= rtau
+    re = tau * rtau + em.e_exp;
+    rE1 = rom + rtau + u;
+  }
+  SegBound b;
+  const double au = 16 * em.abs_unit;   // results below the normal range: the operations of one segment
+  b.bar = E1 * eps_in + (1 - E1) * eps_d + E1 * u * x + x * E1 * rE1 + u * pbar + au;
+  const double out_thin = e * eps_in + om * eps_d + om * u * x + x * om * rom + u * pout + au;
+  const double out_thick = e * eps_in + om * eps_d + e * u * x + x * e * re + u * pout + au;
+  b.out = std::max(may_thin ? out_thin : 0.0, may_thick ? out_thick : 0.0);
+  return b;
+}
 
 template <class R>
 static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m, int gi, int G, int gsel,
                             const double *kappa, const double *B, R inv_cdt, const double *bnd,
                             const double *I_prev, int64_t seg0, double *I_new, double *I_exit, int64_t ray0,
-                            int Gsub, int store_dev, int prev_dev, std::vector<R> *acc, std::vector<R> *facc) {
+                            int Gsub, int store_dev, int prev_dev, std::vector<R> *acc, std::vector<R> *facc,
+                            const oracle_errmodel *em, const double *Ierr_prev, double *Ierr_new,
+                            std::vector<double> *eacc) {
   const Dir<R> &d = geo.dirs[geo.of[m]];
   const int64_t ncell = (int64_t)g.nx * g.ny;
   const R mu = g.mu[m];
@@ -341,10 +405,17 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
   const R Ox = sinz * d.dx, Oy = sinz * d.dy;
   const double *kap = kappa + (int64_t)gsel * ncell;
   const double *Bg = B + (int64_t)gsel * ncell;
+  const double *Brg = em && em->Bref ? em->Bref + (int64_t)gsel * ncell : Bg;
+  // error model: magnitudes of the angular factors of the six outputs, and (path 0) the roundings of the
+  // factors omega (A/V) Omega.. that multiply each segment average on its way into the sums
+  const double mud = (double)mu, oxd = std::fabs((double)Ox), oyd = std::fabs((double)Oy);
+  const double fk[6] = {1.0, oxd, oyd, oxd * oxd, oxd * oyd, oyd * oyd};
+  const double kterm = em && em->path == 0 ? 16.0 + 2.0 * mud * mud / (1.0 - mud * mud) : 0.0;
   int64_t seg = seg0;
   for (size_t k = 0; k < d.rays.size(); ++k) {
     const Ray<R> &r = d.rays[k];
     R I = bnd[r.entry * G + gsel];                 // I_{k,1}: isotropic incoming boundary intensity
+    double eps_out = 0.0, b_prev = (double)I;      // error model: bound of the outgoing deviation; B before
     for (size_t s = 0; s < r.cell.size(); ++s, ++seg) {
       const int i = r.cell[s];
       const R kap_i = kap[i];
@@ -358,6 +429,41 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
       const R Iout = I * e + (Q / kt) * one_m_e;                    // Eq. (12)
       const R alpha = R(1) / tau - e / one_m_e;                     // Eq. (13)
       const R Ibar = alpha * I + (R(1) - alpha) * Iout;             // Eq. (12)
+      if (em) {
+        // running error bound of the path's deviation-form evaluation of this segment (see segment_bound);
+        // all quantities are magnitudes of the exact values, formed from this oracle's own
+        const double u = em->u, Bc = (double)B_i, Br = Brg[i];
+        const double jump = std::fabs(b_prev - Bc);
+        const double psi_in = (double)(I - B_i);
+        // the step of B the path adds at the crossing (FP32: B in two words, 2^-48 of each B)
+        const double ej = (em->path == 1 ? 2 * u * jump + 4 * u * u * (std::fabs(b_prev) + Bc) : u * jump) +
+                          4 * em->abs_unit;
+        const double eps_in = s == 0 ? ej : eps_out + ej + u * std::fabs(psi_in);
+        const double rr = (double)(inv_cdt / kt);                   // 1 / (c dt kappa~)
+        const double dstate = (double)Iprev - Br;                   // the path's stored deviation
+        const double eps_state = Ierr_prev ? Ierr_prev[seg * Gsub + gi] : 0.0;
+        const double dd = (double)(Q / kt - B_i);
+        const double eps_d = (em->path == 1
+            ? u * (3 * std::fabs(dstate * rr) + 5 * std::fabs((Br - Bc) * rr) + std::fabs(dd)) + rr * eps_state
+            : u * rr * (std::fabs(Br - Bc) + 8 * std::fabs((double)Iprev - Bc)) + rr * eps_state) +
+                             4 * em->abs_unit;
+        const double taud = (double)tau, ed = (double)e, omd = (double)one_m_e;
+        const double pbar = (double)(Ibar - B_i);
+        const SegBound sb = segment_bound(*em, taud, ed, omd, omd / taud, std::fabs((double)(I - Q / kt)),
+                                          std::fabs(pbar), std::fabs((double)(Iout - B_i)), eps_in, eps_d, mud);
+        eps_out = sb.out;
+        b_prev = Bc;
+        const double wA = (double)(om * r.area[s]);
+        double *ea = eacc->data();
+        for (int q = 0; q < 6; ++q) {
+          ea[(ERR0 + q) * ncell + i] += wA * fk[q] * (sb.bar + kterm * u * std::fabs(pbar));
+          ea[(DEV0 + q) * ncell + i] += wA * fk[q] * std::fabs(pbar);
+          ea[(PLK0 + q) * ncell + i] += wA * fk[q] * Bc;
+        }
+        ea[ECNT * ncell + i] += 1.0;
+        // the bound of the path's stored deviation, plus this oracle's rounding of its own to double
+        if (Ierr_new) Ierr_new[seg * Gsub + gi] = sb.bar + 0x1p-53 * std::fabs(pbar);
+      }
       if (facc) {   // Eq. (16): omega_m w_k times the intensity at the segment's upwind face
         const int64_t nf = (int64_t)(g.nx + 1) * g.ny + (int64_t)g.nx * (g.ny + 1);
         const int f = r.face[s];
@@ -396,7 +502,8 @@ static void sweep_direction(const oracle_geom &g, const Geometry<R> &geo, int m,
 template <class R>
 static int run_sweep(const oracle_geom *g, int G, const double *kappa, const double *B, double c, double dt,
                      const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                     double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out) {
+                     double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out,
+                     const oracle_errmodel *em, const double *Ierr_prev, double *Ierr_new, double *err_out) {
   if (check_geom(g)) return -1;
   if (G < 1 || !kappa || !B || !bnd || !(c > 0) || !(dt > 0) || !out) return -1;
   Geometry<R> geo;
@@ -422,16 +529,19 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
   const int nblk = std::min(g->ndir, 16);
   if (nthreads < 1) nthreads = 1;
   std::vector<std::vector<R>> acc(nblk), facc(face_out ? nblk : 0);
+  std::vector<std::vector<double>> eacc(em ? nblk : 0);
   const int64_t nf = (int64_t)(g->nx + 1) * g->ny + (int64_t)g->nx * (g->ny + 1);
   for (int gi = 0; gi < Gsub; ++gi) {
     for (auto &a : acc) a.assign((size_t)N_MOM * ncell, R(0));
     for (auto &a : facc) a.assign((size_t)6 * nf, R(0));
+    for (auto &a : eacc) a.assign((size_t)N_ERR * ncell, 0.0);
     auto work = [&](int tid) {
       for (int b = tid; b < nblk; b += nthreads) {
         int m0 = (int)((int64_t)g->ndir * b / nblk), m1 = (int)((int64_t)g->ndir * (b + 1) / nblk);
         for (int m = m0; m < m1; ++m)
           sweep_direction<R>(*g, geo, m, gi, G, gl[gi], kappa, B, inv_cdt, bnd, I_prev, seg_off[m], I_new,
-                             I_exit, ray_off[m], Gsub, store_dev, prev_dev, &acc[b], face_out ? &facc[b] : nullptr);
+                             I_exit, ray_off[m], Gsub, store_dev, prev_dev, &acc[b], face_out ? &facc[b] : nullptr,
+                             em, Ierr_prev, Ierr_new, em ? &eacc[b] : nullptr);
       }
     };
     int nt = std::min(nthreads, nblk);
@@ -447,6 +557,30 @@ static int run_sweep(const oracle_geom *g, int G, const double *kappa, const dou
       double *o = out + ((int64_t)q * Gsub + gi) * ncell;
       const R scale = q == MOM_D ? R(1) / (R(c) * V) : R(1) / V;
       for (int64_t i = 0; i < ncell; ++i) o[i] = (double)(tot[(size_t)q * ncell + i] * scale);
+    }
+    if (em) {
+      // bounds of the six outputs (E, Fx, Fy, Nxx, Nxy, Nyy, in the units of `out`): the propagated segment-average
+      // bounds, the summation (path 1: k_sum roundings per term; path 0: recursive summation of the cell's n terms
+      // in any order, gamma_{n-1}), and the cell assembly in FP64 (the Planck part B times per-cell geometric
+      // moments formed in double-double, plus the deviation sum: 8 units of 2^-53 of both magnitudes)
+      std::vector<double> et((size_t)N_ERR * ncell, 0.0);
+      for (int b = 0; b < nblk; ++b)
+        for (size_t q = 0; q < et.size(); ++q) et[q] += eacc[b][q];
+      const double u64 = 0x1p-53;
+      for (int q = 0; q < 6; ++q) {
+        const double scale = q == 0 ? 1.0 / (c * (double)V) : 1.0 / (double)V;
+        double *ob = err_out + ((int64_t)q * Gsub + gi) * ncell;
+        double *od = err_out + ((int64_t)(6 + q) * Gsub + gi) * ncell;
+        double *op = err_out + ((int64_t)(12 + q) * Gsub + gi) * ncell;
+        for (int64_t i = 0; i < ncell; ++i) {
+          const double E = et[(size_t)(ERR0 + q) * ncell + i], D = et[(size_t)(DEV0 + q) * ncell + i],
+                       P = et[(size_t)(PLK0 + q) * ncell + i], n = et[(size_t)ECNT * ncell + i];
+          const double ksum = em->path == 1 ? em->k_sum : std::max(n - 1.0, 0.0);
+          ob[i] = (E + ksum * em->u * D + 8 * u64 * (D + P)) * scale;
+          od[i] = D * scale;
+          op[i] = P * scale;
+        }
+      }
     }
     if (face_out) {
       // face averages over the face length: E_f = (1/(c |f|)) sum omega w I, F_f, N_f = (1/|f|) sum ...
@@ -535,13 +669,21 @@ int oracle_tracks(const oracle_geom *g, int precision, int64_t *dir_ray_off, int
 //   face_out   [6][Gsub][nfaces] face averages E, Fx, Fy, Nxx, Nxy, Nyy of the intensity at the upwind face of
 //                                every segment, weighted by omega w (Eq. 16), or NULL; faces numbered as in
 //                                trace(): x-faces (nx+1) ny first, then y-faces nx (ny+1)
+//   em         error model of a path to bound, or NULL (then Ierr_prev, Ierr_new and err_out are unused)
+//   Ierr_prev  [nseg][Gsub]      bound of the error of that path's stored deviations entering this step, or NULL (0)
+//   Ierr_new   [nseg][Gsub]      bound of the error of the path's new deviations (plus this oracle's rounding of
+//                                its own to double), or NULL
+//   err_out    [18][Gsub][ncell] bound of the path's error in E, Fx, Fy, Nxx, Nxy, Nyy; then the magnitudes of
+//                                their deviation terms and of their Planck terms (same six, same units as out)
 int oracle_sweep(const oracle_geom *g, int precision, int G, const double *kappa, const double *B, double c,
                  double dt, const double *bnd, const double *I_prev, const int *groups, int ngroups, double *out,
-                 double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out) {
+                 double *I_new, double *I_exit, int nthreads, int store_dev, int prev_dev, double *face_out,
+                 const oracle_errmodel *em, const double *Ierr_prev, double *Ierr_new, double *err_out) {
+  if (em && (!err_out || !(em->u > 0) || (em->path != 0 && em->path != 1))) return -1;
   return precision ? run_sweep<real128>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev, prev_dev, face_out)
+                                       nthreads, store_dev, prev_dev, face_out, em, Ierr_prev, Ierr_new, err_out)
                    : run_sweep<double>(g, G, kappa, B, c, dt, bnd, I_prev, groups, ngroups, out, I_new, I_exit,
-                                       nthreads, store_dev, prev_dev, face_out);
+                                       nthreads, store_dev, prev_dev, face_out, em, Ierr_prev, Ierr_new, err_out);
 }
 
 // Bits of the oracle's real type (bookkeeping, no counterpart in the paper).

@@ -1183,6 +1183,12 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
     e = cudaMemsetAsync(p->d_facc, 0, p->facc_elems * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear face accumulators");
   }
+  if (p->d_balance) {
+    // the balance floor (word 1) follows this call's B and boundary; the residual record (word 0) is kept
+    e = cudaMemsetAsync(p->d_balance + 1, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = launch_balance_scale(p->view, B, bnd, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: balance check set-up");
+  }
   if (prec == MOLC_FP64) {
     e = cudaMemsetAsync(a.acc, 0, rows * kOutputs * sizeof(double), st);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear accumulators");
@@ -1564,6 +1570,12 @@ molc_status molc_kernel_time(molc_plan *p, double *total_ms, int *launches) {
   molc_status s = molc_kernel_time_parts(p, parts, launches);
   if (s == MOLC_OK) *total_ms = parts[1];
   return s;
+}
+
+molc_status molc_fp64_fma_rate(double *flops_per_s) {
+  if (!flops_per_s) return fail(MOLC_ERR_INVALID_ARG, "fp64_fma_rate: NULL argument");
+  cudaError_t e = fp64_fma_rate(flops_per_s);
+  return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "fp64_fma_rate");
 }
 
 molc_status molc_device_status(molc_plan *p, int *code) {

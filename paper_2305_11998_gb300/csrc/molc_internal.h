@@ -192,6 +192,9 @@ cudaError_t launch_moments_fp32_batch(const BatchInst *inst, const int4 *map, in
 // combine step of split cells: map int4 {instance, chunk, block, 0} over the instance's split cells
 cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
 
+// FP64 FMA rate of the current device in FLOP/s (2 per FMA), timed with CUDA events; synchronises.
+cudaError_t fp64_fma_rate(double *flops_per_s);
+
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 // Device address of that array on the current device.  The first call per device looks the symbol up (which

@@ -1335,6 +1335,53 @@ cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const doubl
 }
 
 // ---------------------------------------------------------------------------------------------------------
+// FP64 FMA throughput of this GPU (the bound of the plain FP64 sweep, which spends its time in FP64 exp/expm1
+// and FP64 atomics): every thread runs kFmaChains independent chains of kFmaIters dependent FMAs, so the FP64
+// pipe, not latency, limits the rate.  The result is written so that the work cannot be dropped.
+// ---------------------------------------------------------------------------------------------------------
+constexpr int kFmaChains = 8, kFmaIters = 4096;
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double *sink, double a, double b) {
+  double x[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < kFmaIters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += x[k];
+  if (s == 12345.678) sink[0] = s;   // never true for the arguments used; keeps the chains live
+}
+
+cudaError_t fp64_fma_rate(double *flops_per_s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256;
+  float best = 0.f;
+  for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {   // first run warms up; best of the other three
+    cudaEventRecord(e0, 0);
+    fp64_fma_kernel<<<blocks, threads>>>(nullptr, 0.999999, 1e-7);
+    cudaEventRecord(e1, 0);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  *flops_per_s = 2.0 * (double)blocks * threads * kFmaChains * kFmaIters / (best * 1e-3);
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------------------------------------
 // Static scratch of molc_sweep_static_scratch: the per-sweep workspace (moment accumulators, FP32 cell table)
 // in an array fixed at build time, reserved when the module is loaded on a device, so that entry point
 // allocates nothing.  The host name g_static_scratch is not a device address: its address on a device comes

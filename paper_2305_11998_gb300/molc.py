@@ -34,7 +34,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
             "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure",
-            "molc_ray_balance")
+            "molc_ray_balance", "molc_fp64_fma_rate")
 
 
 class MolcError(RuntimeError):
@@ -112,6 +112,7 @@ def load(build_if_needed: bool = True):
         "molc_kernel_time": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_kernel_time_parts": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_device_status": (C.c_int, [vp, ip]),
+        "molc_fp64_fma_rate": (C.c_int, [dp]),
         "molc_last_error": (C.c_char_p, []),
         "molc_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
         "molc_batch_bind": (C.c_int, [vp, C.POINTER(_SweepArgs)]),
@@ -154,6 +155,13 @@ def _ptr(t):
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+def fp64_fma_rate() -> float:
+    """molc_fp64_fma_rate: FP64 FMA throughput of the current device in FLOP/s (synchronises)."""
+    r = C.c_double()
+    _check(load().molc_fp64_fma_rate(C.byref(r)))
+    return r.value
 
 
 def quadrature_product(n_polar: int, n_azim: int):

@@ -358,6 +358,29 @@ def test_grey_coefficients_special_cases():
     assert np.all(np.abs(r1["eta_y"]) <= 4e-16 * kg[0] * np.abs(Fy[0]) / E[0])
 
 
+def test_grey_eddington_average_special_cases():
+    """Eq. 8 with u = f: factors equal in every group average to that factor; E in one group picks that
+    group's factor; a hand-worked two-group cell; zero E gives 0."""
+    rng = np.random.default_rng(11)
+    G, n, c = 4, 6, 29.98
+    E = rng.uniform(0.1, 1.0, (G, n))
+    f0 = rng.uniform(0.1, 0.5, (3, n))
+    N = [np.tile(f0[i], (G, 1)) * c * E for i in range(3)]
+    for got, want in zip(oracle.grey_eddington(E, *N, c), f0):
+        assert np.allclose(got, want, rtol=4e-16, atol=0)
+    E1 = np.zeros((G, n))
+    E1[1] = E[1]
+    fg = rng.uniform(-0.3, 0.5, (3, G, n))
+    N1 = [fg[i] * c * E1 for i in range(3)]
+    for i, got in enumerate(oracle.grey_eddington(E1, *N1, c)):
+        assert np.allclose(got, fg[i][1], rtol=4e-16, atol=0)
+    # two groups, E = (1, 3), f_xx = (0.2, 0.4): <f_xx>_E = (0.2 + 1.2) / 4 = 0.35
+    E2 = np.array([[1.0], [3.0]])
+    fxx, _, _ = oracle.grey_eddington(E2, np.array([[0.2], [0.4]]) * c * E2, np.zeros((2, 1)), np.zeros((2, 1)), c)
+    assert abs(fxx[0] - 0.35) < 1e-15
+    assert all(np.all(x == 0) for x in oracle.grey_eddington(np.zeros((G, n)), *N, c))
+
+
 def _face_geometry(nx, ny):
     nxf = (nx + 1) * ny
 
