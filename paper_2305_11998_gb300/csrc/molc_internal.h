@@ -195,6 +195,80 @@ cudaError_t launch_moments_combine_batch(const BatchInst *inst, const int4 *map,
 // FP64 FMA rate of the current device in FLOP/s (2 per FMA), timed with CUDA events; synchronises.
 cudaError_t fp64_fma_rate(double *flops_per_s);
 
+// ---- Tiled FP32 sweep (plans without MOLC_FACES / MOLC_BALANCE, at most kMaxPolarFP32 polar cosines) ----------
+// The material grid is cut into tiles of TS x TS cells.  Every characteristic is cut into pieces, one per tile it
+// crosses; a work item is (tile, quadrant, group tile): the pieces of the directions that point into one quadrant
+// (both senses of a pair lie in opposite quadrants) crossing the tile, for GT consecutive groups.  An item takes
+// the intensity entering its pieces from the items upstream in its quadrant (the tiles before it in x and in y)
+// and passes its outgoing intensity on, so the items of one (quadrant, group tile) form a wavefront over the
+// tiles.  The item's previous-step state and cell table are staged in shared memory; its cell moments are summed
+// there, per quadrant, and the four quadrant partials of a (tile, group tile) are combined by whichever item of
+// the four finishes last.
+constexpr int kTileThreads = 256;                 // threads of a tiled-sweep block
+constexpr int kTileStateBytes = 88 * 1024;        // largest item state staged in shared memory
+constexpr int kTileUnitEntries = 64;              // moment entries one thread sums (longer cell lists are split)
+constexpr int kTileMaxUnits = 512;                // moment units of one item (shared-memory partials)
+constexpr int kTileCandidates[] = {16, 8, 4, 2, 1};   // tile sizes tried, largest first
+constexpr int kTileGroupCandidates[] = {4, 2, 1};      // groups per item tried, largest first
+constexpr int kTileWaitLimit = 1 << 22;           // iterations of a bounded wait (with back-off, ~1-2 s)
+constexpr int kStatusTimeout = 4;                 // device status: a bounded wait gave up
+
+struct TileGeom {      // one (tile, quadrant) of a plan's tiled characteristic grid
+  int tile, q;          // tile = ty * ntx + tx; q bit 0: the direction points towards -x, bit 1: towards -y
+  int n_pieces, max_len, n_slots;
+  int P_off;            // Ptab[P_off + t], t = 0..max_len: pieces still walking summed over the steps before t
+  int64_t slot_base;    // first record of the geometry (records are indexed by geometry slot P[t] + rank)
+  int64_t piece_off;    // global index of the geometry's rank-0 piece (pieces sorted longest first)
+  int64_t ent_off;      // first moment entry of the geometry
+  int unit_off, n_units;  // moment units of the geometry (cell-major)
+  int cu_off;           // cell_units[cu_off + cell_local] = {first unit (relative), units}
+  int up_x, up_y;       // upstream geometries of the same quadrant (previous tile in x, in y), or -1
+  int delta;            // wavefront step of the tile in its quadrant
+};
+
+struct TileView {      // a plan's tiled FP32 layout and workspace, by value
+  int TS, TS2p;        // tile side in cells; TS^2 rounded up to a multiple of 4 (per-group stride of tile tables)
+  int ntx, nty, n_tiles, n_geoms;
+  int GT, n_gt;        // groups per item, group tiles
+  int n_items;         // n_gt * n_geoms (item id = gt * n_geoms + geom)
+  int max_item_floats; // largest item state (floats, a multiple of 4)
+  int max_len;
+  const TileGeom *geoms;
+  const int *Ptab;
+  const int4 *pieces;  // {track, 2 len + sense, in (piece index >= 0, or -1 - entry edge), out (piece index or -1)}
+  const int2 *recs;    // {cell_local, l (f32 bits)} per geometry slot, in the traversal order of the quadrant
+  const int2 *ents;    // {geometry slot | pair << 24, A/V (f32 bits)} per (slot, cell), cell-major, by pair
+  const int4 *units;   // {cell_local, first entry (relative), end entry, 0}
+  const int2 *cell_units;
+  const int64_t *item_off;   // state offset (floats) of each item
+  // workspace (plan-owned, or carved from the static scratch)
+  float4 *cdat;        // [tile][G][TS2p] {kappa~, 1/(c dt kappa~) x rescale, B_hi, B_lo}
+  float *cdB;          // [tile][G][TS2p] (B_ref - B) / (c dt kappa~)
+  float *bbuf;         // [piece][G][NP + 2]: intensity deviations entering the piece and B (hi, lo) before it
+  double *part;        // [tile][gt][q][6][GT][TS2p]: per-quadrant moment partials
+  int *cnt;            // [tile][gt]: quadrant items finished this step
+  int *flags;          // [item]: the epoch of the last step the item finished
+  int *ctrl;           // [0] ticket of the running launch, [1] epoch of this plan's steps
+};
+
+struct TileInst {      // one instance of a tiled sweep launch (device memory)
+  PlanView v;
+  TileView t;
+  SweepArgs a;
+};
+
+// tiled sweep launchers: prep (cell tables, ticket reset, epoch), the persistent sweep over the queue
+// {instance, item} (ticket: the launch's counter, reset by the prep), intensity export/import
+cudaError_t launch_tile_prep(const TileInst *inst, const int4 *map, int blocks, int *ticket, cudaStream_t st);
+cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
+                              size_t smem, int grid, cudaStream_t st);
+size_t tile_sweep_smem(int max_item_floats, int TS2p, int GT, int max_len, int n_pairs, int np_max);
+int tile_sweep_grid(int np_max, size_t smem);
+cudaError_t launch_tile_intensity_copy(const PlanView &v, const TileView &t, const int4 *tpiece,
+                                       const int64_t *tpiece_off, float *I, const double *Bref,
+                                       const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
+                                       cudaStream_t st);
+
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
 // Device address of that array on the current device.  The first call per device looks the symbol up (which

@@ -62,9 +62,10 @@ def run_sequence(plan, wl, Ts, prec, device="cuda", on_step=None):
     return res
 
 
-def precision_errors(m32, m64, c):
-    """Errors of FP32 moments against FP64 ones: E relative (floor 1e-30 max|E|), F and N_xy relative to c E,
-    Eddington factors absolute where E is above the floor."""
+def precision_errors(m32, m64, c, tol=2e-5):
+    """Errors of FP32 moments against FP64 ones: E relative (floor 1e-30 max|E|); F and N_xy both in the stated
+    per-cell metric (relative to max(|x|, 1e-30 max|x|): the largest value and the fraction of cells within
+    `tol`) and relative to c E; Eddington factors absolute where E is above the floor."""
     E = m64["E"]
     floor = 1e-30 * np.abs(E).max()
     den = np.maximum(np.abs(E), floor)
@@ -72,6 +73,10 @@ def precision_errors(m32, m64, c):
     out = {"E": float(np.max(np.abs(m32["E"] - E) / den))}
     for k in ("Fx", "Fy", "Nxy"):
         out[k + "/cE"] = float(np.max(np.abs(m32[k] - m64[k]) / cE))
+        dk = np.maximum(np.abs(m64[k]), 1e-30 * np.abs(m64[k]).max())
+        lit = np.abs(m32[k] - m64[k]) / np.where(dk > 0, dk, 1e-300)
+        out[k] = float(np.max(lit))
+        out[k + "_literal_pass"] = float(np.mean(lit <= tol))
     ok = np.abs(E) > floor
     for k, n in (("fxx", "Nxx"), ("fxy", "Nxy"), ("fyy", "Nyy")):
         f32 = np.where(ok, m32[n] / (c * np.where(ok, m32["E"], 1.0)), 0.0)

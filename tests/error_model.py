@@ -36,8 +36,10 @@ def model(prec: str, n_polar: int, B=None, bnd=None, Bref=None) -> dict:
     if prec == "fp64":
         m = dict(FP64)
     else:
+        # the path keeps a scale while the scaled maximum stays within 2^-7 .. 2^8 of its target: the smallest
+        # scale it may sweep with is 2^-7 of fp32_scale
         m = {"path": 1, "u": 2.0 ** -24, "e_exp": FP32_E_EX2, "e_rcp": FP32_E_RCP, "k_sum": n_polar + 18.0,
-             "abs_unit": 2.0 ** -126 / fp32_scale(B, bnd)}
+             "abs_unit": 2.0 ** -126 * 2.0 ** 7 / fp32_scale(B, bnd)}
     if Bref is not None:
         m["Bref"] = Bref
     return m

@@ -70,3 +70,25 @@ def test_moment_bounds_scale_with_unit_roundoff_and_cover_magnitudes():
         ratio = v2[live] / v1[live]
         assert np.all((ratio > 1.9) & (ratio < 4.01)), (k, float(ratio.min()), float(ratio.max()))
         assert np.all(r1["bound"][k] >= em["k_sum"] * em["u"] * r1["dev"][k] * (1 - 1e-12)), k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_bound_holds_when_B_changes_between_steps(prec):
+    """Step 2 with a new B: the path's stored deviations refer to the old B (B_ref), the oracle's are re-referenced
+    to the new B in double (that rounding added to the carried bound)."""
+    wl, d, geom = _case("fc16_g4_d32", 3)
+    tr = oracle.tracks(geom)
+    cells = tr["cell"]
+    B2 = d["B"] * np.exp(np.random.default_rng(9).uniform(-0.3, 0.3, d["B"].shape))
+    em1 = error_model.model(prec, wl.n_polar, d["B"], d["bnd"])
+    r1 = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_as_deviation=True, errmodel=em1)
+    e1 = fp_emulation.emulate(tr, geom.mu, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], prec)
+    jump = (d["B"] - B2)[:, cells].T
+    dev2 = r1["I"] + jump
+    err2 = r1["I_err"] + 2 * 2.0 ** -53 * (np.abs(dev2) + np.abs(jump))
+    em2 = error_model.model(prec, wl.n_polar, B2, d["bnd"], Bref=d["B"])
+    r2 = oracle.sweep(geom, d["kappa"], B2, d["c"], d["dt"], d["bnd"], I_prev=dev2, I_as_deviation=True,
+                      I_prev_is_deviation=True, errmodel=em2, I_err=err2)
+    e2 = fp_emulation.emulate(tr, geom.mu, d["kappa"], B2, d["c"], d["dt"], d["bnd"], prec, dev_prev=e1,
+                              Bref=d["B"])
+    assert np.all(np.abs(e2 - r2["I"]) <= r2["I_err"])

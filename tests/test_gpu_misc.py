@@ -29,8 +29,8 @@ def host(d):
 
 def test_full_size_512_sampled_groups(molc):
     """The production workload (512^2, 17 groups, 128 directions, h/2, three fronts) in the launch
-    configuration the benchmark times; four groups checked against the double oracle (the floor of the
-    relative metric is taken over all groups of the GPU output)."""
+    configuration the benchmark times; the group holding the Planck peak of the hot region checked against the
+    binary128 oracle (the floor of the relative metric is taken over all groups of the GPU output)."""
     wl = synth.WORKLOADS["fc512_g17_d128"]
     d = wl.inputs(0)
     P = molc.Plan.from_workload(wl)
@@ -44,13 +44,11 @@ def test_full_size_512_sampled_groups(molc):
     del I
     torch.cuda.empty_cache()
     assert n_upd > 1.4e9
-    groups = [0, 8, 11, 16]     # 11 holds the Planck peak of the hot region
+    groups = [11]     # the Planck peak of the hot region
     geom = oracle.Geometry.from_workload(wl)
-    ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="double",
-                       want_I=False)
+    ref = parity.reference(geom, d, "fp32", wl.n_polar, groups=groups)
     fm = {k: float(np.abs(v).max()) for k, v in got.items()}
-    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"], ref_precision="double",
-                   floor_max=fm)
+    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"], floor_max=fm)
 
 
 def test_closure_and_grey_average(molc):
@@ -169,7 +167,7 @@ def test_fp32_state_scale_follows_the_intensities(molc):
     m = host(P.sweep("fp32", dev(d["kappa"]), dev(d["B"] * 2.0 ** 40), d["c"], d["dt"], I, dev(d["bnd"] * 2.0 ** 40)))
     assert P.device_status() == 0 and all(np.isfinite(v).all() for v in m.values())
     P.close()
-    # cold start under the hot left edge, against the double oracle
+    # cold start under the hot left edge, against the binary128 oracle
     wc = synth.Workload("cold16", 16, 16, 6.0, 4, 0.01, 10.0, 2, 16, 2, 1, cold_start=True)
     dc = wc.inputs(0)
     assert dc["bnd"].max() > 1e10 * dc["B"].max()
@@ -180,8 +178,7 @@ def test_fp32_state_scale_follows_the_intensities(molc):
     got = host(Pc.sweep("fp32", dev(dc["kappa"]), Bc, dc["c"], dc["dt"], Ic, dev(dc["bnd"])))
     assert Pc.device_status() == 0
     Pc.close()
-    ref = oracle.sweep(oracle.Geometry.from_workload(wc), dc["kappa"], dc["B"], dc["c"], dc["dt"], dc["bnd"],
-                       precision="quad", want_I=False)
+    ref = parity.reference(oracle.Geometry.from_workload(wc), dc, "fp32", wc.n_polar)
     parity.compare(got, ref, "fp32", dc["c"])
 
 

@@ -32,18 +32,12 @@ def test_paper_layout_production_spacing(prec):
     got = {k: v.cpu().numpy() for k, v in P.sweep(prec, dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"])).items()}
     assert P.device_status() == 0
     P.close()
-    # The FP64 path is held against the binary128 oracle: with ~1.6e5 segment terms per cell, the double
-    # oracle's own summation error on the cancelling F exceeds the 64 u c E its reference allowance assumes.
-    # The FP32 path's tolerance is far above either oracle's error.  For the same reason the gate of the signed
-    # moments takes C = the largest number of terms the FP64 path adds into one cell (one per segment and
-    # direction): its worst-case summation bound.
-    groups = [0, 11] if prec == "fp64" else [0, 8, 11, 16]
-    precision = "quad" if prec == "fp64" else "double"
+    # Both paths against the binary128 oracle on two sampled groups: with ~1.6e5 segment terms per cell, the FP64
+    # path's own summation bound (gamma_{n-1} of the cell's n terms) is part of the oracle's derived bound.
+    groups = [0, 11]
     geom = oracle.Geometry(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, h_moc, 1, 0)
     n_terms = int(np.bincount(oracle.tracks(geom, "double")["cell"], minlength=wl.ncell).max())
     assert n_terms > 5000
-    ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision=precision,
-                       want_I=False)
+    ref = parity.reference(geom, d, prec, wl.n_polar, groups=groups)
     fm = {k: float(np.abs(v).max()) for k, v in got.items()}
-    parity.compare({k: v[groups] for k, v in got.items()}, ref, prec, d["c"], ref_precision=precision,
-                   floor_max=fm, eta_c=n_terms if prec == "fp64" else None)
+    parity.compare({k: v[groups] for k, v in got.items()}, ref, prec, d["c"], floor_max=fm)

@@ -1,8 +1,9 @@
-"""GPU parity: the CUDA sweeps (through the C ABI) against the oracle on the same seeded inputs.
+"""GPU parity: the CUDA sweeps (through the C ABI) against the binary128 oracle on the same seeded inputs.
 
-FP64 path: relative 1e-12 against the binary128 oracle.  FP32 path: relative 2e-5 on E and F, 1e-6 absolute on
-the Eddington factors, against the binary128 oracle (small cases) or the double oracle (larger cases, whose own
-error is far below those bounds).  Signed moments use the conditioned denominator described in parity.py.
+FP64 path: relative 1e-12.  FP32 path: relative 2e-5 on E and F, 1e-6 absolute on the Eddington factors.  The
+signed moments are held to the literal metric where the path's arithmetic resolves them and to the oracle's
+derived bound of that arithmetic elsewhere (tests/parity.py); the carried state per segment to that bound too.
+Large cases are compared on sampled groups (the groups of a sweep are independent).
 """
 import math
 
@@ -47,20 +48,19 @@ def run_gpu(molc, wl, d, prec, steps=1, quad=None, layout="uniform", renorm=True
     return outs, Is
 
 
-def run_oracle(wl, d, precision, steps=1, quad=None, layout=0, renorm=1, spacing=None, want_I=False):
-    """The oracle over `steps` steps; between steps it carries its state as deviations from B (fixed B here),
-    so the carried state keeps the oracle's precision.  Returns the moments and the segment averages."""
+def run_oracle(wl, d, prec, steps=1, quad=None, layout=0, renorm=1, spacing=None, want_I=False, groups=None):
+    """The binary128 oracle with the error model of path `prec` over `steps` steps; between steps it carries
+    its state as deviations from B (fixed B here) and the bound of the path's state.  Returns the results
+    (moments, bounds, state) per step."""
     geom = oracle.Geometry.from_workload(wl, quad=quad, layout=layout, renorm=renorm, spacing=spacing)
-    outs, Is = [], []
-    dev = None
-    cells = oracle.tracks(geom, "double")["cell"] if (steps > 1 or want_I) else None
+    outs = []
+    dev = err = None
     for _ in range(steps):
-        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=dev, precision=precision,
-                         want_I=(steps > 1 or want_I), I_as_deviation=True, I_prev_is_deviation=True)
-        dev = r.get("I")
+        r = parity.reference(geom, d, prec, wl.n_polar, groups=groups, I_prev=dev, I_err=err,
+                             want_I=(steps > 1 or want_I))
+        dev, err = r.get("I"), r.get("I_err")
         outs.append(r)
-        Is.append(None if dev is None else dev + d["B"][:, cells].T)
-    return outs, Is
+    return outs
 
 
 C0 = synth.WORKLOADS["fc16_g4_d32"]
@@ -71,32 +71,35 @@ C0 = synth.WORKLOADS["fc16_g4_d32"]
 def test_small_one_step_vs_binary128(molc, prec, seed):
     d = C0.inputs(seed)
     got, gI = run_gpu(molc, C0, d, prec, export=True)
-    ref, rI = run_oracle(C0, d, "quad", want_I=True)
+    ref = run_oracle(C0, d, prec, want_I=True)
     parity.compare(got[0], ref[0], prec, d["c"])
-    # carried state, per segment, against its deviation from B (FP32: the tau u error accumulated along beams)
-    tol_I = 1e-12 if prec == "fp64" else 2e-5
+    # carried state, per segment, direction and group, within the bound of the path's state
     Bseg = d["B"][:, oracle.tracks(oracle.Geometry.from_workload(C0), "double")["cell"]].T
-    scale = np.maximum(np.abs(rI[0] - Bseg), 1e-30 * np.abs(rI[0]).max())
-    scale = np.maximum(scale, np.abs(rI[0]) * (1e-3 if prec == "fp64" else 1.0))
-    assert np.max(np.abs(gI[0] - rI[0]) / scale) < tol_I
+    parity.check_state(gI[0], ref[0]["I"], Bseg, ref[0]["I_err"], prec)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_small_multistep_vs_binary128(molc, prec):
     d = C0.inputs(7)
-    got, _ = run_gpu(molc, C0, d, prec, steps=4)
-    ref, _ = run_oracle(C0, d, "quad", steps=4)
-    for g_, r_ in zip(got, ref):
+    got, gI = run_gpu(molc, C0, d, prec, steps=4, export=True)
+    ref = run_oracle(C0, d, prec, steps=4)
+    Bseg = d["B"][:, oracle.tracks(oracle.Geometry.from_workload(C0), "double")["cell"]].T
+    for g_, gi_, r_ in zip(got, gI, ref):
         parity.compare(g_, r_, prec, d["c"])
+        parity.check_state(gi_, r_["I"], Bseg, r_["I_err"], prec)
 
 
-def test_fp32_ten_steps_64x64(molc):
+def test_fp32_ten_steps_64x64_sampled_groups(molc):
+    """configs[1]-shaped: 64^2 cells, 17 groups, 4 x 32 directions, h/4, ten steps with the state carried; the
+    GPU sweeps all groups, three are followed by the binary128 oracle with the carried state bound."""
     wl = synth.WORKLOADS["fc64_g17_d128"]
     d = wl.inputs(0)
     got, _ = run_gpu(molc, wl, d, "fp32", steps=wl.steps)
-    ref, _ = run_oracle(wl, d, "double", steps=wl.steps)
+    groups = [0, 8, 16]
+    ref = run_oracle(wl, d, "fp32", steps=wl.steps, groups=groups)
     for g_, r_ in zip(got, ref):
-        parity.compare(g_, r_, "fp32", d["c"], ref_precision="double")
+        fm = {k: float(np.abs(v).max()) for k, v in g_.items()}
+        parity.compare({k: v[groups] for k, v in g_.items()}, r_, "fp32", d["c"], floor_max=fm)
 
 
 def test_fp64_64x64_sampled_groups_vs_binary128(molc):
@@ -104,11 +107,9 @@ def test_fp64_64x64_sampled_groups_vs_binary128(molc):
     d = wl.inputs(1)
     got, _ = run_gpu(molc, wl, d, "fp64")
     groups = [0, 8, 11, 16]
-    geom = oracle.Geometry.from_workload(wl)
-    ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="quad",
-                       want_I=False)
+    ref = run_oracle(wl, d, "fp64", groups=groups)
     fm = {k: float(np.abs(v).max()) for k, v in got[0].items()}
-    parity.compare({k: v[groups] for k, v in got[0].items()}, ref, "fp64", d["c"], floor_max=fm)
+    parity.compare({k: v[groups] for k, v in got[0].items()}, ref[0], "fp64", d["c"], floor_max=fm)
 
 
 # Varied shapes: rectangular cells, G = 1, odd polar counts (every FP32 template), the paper's layout,
@@ -164,11 +165,10 @@ def test_variants_vs_binary128(molc, prec, vi):
     P.close()
     geom = oracle.Geometry(v["nx"], v["ny"], wl.L, Ly, q.mu, q.cos_phi, q.sin_phi, q.w, sp,
                            0 if layout == "uniform" else 1, int(renorm))
-    Iq = None
+    Iq = Ie = None
     for step in range(2):
-        r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=Iq, precision="quad",
-                         I_as_deviation=True, I_prev_is_deviation=True)
-        Iq = r["I"]
+        r = parity.reference(geom, d, prec, v["npol"], I_prev=Iq, I_err=Ie, want_I=True)
+        Iq, Ie = r["I"], r["I_err"]
         parity.compare(res[step], r, prec, d["c"])
 
 
