@@ -112,6 +112,11 @@ typedef struct {
   int n_faces;              /* MOLC_FACES: (nx + 1) ny x-faces then nx (ny + 1) y-faces; else 0 */
   int n_split_cells;        /* FP32 moments: cells crossed by more than 256 segment entries, summed in parts and
                                combined by one more kernel launch per sweep (0: no such launch) */
+  int fp32_tile_cells;      /* tiled FP32 sweep (plans without MOLC_FACES / MOLC_BALANCE): tile side in cells, or 0
+                               when the plan sweeps FP32 without tiles */
+  int fp32_tile_groups;     /* tiled FP32 sweep: groups per work item */
+  int fp32_tile_items;      /* tiled FP32 sweep: work items per step (tiles x 4 quadrants x group tiles) */
+  int fp32_sweep_blocks;    /* tiled FP32 sweep: blocks of its persistent launch */
 } molc_plan_info;
 
 /* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,

@@ -11,10 +11,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmolc.so")
-SOURCES = ["molc_host.cpp", "molc_kernels.cu"]
+SOURCES = ["molc_host.cpp", "molc_tiles.cpp", "molc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the host planner defines the characteristic grid by plain double evaluation: no FMA contraction there
-PER_FILE = {"molc_host.cpp": ["-Xcompiler", "-ffp-contract=off"]}
+PER_FILE = {"molc_host.cpp": ["-Xcompiler", "-ffp-contract=off"], "molc_tiles.cpp": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def nvcc() -> str:

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "molc_internal.h"
+#include "molc_tiles.h"
 
 using namespace molc;
 
@@ -113,6 +114,21 @@ struct molc_plan {
   size_t acc_elems = 0;
   size_t device_bytes = 0;
   PlanView view{};
+  // tiled FP32 sweep (plans without MOLC_FACES / MOLC_BALANCE): tables, plan-owned workspace, launch shape
+  bool tiled = false;
+  TileView tv{};
+  TileShape tshape{};
+  int np_class = 0;          // polar count the sweep kernel is compiled for (1, 2, 4, 8)
+  int tgrid = 0;             // blocks of the persistent sweep launch
+  int64_t tstate_floats = 0;
+  int64_t tn_pieces = 0;
+  int n_tprep = 0;
+  TileInst *d_tinst = nullptr;   // the instance of this plan's own launches (written by the prep launch)
+  int2 *d_tqueue = nullptr;
+  int4 *d_tprep = nullptr;
+  int4 *d_tpiece = nullptr;
+  int64_t *d_tpiece_off = nullptr;
+  std::vector<void *> tdev;  // every tiled allocation (freed with the plan)
   // benchmark timing of the sweep kernel
   bool timing = false;
   std::vector<cudaEvent_t> ev;   // pairs
@@ -320,9 +336,47 @@ void free_device(molc_plan *p) {
                   p->d_munit, p->d_mmulti, p->d_mscratch, p->d_balance};
   for (void *q : ptrs)
     if (q) cudaFree(q);
+  for (void *q : p->tdev)
+    if (q) cudaFree(q);
+  p->tdev.clear();
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0; }
+
+// Workspace of a tiled sweep, in the order it is carved: control words, item flags, quadrant arrival counts,
+// cell tables, quadrant moment partials, boundary buffer.  Each part is rounded up to 256 bytes.
+struct TileWorkspace {
+  size_t ctrl, flags, cnt, cdat, cdB, part, bbuf, total;
+};
+TileWorkspace tile_workspace(const TileView &t, int G, int np, int64_t n_pieces) {
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  TileWorkspace w;
+  w.ctrl = 256;
+  w.flags = up((size_t)t.n_items * sizeof(int));
+  w.cnt = up((size_t)t.n_tiles * t.n_gt * sizeof(int));
+  w.cdat = up((size_t)t.n_tiles * G * t.TS2p * sizeof(float4));
+  w.cdB = up((size_t)t.n_tiles * G * t.TS2p * sizeof(float));
+  w.part = up((size_t)t.n_tiles * t.n_gt * 4 * kOutputs * t.GT * t.TS2p * sizeof(double));
+  w.bbuf = up((size_t)n_pieces * G * (np + 2) * sizeof(float));
+  w.total = w.ctrl + w.flags + w.cnt + w.cdat + w.cdB + w.part + w.bbuf;
+  return w;
+}
+// Point a view's workspace into `base` (at least tile_workspace().total bytes, 256-byte aligned).
+void tile_carve(TileView &t, char *base, const TileWorkspace &w) {
+  t.ctrl = (int *)base;
+  base += w.ctrl;
+  t.flags = (int *)base;
+  base += w.flags;
+  t.cnt = (int *)base;
+  base += w.cnt;
+  t.cdat = (float4 *)base;
+  base += w.cdat;
+  t.cdB = (float *)base;
+  base += w.cdB;
+  t.part = (double *)base;
+  base += w.part;
+  t.bbuf = (float *)base;
+}
 
 size_t state_bytes_fp32(const molc_plan *p);
 double *bref_ptr(const molc_plan *p, molc_precision prec, void *I);
@@ -393,6 +447,120 @@ molc_status autotune(molc_plan *p) {
   int code = 0;
   cudaMemcpy(&code, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemset(p->d_status, 0, sizeof(int));   // the temporaries' checks leave no trace
+  return MOLC_OK;
+}
+
+// Tiled FP32 sweep of a plan: cut its characteristic grid into per-tile pieces (tile size and groups per item
+// chosen by plan_tiles, or pinned by force_ts / force_gt), upload the tables, allocate the workspace (zeroed) and
+// fix the launch shape.  Replaces an earlier tiled build of the plan.
+molc_status build_tiled(molc_plan *p, int force_ts, int force_gt, bool *fits = nullptr) {
+  const int64_t T = (int64_t)p->tracks.size();
+  std::vector<TileTrack> tt((size_t)T);
+  for (int j = 0; j < p->n_pairs; ++j)
+    for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) {
+      const HostTrack &h = p->tracks[k];
+      tt[k] = TileTrack{h.seg_off, h.nseg, j, h.entry_plus, h.entry_minus};
+    }
+  std::vector<double> pc(p->n_pairs), ps(p->n_pairs);
+  for (int j = 0; j < p->n_pairs; ++j) {
+    pc[j] = p->pairs[j].c;
+    ps[j] = p->pairs[j].s;
+  }
+  TilePlanInput in{p->grid.nx, p->grid.ny, p->G, p->n_pairs, p->n_polar, pc.data(), ps.data(), &tt,
+                   p->seg_cell.data(), p->seg_len.data(), p->seg_afrac.data()};
+  TileTables tb;
+  std::string why;
+  if (!plan_tiles(in, tb, why, force_ts, force_gt)) {
+    if (fits) *fits = false;
+    return fail(MOLC_ERR_INVALID_ARG, "create: tiled FP32 sweep: %s", why.c_str());
+  }
+  if (fits) *fits = true;
+  for (void *q : p->tdev)
+    if (q) cudaFree(q);
+  p->tdev.clear();
+  p->d_tinst = nullptr;
+  p->d_tqueue = nullptr;
+  p->d_tprep = nullptr;
+  p->d_tpiece = nullptr;
+  p->d_tpiece_off = nullptr;
+  TileView t{};
+  t.TS = tb.TS;
+  t.TS2p = tb.TS2p;
+  t.ntx = tb.ntx;
+  t.nty = tb.nty;
+  t.n_tiles = tb.n_tiles;
+  t.n_geoms = tb.n_geoms;
+  t.GT = tb.GT;
+  t.n_gt = tb.n_gt;
+  t.n_items = tb.n_items;
+  t.max_item_floats = tb.max_item_floats;
+  t.max_len = tb.max_len;
+  p->tstate_floats = tb.state_floats;
+  p->tn_pieces = tb.n_pieces;
+  if (p->host_only) {   // the layout's sizes only (plan information); nothing on the device
+    p->tv = t;
+    return MOLC_OK;
+  }
+  std::vector<int2> queue(tb.queue.size());
+  for (size_t i = 0; i < queue.size(); ++i) queue[i] = make_int2(0, tb.queue[i]);
+  std::vector<int4> prep;
+  const int tpb = std::max(1, 256 / (tb.TS * tb.TS));
+  for (int g = 0; g < p->G; ++g)
+    for (int t0 = 0; t0 < tb.n_tiles; t0 += tpb) prep.push_back(make_int4(0, t0, g, g == 0 && t0 == 0));
+  molc_status st = MOLC_OK;
+  size_t &tot = p->device_bytes;
+  auto up = [&](auto **dst, const auto &vec, const char *what) {
+    if (st == MOLC_OK) st = upload(dst, vec.data(), vec.size(), tot, what);
+    p->tdev.push_back((void *)*dst);
+  };
+  TileGeom *geoms = nullptr;
+  int *Ptab = nullptr;
+  int4 *pieces = nullptr, *units = nullptr;
+  int2 *recs = nullptr, *ents = nullptr, *cu = nullptr;
+  int64_t *item_off = nullptr;
+  up(&geoms, tb.geoms, "tile geometries");
+  up(&Ptab, tb.Ptab, "tile step offsets");
+  up(&pieces, tb.pieces, "tile pieces");
+  up(&recs, tb.recs, "tile records");
+  up(&ents, tb.ents, "tile moment entries");
+  up(&units, tb.units, "tile moment units");
+  up(&cu, tb.cell_units, "tile cell units");
+  up(&item_off, tb.item_off, "tile state offsets");
+  up(&p->d_tqueue, queue, "tile queue");
+  up(&p->d_tprep, prep, "tile prep map");
+  up(&p->d_tpiece, tb.tpiece, "tile piece list");
+  up(&p->d_tpiece_off, tb.tpiece_off, "tile piece offsets");
+  if (st != MOLC_OK) return st;
+  t.geoms = geoms;
+  t.Ptab = Ptab;
+  t.pieces = pieces;
+  t.recs = recs;
+  t.ents = ents;
+  t.units = units;
+  t.cell_units = cu;
+  t.item_off = item_off;
+  const TileWorkspace w = tile_workspace(t, p->G, p->n_polar, tb.n_pieces);
+  char *ws = nullptr;
+  cudaError_t e = cudaMalloc((void **)&ws, w.total);
+  if (e == cudaSuccess) {
+    p->tdev.push_back(ws);
+    tot += w.total;
+    e = cudaMemset(ws, 0, w.ctrl + w.flags + w.cnt);   // control words, flags and counts start at zero
+  }
+  if (e == cudaSuccess) {
+    e = cudaMalloc((void **)&p->d_tinst, sizeof(TileInst));
+    if (e == cudaSuccess) {
+      p->tdev.push_back(p->d_tinst);
+      tot += sizeof(TileInst);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "create: tiled sweep workspace");
+  tile_carve(t, ws, w);
+  p->tv = t;
+  p->n_tprep = (int)prep.size();
+  p->np_class = p->n_polar <= 1 ? 1 : p->n_polar <= 2 ? 2 : p->n_polar <= 4 ? 4 : 8;
+  p->tshape = tile_shape(tb, p->n_pairs, p->n_polar);
+  p->tgrid = tile_sweep_grid(p->np_class, tile_sweep_smem(p->tshape, p->np_class));
   return MOLC_OK;
 }
 
@@ -726,8 +894,24 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   // by up to 32 lanes, and a sweep block (128 consecutive items) holds neighbouring parallel tracks of one
   // sense, which cross neighbouring cells at the same steps.  Blocks are launched longest first (block_order)
   // for load balance.
+  // FP32 plans without the face or balance reductions use the tiled sweep when a tile of one cell or more keeps a
+  // work item within shared memory; the others the bundle sweep and the moment gather below
+  p->tiled = p->n_polar <= kMaxPolarFP32 && !(flags & (MOLC_FACES | MOLC_BALANCE));
+  if (p->tiled) {
+    bool fits = true;
+    const molc_status ts = build_tiled(p, 0, 0, &fits);
+    if (ts != MOLC_OK && fits) {
+      free_device(p);
+      delete p;
+      return ts;
+    }
+    if (!fits) {
+      p->tiled = false;
+      g_last_error.clear();
+    }
+  }
   const int gc32 = std::min(p->G, 32);
-  const int nch32 = p->n_polar <= kMaxPolarFP32 ? (p->G + gc32 - 1) / gc32 : 0;
+  const int nch32 = p->n_polar <= kMaxPolarFP32 && !p->tiled ? (p->G + gc32 - 1) / gc32 : 0;
   if (T > (int64_t)0x3fffffff) {
     delete p;
     return fail(MOLC_ERR_INVALID_ARG, "create: too many characteristics");
@@ -991,6 +1175,10 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->fp32_sweep_depth = p->view.sweep_depth;
   info->n_faces = p->view.n_faces;
   info->n_split_cells = p->n_split_cells;
+  info->fp32_tile_cells = p->tiled ? p->tv.TS : 0;
+  info->fp32_tile_groups = p->tiled ? p->tv.GT : 0;
+  info->fp32_tile_items = p->tiled ? p->tv.n_items : 0;
+  info->fp32_sweep_blocks = p->tiled ? p->tgrid : 0;
   return MOLC_OK;
 }
 
@@ -1000,7 +1188,8 @@ int64_t molc_intensity_count(const molc_plan *p) {
 
 // Elements of the stored deviations: FP64, one per (segment, direction, group); FP32, the bundle slots.
 static int64_t state_elems(const molc_plan *p, molc_precision prec) {
-  return prec == MOLC_FP64 ? molc_intensity_count(p) : p->bundle_slots * kSweepBlock * p->n_polar;
+  if (prec == MOLC_FP64) return molc_intensity_count(p);
+  return p->tiled ? p->tstate_floats : p->bundle_slots * kSweepBlock * p->n_polar;
 }
 
 size_t molc_intensity_bytes(const molc_plan *p, molc_precision prec) {
@@ -1050,6 +1239,25 @@ molc_status molc_intensity_init(molc_plan *p, molc_precision prec, void *I, cons
   if (e == cudaSuccess) e = cudaMemcpyAsync(bref_of(p, prec, I), B, nb, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = launch_set_scale(p->view, prec, B, header_of(p, prec, I), st);
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "intensity_init");
+}
+
+// One tiled FP32 step after the scale update: the prep launch (cell tables, ticket, epoch; it also stores this
+// call's instance for the sweep) and the persistent sweep.  ev: events {.., before sweep, after, after} or null.
+static cudaError_t tile_step(molc_plan *p, const SweepArgs &a, const TileView &tv, cudaStream_t st,
+                             cudaEvent_t *ev) {
+  TileInst ti;
+  ti.v = p->view;
+  ti.t = tv;
+  ti.a = a;
+  cudaError_t e = launch_tile_prep_one(ti, p->d_tinst, p->d_tprep, p->n_tprep, tv.ctrl, st);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess)
+    e = launch_tile_sweep(p->d_tinst, p->d_tqueue, tv.n_items, tv.ctrl, p->np_class, p->tshape, p->tgrid, st);
+  if (e == cudaSuccess && ev) {
+    e = cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+  }
+  return e;
 }
 
 // molc_sweep, and with factor outputs molc_sweep_closure (`who` names the entry point in error messages).
@@ -1103,6 +1311,13 @@ static molc_status sweep_step(molc_plan *p, molc_precision prec, const double *k
   }
   const bool timed = p->timing && p->n_timed < kMaxTimed;
   cudaEvent_t *ev = timed ? &p->ev[4 * (size_t)p->n_timed] : nullptr;
+  if (prec == MOLC_FP32 && p->tiled) {
+    if (timed) cudaEventRecord(ev[0], st);
+    e = tile_step(p, a, p->tv, st, timed ? ev : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, who, "tiled sweep");
+    if (timed) ++p->n_timed;
+    return MOLC_OK;
+  }
   if (timed) cudaEventRecord(ev[0], st);
   e = launch_prep(p->view, prec, a, st);
   if (e != cudaSuccess) return cuda_fail(e, who, "prep");
@@ -1142,6 +1357,39 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
     return fail(MOLC_ERR_INVALID_ARG, "sweep_static_scratch: need c > 0 and dt > 0");
   molc_status s = check_prec(p, prec, "sweep_static_scratch");
   if (s) return s;
+  if (prec == MOLC_FP32 && p->tiled) {
+    // workspace carved from the static array: control words, item flags, quadrant counts (left at zero by every
+    // completed call; the array starts at zero), cell tables (rewritten by every call), quadrant partials and the
+    // boundary buffer (written before they are read within the call)
+    TileView tv = p->tv;
+    const TileWorkspace w = tile_workspace(tv, p->G, p->n_polar, p->tn_pieces);
+    if (w.total > kStaticScratchBytes)
+      return fail(MOLC_ERR_INVALID_ARG,
+                  "sweep_static_scratch: this plan needs %zu bytes of workspace (%d cells x %d groups), more than "
+                  "the %zu-byte static scratch; use molc_sweep",
+                  w.total, p->view.ncell, p->G, kStaticScratchBytes);
+    DeviceGuard dg(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void *base = nullptr;
+    cudaError_t e = static_scratch_address(&base);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: scratch address");
+    tile_carve(tv, (char *)base, w);
+    SweepArgs a{};
+    a.kappa = kappa;
+    a.B = B;
+    a.bnd = bnd;
+    a.c = c;
+    a.dt = dt;
+    a.inv_c = 1.0 / c;
+    a.inv_cdt = 1.0 / (c * dt);
+    a.I = I;
+    a.Bref = bref_of(p, prec, I);
+    a.scale = header_of(p, prec, I);
+    a.out = *out;
+    e = launch_update_scale(p->view, B, bnd, header_of(p, prec, I), st);
+    if (e == cudaSuccess) e = tile_step(p, a, tv, st, nullptr);
+    return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "sweep_static_scratch: tiled sweep");
+  }
   // workspace carved from the static array: FP64, the accumulators [cell][6][G] (must start at zero, cleared
   // below on every call); FP32, the cell tables [chunk][cell][gc] (fully written by prep_kernel)
   const Layout L = layout_for(p->view, prec);
@@ -1230,11 +1478,24 @@ struct molc_batch {
   int4 *d_combine = nullptr;
   int n_combine = 0;
   bool bound = false;
+  // tiled plans: one prep and one persistent sweep launch over the items of every instance
+  bool tiled = false;
+  molc::TileInst *d_tinst = nullptr;
+  std::vector<molc::TileInst> h_tinst;
+  int2 *d_tqueue = nullptr;
+  int n_tqueue = 0;
+  int4 *d_tprep = nullptr;
+  int n_tprep = 0;
+  int *d_ticket = nullptr;
+  molc::TileShape shape{};
+  int np_max = 0, grid = 0;
 };
 
 namespace {
 void batch_free(molc_batch *b) {
   DeviceGuard dg(b->device);
+  for (void *q : {(void *)b->d_tinst, (void *)b->d_tqueue, (void *)b->d_tprep, (void *)b->d_ticket})
+    if (q) cudaFree(q);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_prep) cudaFree(b->d_prep);
   if (b->d_combine) cudaFree(b->d_combine);
@@ -1265,7 +1526,7 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
   for (int i = 0; i < n; ++i) {
     if (!plans[i]) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is NULL", i);
     if (plans[i]->host_only) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is MOLC_HOST_ONLY", i);
-    if (plans[i]->n_polar > kMaxPolarFP32 || plans[i]->n_items32 == 0)
+    if (plans[i]->n_polar > kMaxPolarFP32 || (plans[i]->n_items32 == 0 && !plans[i]->tiled))
       return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d has no FP32 sweep (more than %d polar cosines)", i,
                   kMaxPolarFP32);
     if (plans[i]->device != dev) return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d is on another device", i);
@@ -1276,9 +1537,72 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
       return fail(MOLC_ERR_INVALID_ARG, "batch_create: plan %d was created with MOLC_FACES (face moments come from "
                                         "molc_sweep only)", i);
   }
+  int n_tiled = 0;
+  for (int i = 0; i < n; ++i) n_tiled += plans[i]->tiled ? 1 : 0;
+  if (n_tiled != 0 && n_tiled != n)
+    return fail(MOLC_ERR_INVALID_ARG, "batch_create: plans with and without the tiled FP32 sweep cannot be batched "
+                                      "together (%d of %d are tiled)", n_tiled, n);
   auto b = new molc_batch();
   b->device = dev;
   b->plans.assign(plans, plans + n);
+  if (n_tiled) {
+    // items of all instances, those with the longest remaining wavefront first (an item's upstream items have a
+    // longer one, so they come earlier); prep blocks of all instances
+    b->tiled = true;
+    b->h_tinst.resize(n);
+    std::vector<std::pair<std::pair<int, int>, int2>> items;   // ((-remaining, instance), {instance, item})
+    std::vector<int4> prep;
+    TileShape sh{0, 0, 0, 0, 0, plans[0]->n_polar};
+    for (int i = 0; i < n; ++i) {
+      const molc_plan *p = plans[i];
+      const TileView &t = p->tv;
+      std::vector<int2> q(t.n_items);
+      std::vector<TileGeom> geoms(t.n_geoms);
+      cudaError_t e = cudaMemcpy(q.data(), p->d_tqueue, q.size() * sizeof(int2), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(geoms.data(), t.geoms, geoms.size() * sizeof(TileGeom), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch_create: reading the tiled queue");
+      }
+      const int D = t.ntx + t.nty - 1;
+      for (const int2 &x : q) {
+        const TileGeom &gm = geoms[x.y % t.n_geoms];
+        items.push_back({{-(D - 1 - gm.delta), i}, make_int2(i, x.y)});
+      }
+      const int tpb = std::max(1, 256 / (t.TS * t.TS));
+      for (int g = 0; g < p->G; ++g)
+        for (int t0 = 0; t0 < t.n_tiles; t0 += tpb) prep.push_back(make_int4(i, t0, g, g == 0 && t0 == 0));
+      sh.max_item_floats = std::max(sh.max_item_floats, p->tshape.max_item_floats);
+      sh.cd_entries = std::max(sh.cd_entries, p->tshape.cd_entries);
+      sh.max_len = std::max(sh.max_len, p->tshape.max_len);
+      sh.n_pairs = std::max(sh.n_pairs, p->tshape.n_pairs);
+      sh.split_units = std::max(sh.split_units, p->tshape.split_units);
+      if (p->n_polar != sh.np_exact) sh.np_exact = 0;
+      b->np_max = std::max(b->np_max, p->np_class);
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::pair<std::pair<int, int>, int2> &x, const std::pair<std::pair<int, int>, int2> &y) {
+                       return x.first.first < y.first.first;
+                     });
+    std::vector<int2> queue(items.size());
+    for (size_t k = 0; k < items.size(); ++k) queue[k] = items[k].second;
+    b->shape = sh;
+    b->n_tqueue = (int)queue.size();
+    b->n_tprep = (int)prep.size();
+    cudaError_t e = cudaMalloc((void **)&b->d_tinst, n * sizeof(TileInst));
+    if (e == cudaSuccess) e = upload_vec(&b->d_tqueue, queue);
+    if (e == cudaSuccess) e = upload_vec(&b->d_tprep, prep);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ticket, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ticket, 0, sizeof(int));
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return cuda_fail(e, "batch_create");
+    }
+    b->grid = tile_sweep_grid(b->np_max, tile_sweep_smem(sh, b->np_max));
+    *out = b;
+    return MOLC_OK;
+  }
   b->h_inst.resize(n);
   // block maps
   std::vector<int4> prep;
@@ -1356,10 +1680,12 @@ molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
     const bool f = x.fxx || x.fxy || x.fyy;
     if (f && !(x.fxx && x.fxy && x.fyy))
       return fail(MOLC_ERR_INVALID_ARG, "batch_bind: instance %zu: give all of fxx, fxy, fyy or none", i);
-    BatchInst &h = b->h_inst[i];
-    h.v = p->view;
-    h.L = layout_for(p->view, MOLC_FP32);
-    SweepArgs &a = h.a;
+    SweepArgs a0{};
+    SweepArgs &a = b->tiled ? a0 : b->h_inst[i].a;
+    if (!b->tiled) {
+      b->h_inst[i].v = p->view;
+      b->h_inst[i].L = layout_for(p->view, MOLC_FP32);
+    }
     a = SweepArgs{};
     a.kappa = x.kappa;
     a.B = x.B;
@@ -1380,10 +1706,22 @@ molc_status molc_batch_bind(molc_batch *b, const molc_sweep_args *args) {
     a.fxx = x.fxx;   // factors formed where the moments are assembled
     a.fxy = x.fxy;
     a.fyy = x.fyy;
+    if (b->tiled) {
+      a.cdat = nullptr;
+      a.cdB = nullptr;
+      a.items = nullptr;
+      a.n_items = 0;
+      TileInst &ti = b->h_tinst[i];
+      ti.v = p->view;
+      ti.t = p->tv;
+      ti.a = a;
+    }
   }
   DeviceGuard dg(b->device);
-  cudaError_t e = cudaMemcpy(b->d_inst, b->h_inst.data(), b->h_inst.size() * sizeof(BatchInst),
-                             cudaMemcpyHostToDevice);
+  cudaError_t e = b->tiled ? cudaMemcpy(b->d_tinst, b->h_tinst.data(), b->h_tinst.size() * sizeof(TileInst),
+                                        cudaMemcpyHostToDevice)
+                           : cudaMemcpy(b->d_inst, b->h_inst.data(), b->h_inst.size() * sizeof(BatchInst),
+                                        cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "batch_bind");
   b->bound = true;
   return MOLC_OK;
@@ -1394,6 +1732,13 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
   if (!b->bound) return fail(MOLC_ERR_INVALID_ARG, "batch_sweep: no arguments bound (molc_batch_bind)");
   DeviceGuard dg(b->device);
   cudaStream_t st = (cudaStream_t)stream;
+  if (b->tiled) {
+    cudaError_t e = launch_update_scale_tiles(b->d_tinst, (int)b->plans.size(), st);
+    if (e == cudaSuccess) e = launch_tile_prep(b->d_tinst, b->d_tprep, b->n_tprep, b->d_ticket, st);
+    if (e == cudaSuccess)
+      e = launch_tile_sweep(b->d_tinst, b->d_tqueue, b->n_tqueue, b->d_ticket, b->np_max, b->shape, b->grid, st);
+    return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "batch_sweep");
+  }
   cudaError_t e = launch_update_scale_batch(b->d_inst, (int)b->plans.size(), st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: scale");
   e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
@@ -1480,8 +1825,14 @@ static molc_status intensity_copy(const molc_plan *p, molc_precision prec, void 
     e = cudaMemcpyAsync(bref + off, B + off, (size_t)g_count * p->view.ncell * sizeof(double),
                         cudaMemcpyDeviceToDevice, st);
   }
-  if (e == cudaSuccess)
-    e = launch_intensity_copy(p->view, prec, I, bref, header_of(p, prec, I), g_begin, g_count, canon, to_canon, st);
+  if (e == cudaSuccess) {
+    if (prec == MOLC_FP32 && p->tiled)
+      e = launch_tile_intensity_copy(p->view, p->tv, p->d_tpiece, p->d_tpiece_off, (float *)I, bref,
+                                     header_of(p, prec, I), g_begin, g_count, canon, to_canon, st);
+    else
+      e = launch_intensity_copy(p->view, prec, I, bref, header_of(p, prec, I), g_begin, g_count, canon, to_canon,
+                                st);
+  }
   return e == cudaSuccess ? MOLC_OK : cuda_fail(e, who);
 }
 

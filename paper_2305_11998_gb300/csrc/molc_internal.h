@@ -257,12 +257,24 @@ struct TileInst {      // one instance of a tiled sweep launch (device memory)
   SweepArgs a;
 };
 
-// tiled sweep launchers: prep (cell tables, ticket reset, epoch), the persistent sweep over the queue
-// {instance, item} (ticket: the launch's counter, reset by the prep), intensity export/import
+// Shared-memory shape of a tiled-sweep launch: the largest item state (floats), cell-table entries (TS2p x GT),
+// step count, azimuth pairs and split-cell moment units (units x GT) over its instances, and their common polar
+// count (0 if they differ).
+struct TileShape {
+  int max_item_floats, cd_entries, max_len, n_pairs, split_units, np_exact;
+};
+// tiled sweep launchers: prep (cell tables, ticket reset, epoch; map {instance, first tile, group, check bnd}), the
+// persistent sweep over the queue {instance, item} (ticket: the launch's counter, reset by the prep), intensity
+// export/import
 cudaError_t launch_tile_prep(const TileInst *inst, const int4 *map, int blocks, int *ticket, cudaStream_t st);
+// one plan: `ov` (by value) is also stored at dst for the sweep launch that follows
+cudaError_t launch_tile_prep_one(const TileInst &ov, TileInst *dst, const int4 *map, int blocks, int *ticket,
+                                 cudaStream_t st);
+// batched FP32 state scale update over tiled instances
+cudaError_t launch_update_scale_tiles(const TileInst *inst, int n, cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
-                              size_t smem, int grid, cudaStream_t st);
-size_t tile_sweep_smem(int max_item_floats, int TS2p, int GT, int max_len, int n_pairs, int np_max);
+                              const TileShape &shape, int grid, cudaStream_t st);
+size_t tile_sweep_smem(const TileShape &shape, int np_max);
 int tile_sweep_grid(int np_max, size_t smem);
 cudaError_t launch_tile_intensity_copy(const PlanView &v, const TileView &t, const int4 *tpiece,
                                        const int64_t *tpiece_off, float *I, const double *Bref,
@@ -270,7 +282,7 @@ cudaError_t launch_tile_intensity_copy(const PlanView &v, const TileView &t, con
                                        cudaStream_t st);
 
 // Fixed workspace of molc_sweep_static_scratch: a file-scope device array in molc_kernels.cu, 256-byte aligned.
-constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;
 // Device address of that array on the current device.  The first call per device looks the symbol up (which
 // also loads the library's kernels on that device if nothing has yet); later calls return the cached address.
 cudaError_t static_scratch_address(void **ptr);

@@ -1042,9 +1042,10 @@ __global__ void __launch_bounds__(256) update_scale_kernel(const double *B, int6
 }
 
 // Batched: one block per instance reduces max(B, boundary) and updates that instance's scale.
-__global__ void __launch_bounds__(256) update_scale_batch_kernel(const BatchInst *inst) {
+template <class Inst>
+__global__ void __launch_bounds__(256) update_scale_batch_kernel(const Inst *inst) {
   __shared__ unsigned long long red[8];
-  const BatchInst &b = inst[blockIdx.x];
+  const Inst &b = inst[blockIdx.x];
   const int64_t n = (int64_t)b.v.G * b.v.ncell;
   unsigned long long m = 0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
@@ -1231,7 +1232,7 @@ cudaError_t launch_update_scale(const PlanView &v, const double *B, const double
 
 cudaError_t launch_update_scale_batch(const BatchInst *inst, int n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  update_scale_batch_kernel<<<n, 256, 0, st>>>(inst);
+  update_scale_batch_kernel<BatchInst><<<n, 256, 0, st>>>(inst);
   return cudaGetLastError();
 }
 
@@ -1407,6 +1408,598 @@ cudaError_t static_scratch_address(void **ptr) {
   if (dev >= 0 && dev < kMaxDevices) cached[dev] = addr;
   *ptr = addr;
   return cudaSuccess;
+}
+
+
+// =========================================================================================================
+// Tiled FP32 sweep: the characteristic grid cut into per-tile pieces (molc_tiles.cpp), one persistent launch
+// over work items (tile, quadrant, group tile) taken from an atomic ticket in wavefront order.  Per item:
+//   1. one thread starts bulk copies (cp.async.bulk, completion on an mbarrier) of the item's previous-step state
+//      (its pieces' deviations, packed step by step exactly as the item walks them) and of its cell table into
+//      shared memory, and waits (bounded) until the items upstream in its quadrant have finished this step;
+//   2. each thread walks one (piece, group): the deviation-form update of Eqs. 11-13, arithmetic identical to
+//      sweep_fp32_body, with the state read and rewritten in shared memory and the records (cell, l) prefetched
+//      four steps ahead from L2; the intensity leaving the tile goes to the next piece's slot of the boundary
+//      buffer (L2), the item's flag is raised, and the new state is bulk-copied back;
+//   3. each thread sums one cell's moment entries of this quadrant from the new state in shared memory (polar
+//      fold in FP32, runs of one pair in FP32, two-word FP32 across runs) and writes the quadrant's partial
+//      moments (FP64); the last of the four quadrant items of a (tile, group tile) adds the four partials in
+//      quadrant order and assembles E, F, N (and f) like the moment gather.
+// No block waits on a block that has not started: a ticket is taken only by a running block, and an item waits
+// only on items of earlier tickets.  Every wait is bounded and records kStatusTimeout when it gives up.
+// =========================================================================================================
+namespace {
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completing on `bar`
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// shared -> global bulk copy in the issuing thread's bulk group
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's shared-memory writes before later bulk copies (async proxy) read them
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr unsigned kBulkChunk = 32768;   // bytes per bulk-copy instruction
+
+// shared memory of one block: state | cdat (float4) | cdB | P | direction table | split-cell partials (double)
+struct TileSmem {
+  size_t state, cdat, cdB, P, dir, split, total;
+};
+__host__ __device__ inline size_t up16(size_t b) { return (b + 15) / 16 * 16; }
+__host__ __device__ inline TileSmem tile_smem_layout(int max_item_floats, int TS2p, int GT, int max_len,
+                                                     int n_pairs, int np, int split_units) {
+  TileSmem m;
+  m.state = 0;
+  m.cdat = up16((size_t)max_item_floats * 4);
+  m.cdB = m.cdat + (size_t)GT * TS2p * 16;
+  m.P = m.cdB + up16((size_t)GT * TS2p * 4);
+  m.dir = m.P + up16((size_t)(max_len + 1) * 4);
+  m.split = m.dir + up16((size_t)n_pairs * (3 * np + 2) * 4);
+  m.total = m.split + (size_t)split_units * GT * kOutputs * 8;
+  return m;
+}
+
+// Bounded spin of one thread on a flag reaching `epoch`; false (and the status recorded) if it gave up.
+__device__ bool wait_flag(const int *flag, int epoch, int *status) {
+  for (int it = 0; it < kTileWaitLimit; ++it) {
+    if (ld_acquire_gpu(flag) >= epoch) return true;
+    __nanosleep(it < 64 ? 32 : 256);
+  }
+  atomicOr(status, kStatusTimeout);
+  return false;
+}
+
+// Cell tables of the tiles (prep_tiles, laid out [tile][G][TS2p], the state's rescale folded into the second
+// entry), the input checks, the ticket reset of the coming sweep launch and the plan's step epoch.
+__device__ __forceinline__ void tile_prep_body(const PlanView &v, const TileView &t, const SweepArgs &a, int4 m,
+                                               int *ticket) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0;
+  if (m.w && threadIdx.x == 0) t.ctrl[1] += 1;   // a new step of this plan: flags of earlier steps are stale
+  const int TS = t.TS, TS2 = TS * TS;
+  const int tpb = max(1, (int)blockDim.x / TS2);
+  const int tile = m.y + threadIdx.x / TS2, cl = threadIdx.x % TS2;
+  const int g = m.z;
+  bool bad = false, range = false;
+  if (threadIdx.x < tpb * TS2 && tile < t.n_tiles) {
+    const int ix = (tile % t.ntx) * TS + cl % TS, iy = (tile / t.ntx) * TS + cl / TS;
+    if (ix < v.nx && iy < v.ny) {
+      const float inv_cdt_f = (float)a.inv_cdt;
+      const double sc = a.scale[0];
+      const float rescale = (float)a.scale[3];
+      const int64_t idx = (int64_t)g * v.ncell + (int64_t)iy * v.nx + ix;
+      const double kap = a.kappa[idx], B = a.B[idx];
+      bad = bad_input(kap) | bad_input(B);
+      const float kt = (float)(kap + a.inv_cdt);
+      const float r = __fdiv_rn(inv_cdt_f, kt);
+      const double Bs = B * sc;
+      range = __double_as_longlong(Bs) >= __double_as_longlong(kScaledMax);
+      const float bhi = (float)Bs;
+      const float blo = (float)(Bs - f32_to_f64_exact(bhi));
+      const int64_t o = ((int64_t)tile * v.G + g) * t.TS2p + cl;
+      t.cdat[o] = make_float4(kt, r * rescale, bhi, blo);
+      t.cdB[o] = (float)((a.Bref[idx] - B) * sc) * r;
+    }
+  }
+  if (m.w)
+    for (int i = threadIdx.x; i < 4 * v.G; i += blockDim.x) {
+      bad |= bad_input(a.bnd[i]);
+      range |= !(a.bnd[i] * a.scale[0] < kScaledMax);
+    }
+  if (bad) atomicOr(v.status, kStatusNonfinite);
+  if (range && !bad) atomicOr(v.status, kStatusRange);
+}
+
+// map[block] = {instance, first tile, group, 1: this block also checks the boundary and starts the plan's step}
+__global__ void __launch_bounds__(256) tile_prep_kernel(const TileInst *inst, const int4 *map, int *ticket) {
+  const int4 m = map[blockIdx.x];
+  const TileInst &I = inst[m.x];
+  tile_prep_body(I.v, I.t, I.a, m, ticket);
+}
+
+// One plan: the call's instance comes by value and is stored for the sweep launch that follows.
+__global__ void __launch_bounds__(256) tile_prep_one_kernel(TileInst ov, TileInst *dst, const int4 *map,
+                                                            int *ticket) {
+  const int4 m = map[blockIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dst = ov;
+  tile_prep_body(ov.v, ov.t, ov.a, m, ticket);
+}
+
+// Moments of one cell unit (entries [e0, e1) of the geometry) from the new state in shared memory: polar fold
+// in FP32, runs of at most kPairRun entries of one pair in FP32, two-word FP32 across runs (as the moment
+// gather), then FP64.
+template <int NPM, bool EXACT>
+__device__ __forceinline__ void tile_unit_sums(const TileView &t, const TileGeom &gm, int np, int gcnt, int gl,
+                                               const float *sst, const float *dirt, int e0, int e1,
+                                               double (&D)[kOutputs]) {
+  float hi[kOutputs], lo[kOutputs];
+#pragma unroll
+  for (int k = 0; k < kOutputs; ++k) hi[k] = lo[k] = 0.f;
+  const int dstride = 3 * np + 2;
+  int cur = -1, run = 0;
+  float P0 = 0.f, P1 = 0.f, P2 = 0.f;
+  auto flush = [&]() {
+    if (cur < 0) return;
+    const float cf = dirt[cur * dstride + 3 * np], sf = dirt[cur * dstride + 3 * np + 1];
+    two_sum_add(hi[0], lo[0], P0);
+    two_sum_add(hi[1], lo[1], cf * P1);
+    two_sum_add(hi[2], lo[2], sf * P1);
+    two_sum_add(hi[3], lo[3], (cf * cf) * P2);
+    two_sum_add(hi[4], lo[4], (cf * sf) * P2);
+    two_sum_add(hi[5], lo[5], (sf * sf) * P2);
+  };
+  const int2 *ent = t.ents + gm.ent_off;
+  for (int e = e0; e < e1; ++e) {
+    const int2 en = __ldg(ent + e);
+    const int slot = en.x & 0xFFFFFF, pr = (int)((unsigned)en.x >> 24);
+    if (pr != cur || run == kPairRun) {
+      flush();
+      cur = pr;
+      run = 0;
+      P0 = P1 = P2 = 0.f;
+    }
+    ++run;
+    const float *dv = sst + ((int64_t)slot * gcnt + gl) * np;
+    const float *c0 = dirt + pr * dstride;
+    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+    for (int p = 0; p < NPM; ++p)
+      if (EXACT || p < np) {
+        const float x = dv[p];
+        S0 = fmaf(c0[p], x, S0);
+        S1 = fmaf(c0[np + p], x, S1);
+        S2 = fmaf(c0[2 * np + p], x, S2);
+      }
+    const float af = __int_as_float(en.y);
+    P0 = fmaf(af, S0, P0);
+    P1 = fmaf(af, S1, P1);
+    P2 = fmaf(af, S2, P2);
+  }
+  flush();
+#pragma unroll
+  for (int k = 0; k < kOutputs; ++k) D[k] = f32_to_f64(hi[k]) + f32_to_f64(lo[k]);
+}
+
+template <int NPM, bool EXACT>
+__global__ void __launch_bounds__(512) tile_sweep_kernel(const TileInst *inst, const int2 *queue, int n_queue,
+                                                        int *ticket, TileSmem lay) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long bar;
+  __shared__ int s_q, s_last;
+  float *sst = reinterpret_cast<float *>(smem + lay.state);
+  float4 *scd = reinterpret_cast<float4 *>(smem + lay.cdat);
+  float *scdB = reinterpret_cast<float *>(smem + lay.cdB);
+  int *sP = reinterpret_cast<int *>(smem + lay.P);
+  float *sdir = reinterpret_cast<float *>(smem + lay.dir);
+  double *ssplit = reinterpret_cast<double *>(smem + lay.split);
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_proxy_async_smem();
+  }
+  __syncthreads();
+  unsigned phase = 0;
+  bool stored = false;   // a bulk store of this block may still be reading shared memory
+  for (;;) {
+    if (tid == 0) s_q = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int qi = s_q;
+    if (qi >= n_queue) break;
+    const int2 qe = queue[qi];
+    const TileInst &I = inst[qe.x];
+    const PlanView &v = I.v;
+    const TileView &t = I.t;
+    const SweepArgs &a = I.a;
+    const int item = qe.y;
+    const int gt = item / t.n_geoms, gidx = item - gt * t.n_geoms;
+    const TileGeom gm = t.geoms[gidx];
+    const int np = EXACT ? NPM : v.n_polar;
+    const int g0 = gt * t.GT, gcnt = min(t.GT, v.G - g0);
+    const int epoch = t.ctrl[1];
+    float *state_g = (float *)a.I + t.item_off[item];
+    const unsigned state_bytes = (unsigned)((((int64_t)gm.n_slots * gcnt * np + 3) / 4 * 4) * 4);
+    const int64_t cd_off = ((int64_t)gm.tile * v.G + g0) * t.TS2p;
+    // 1. stage the state and the cell table (one thread), wait for the upstream items (one thread)
+    if (tid == 0) {
+      if (stored) bulk_wait_read_all();   // the previous item's store has read the buffer
+      const unsigned cd_bytes = (unsigned)gcnt * t.TS2p * 16, cdB_bytes = (unsigned)gcnt * t.TS2p * 4;
+      mbar_arrive_expect_tx(&bar, state_bytes + cd_bytes + cdB_bytes);
+      for (unsigned o = 0; o < state_bytes; o += kBulkChunk)
+        bulk_load((char *)sst + o, (const char *)state_g + o, min(kBulkChunk, state_bytes - o), &bar);
+      bulk_load(scd, t.cdat + cd_off, cd_bytes, &bar);
+      bulk_load(scdB, t.cdB + cd_off, cdB_bytes, &bar);
+    }
+    for (int i = tid; i <= gm.max_len; i += nthr) sP[i] = t.Ptab[gm.P_off + i];
+    {
+      // direction table of this quadrant: per pair the polar folds {w, w sin, w sin^2} and the in-plane
+      // direction of the pair's sense that points into q
+      const int dstride = 3 * np + 2;
+      for (int i = tid; i < v.n_pairs * dstride; i += nthr) {
+        const int pr = i / dstride, k = i - pr * dstride;
+        float val;
+        if (k < 3 * np) {
+          const int p = k % np, kind = k / np;
+          const PolarDev pd = v.polar[pr * np + p];
+          val = kind == 0 ? pd.wf : kind == 1 ? pd.wf * pd.sinzf : (pd.wf * pd.sinzf) * pd.sinzf;
+        } else {
+          const PairDev pp = v.pairs[pr];
+          const bool minus = ((pp.c < 0) != ((gm.q & 1) != 0)) || ((pp.s < 0) != ((gm.q & 2) != 0));
+          const float cf = minus ? -pp.cf : pp.cf, sf = minus ? -pp.sf : pp.sf;
+          val = k == 3 * np ? cf : sf;
+        }
+        sdir[i] = val;
+      }
+    }
+    if (tid == 0) {
+      const int base = gt * t.n_geoms;
+      if (gm.up_x >= 0) wait_flag(t.flags + base + gm.up_x, epoch, v.status);
+      if (gm.up_y >= 0) wait_flag(t.flags + base + gm.up_y, epoch, v.status);
+      int it = 0;
+      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) __nanosleep(32);
+      if (it >= kTileWaitLimit) atomicOr(v.status, kStatusTimeout);
+    }
+    __syncthreads();
+    // all threads observe the completed phase (the copies' data is visible to them after this wait)
+    {
+      int it = 0;
+      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) __nanosleep(32);
+    }
+    phase ^= 1;
+    // 2. walk the pieces
+    const double sc = a.scale[0];
+    for (int k = tid; k < gm.n_pieces * gcnt; k += nthr) {
+      const int r = k / gcnt, gl = k - r * gcnt, g = g0 + gl;
+      const int4 pc = t.pieces[gm.piece_off + r];
+      const int len = pc.y >> 1;
+      const int pair = v.tracks[pc.x].pair;
+      float half_inv_sinz[NPM], sinz[NPM], psi[NPM];
+#pragma unroll
+      for (int p = 0; p < NPM; ++p) {
+        half_inv_sinz[p] = sinz[p] = psi[p] = 0.f;
+        if (EXACT || p < np) {
+          const PolarDev pd = v.polar[pair * np + p];
+          half_inv_sinz[p] = 0.5f * pd.inv_sinzf;
+          sinz[p] = pd.sinzf;
+        }
+      }
+      float bhi_prev, blo_prev;
+      if (pc.z < 0) {   // the piece starts on the domain boundary: entering intensity, split like B
+        const double bin = a.bnd[(-1 - pc.z) * v.G + g] * sc;
+        bhi_prev = (float)bin;
+        blo_prev = (float)(bin - (double)bhi_prev);
+      } else {          // from the previous piece of the characteristic (through L2)
+        const float *bb = t.bbuf + ((int64_t)pc.z * v.G + g) * (np + 2);
+#pragma unroll
+        for (int p = 0; p < NPM; ++p)
+          if (EXACT || p < np) psi[p] = __ldcg(bb + p);
+        bhi_prev = __ldcg(bb + np);
+        blo_prev = __ldcg(bb + np + 1);
+      }
+      const int2 *rec = t.recs + gm.slot_base + r;
+      int2 rr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rr[u] = u < len ? ld_record(rec + sP[u]) : make_int2(0, 0);
+      for (int s0 = 0; s0 < len; s0 += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int s = s0 + u;
+          if (s < len) {
+            const int2 rc = rr[u];
+            if (s + 4 < len) rr[u] = ld_record(rec + sP[s + 4]);
+            float *sv = sst + ((int64_t)(sP[s] + r) * gcnt + gl) * np;
+            const float4 q = scd[gl * t.TS2p + rc.x];
+            const float dB = scdB[gl * t.TS2p + rc.x];
+            const float len_f = __int_as_float(rc.y);
+            const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
+            const float kl = q.x * len_f;
+            const float rkl = rcp_approx(kl);
+            float dv[NPM];
+            if constexpr (NPM == 4) {
+              if (EXACT) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(sv);
+                dv[0] = d4.x;
+                dv[1] = d4.y;
+                dv[2] = d4.z;
+                dv[3] = d4.w;
+              } else {
+#pragma unroll
+                for (int p = 0; p < NPM; ++p) dv[p] = p < np ? sv[p] : 0.f;
+              }
+            } else {
+#pragma unroll
+              for (int p = 0; p < NPM; ++p) dv[p] = (EXACT || p < np) ? sv[p] : 0.f;
+            }
+#pragma unroll
+            for (int p = 0; p < NPM; ++p) psi[p] += jump;
+#pragma unroll
+            for (int p = 0; p < NPM; ++p) {
+              if (EXACT || p < np) {
+                float E1, om, ex;
+                bool thin;
+                const float ahalf = kl * half_inv_sinz[p];
+                attenuation(ahalf, sinz[p] * rkl, E1, om, ex, thin);
+                const float d = fmaf(dv[p], q.y, dB);
+                const float pin = psi[p];
+                const float x = pin - d;
+                dv[p] = fmaf(x, E1, d);
+                psi[p] = thin ? fmaf(-x, om, pin) : fmaf(x, ex, d);
+              }
+            }
+            if constexpr (NPM == 4) {
+              if (EXACT) {
+                *reinterpret_cast<float4 *>(sv) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+              } else {
+#pragma unroll
+                for (int p = 0; p < NPM; ++p)
+                  if (p < np) sv[p] = dv[p];
+              }
+            } else {
+#pragma unroll
+              for (int p = 0; p < NPM; ++p)
+                if (EXACT || p < np) sv[p] = dv[p];
+            }
+            bhi_prev = q.z;
+            blo_prev = q.w;
+          }
+        }
+      }
+      if (pc.w >= 0) {   // hand the outgoing intensity to the next piece
+        float *bb = t.bbuf + ((int64_t)pc.w * v.G + g) * (np + 2);
+#pragma unroll
+        for (int p = 0; p < NPM; ++p)
+          if (EXACT || p < np) __stcg(bb + p, psi[p]);
+        __stcg(bb + np, bhi_prev);
+        __stcg(bb + np + 1, blo_prev);
+      }
+    }
+    fence_proxy_async_smem();   // this thread's state writes before the bulk store reads them
+    __syncthreads();
+    if (tid == 0) {
+      if (state_bytes) {
+        for (unsigned o = 0; o < state_bytes; o += kBulkChunk)
+          bulk_store((char *)state_g + o, (const char *)sst + o, min(kBulkChunk, state_bytes - o));
+        bulk_commit();
+        stored = true;
+      }
+      __threadfence();   // every thread's boundary writes (ordered by the barrier) before the flag
+      st_release_gpu(t.flags + item, epoch);
+    }
+    // 3. moments of this quadrant: split cells' parts into shared memory first, then one task per (cell, group)
+    const int TS2 = t.TS * t.TS;
+    const int2 *cu = t.cell_units + gm.cu_off;
+    const int4 *un = t.units + gm.unit_off;
+    if (lay.total > lay.split) {
+      for (int k = tid; k < gm.n_units * gcnt; k += nthr) {
+        const int u = k / gcnt, gl = k - u * gcnt;
+        const int4 uu = un[u];
+        if (cu[uu.x].y > 1) {
+          double D[kOutputs];
+          tile_unit_sums<NPM, EXACT>(t, gm, np, gcnt, gl, sst, sdir, uu.y, uu.z, D);
+#pragma unroll
+          for (int o = 0; o < kOutputs; ++o) ssplit[((int64_t)u * gcnt + gl) * kOutputs + o] = D[o];
+        }
+      }
+      __syncthreads();
+    }
+    double *part = t.part + (((int64_t)gm.tile * t.n_gt + gt) * 4 + gm.q) * kOutputs * t.GT * t.TS2p;
+    for (int k = tid; k < TS2 * gcnt; k += nthr) {
+      const int gl = k / TS2, cl = k - gl * TS2;
+      const int2 c = cu[cl];
+      double D[kOutputs] = {0, 0, 0, 0, 0, 0};
+      if (c.y == 1) {
+        const int4 uu = un[c.x];
+        tile_unit_sums<NPM, EXACT>(t, gm, np, gcnt, gl, sst, sdir, uu.y, uu.z, D);
+      } else {
+        for (int j = 0; j < c.y; ++j)
+#pragma unroll
+          for (int o = 0; o < kOutputs; ++o) D[o] += ssplit[((int64_t)(c.x + j) * gcnt + gl) * kOutputs + o];
+      }
+#pragma unroll
+      for (int o = 0; o < kOutputs; ++o) part[((int64_t)o * t.GT + gl) * t.TS2p + cl] = D[o];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      int *cnt = t.cnt + (int64_t)gm.tile * t.n_gt + gt;
+      const int prev = atomicAdd(cnt, 1);
+      s_last = prev == 3;
+      if (prev == 3) {
+        *cnt = 0;   // ready for the next step (its items start after this launch ends)
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    if (s_last) {   // the four quadrant partials are in place: assemble the tile's cells
+      const double *pt = t.part + ((int64_t)gm.tile * t.n_gt + gt) * 4 * kOutputs * t.GT * t.TS2p;
+      const int tx = gm.tile % t.ntx, ty = gm.tile / t.ntx;
+      for (int k = tid; k < TS2 * gcnt; k += nthr) {
+        const int gl = k / TS2, cl = k - gl * TS2;
+        const int ix = tx * t.TS + cl % t.TS, iy = ty * t.TS + cl / t.TS;
+        if (ix >= v.nx || iy >= v.ny) continue;
+        double D[kOutputs] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int o = 0; o < kOutputs; ++o)
+            D[o] += __ldcg(pt + (((int64_t)q * kOutputs + o) * t.GT + gl) * t.TS2p + cl);
+        assemble_cell(v, a, iy * v.nx + ix, g0 + gl, D);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && stored) bulk_wait_all();   // the last state store has completed
+}
+
+// Canonical segment averages <-> tiled FP32 state: one thread per row (track, sense, step), looping over polar
+// cosines and the selected groups (as intensity_copy_kernel; only the element address differs).
+__global__ void tile_intensity_copy_kernel(PlanView v, TileView t, const int4 *tpiece, const int64_t *tpiece_off,
+                                           float *I, const double *Bref, const double *scale, int g_begin,
+                                           int g_count, double *canon, int to_canon, int64_t rows) {
+  const int NP = v.n_polar;
+  const double sc = scale[0], is = scale[1];
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = find_track(v.tracks, v.n_tracks, row);
+    const TrackDev tr = v.tracks[k];
+    const int64_t local = row - 2 * tr.seg_off;
+    const int sense = local >= tr.nseg;
+    const int s = (int)(local - (int64_t)sense * tr.nseg);
+    const int cell = v.seg_cell[sense ? tr.seg_off + tr.nseg - 1 - s : tr.seg_off + s];
+    // the piece holding step s of this sense
+    const int64_t a0 = tpiece_off[2 * k + sense], a1 = tpiece_off[2 * k + sense + 1];
+    int64_t pi = a0;
+    while (pi + 1 < a1 && tpiece[pi + 1].z <= s) ++pi;
+    const int4 tp = tpiece[pi];
+    const TileGeom gm = t.geoms[tp.x];
+    const int slot = t.Ptab[gm.P_off + (s - tp.z)] + tp.y;
+    for (int p = 0; p < NP; ++p) {
+      const PolarDev pd = v.polar[tr.pair * NP + p];
+      const int dir = sense ? pd.dir_minus : pd.dir_plus;
+      const int64_t cs = v.dir_seg_off[dir] + (sense ? tr.canon_minus : tr.canon_plus) + s;
+      for (int g = g_begin; g < g_begin + g_count; ++g) {
+        const int gt = g / t.GT, gl = g - gt * t.GT, gcnt = min(t.GT, v.G - gt * t.GT);
+        float *el = I + t.item_off[(int64_t)gt * t.n_geoms + tp.x] + ((int64_t)slot * gcnt + gl) * NP + p;
+        const double br = Bref[(int64_t)g * v.ncell + cell];
+        double *cv = canon + cs * g_count + (g - g_begin);
+        if (to_canon)
+          *cv = br + (double)*el * is;
+        else
+          *el = (float)((*cv - br) * sc);
+      }
+    }
+  }
+}
+
+template <int NPM, bool EXACT>
+cudaError_t launch_tile_np(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, const TileSmem &lay,
+                           int grid, cudaStream_t st) {
+  static bool attr = false;   // allow the largest dynamic shared memory once per instantiation
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tile_sweep_kernel<NPM, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  tile_sweep_kernel<NPM, EXACT><<<grid, kTileThreads, lay.total, st>>>(inst, queue, n_queue, ticket, lay);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tile_sweep_smem(const TileShape &sh, int np_max) {
+  return tile_smem_layout(sh.max_item_floats, sh.cd_entries, 1, sh.max_len, sh.n_pairs, np_max, sh.split_units).total;
+}
+
+cudaError_t launch_update_scale_tiles(const TileInst *inst, int n, cudaStream_t st) {
+  update_scale_batch_kernel<TileInst><<<n, 256, 0, st>>>(inst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_prep(const TileInst *inst, const int4 *map, int blocks, int *ticket, cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  tile_prep_kernel<<<blocks, 256, 0, st>>>(inst, map, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_prep_one(const TileInst &ov, TileInst *dst, const int4 *map, int blocks, int *ticket,
+                                 cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  tile_prep_one_kernel<<<blocks, 256, 0, st>>>(ov, dst, map, ticket);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
+                              const TileShape &sh, int grid, cudaStream_t st) {
+  const TileSmem lay = tile_smem_layout(sh.max_item_floats, sh.cd_entries, 1, sh.max_len, sh.n_pairs, np_max,
+                                        sh.split_units);
+  const bool exact = sh.np_exact == np_max;
+  switch (np_max) {
+    case 1: return exact ? launch_tile_np<1, true>(inst, queue, n_queue, ticket, lay, grid, st)
+                         : launch_tile_np<1, false>(inst, queue, n_queue, ticket, lay, grid, st);
+    case 2: return exact ? launch_tile_np<2, true>(inst, queue, n_queue, ticket, lay, grid, st)
+                         : launch_tile_np<2, false>(inst, queue, n_queue, ticket, lay, grid, st);
+    case 3: case 4: return exact && np_max == 4 ? launch_tile_np<4, true>(inst, queue, n_queue, ticket, lay, grid, st)
+                                                : launch_tile_np<4, false>(inst, queue, n_queue, ticket, lay, grid, st);
+    default: return exact && np_max == 8 ? launch_tile_np<8, true>(inst, queue, n_queue, ticket, lay, grid, st)
+                                         : launch_tile_np<8, false>(inst, queue, n_queue, ticket, lay, grid, st);
+  }
+}
+
+int tile_sweep_grid(int np_max, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void *fn = np_max <= 1 ? (const void *)tile_sweep_kernel<1, true>
+                 : np_max <= 2 ? (const void *)tile_sweep_kernel<2, true>
+                 : np_max <= 4 ? (const void *)tile_sweep_kernel<4, true> : (const void *)tile_sweep_kernel<8, true>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileThreads, smem) != cudaSuccess || per < 1) per = 1;
+  return sms * per;
+}
+
+cudaError_t launch_tile_intensity_copy(const PlanView &v, const TileView &t, const int4 *tpiece,
+                                       const int64_t *tpiece_off, float *I, const double *Bref,
+                                       const double *scale, int g_begin, int g_count, double *canon, bool to_canon,
+                                       cudaStream_t st) {
+  const int64_t rows = 2 * v.n_track_segments;
+  tile_intensity_copy_kernel<<<grid_for(rows, 128), 128, 0, st>>>(v, t, tpiece, tpiece_off, I, Bref, scale, g_begin,
+                                                                  g_count, canon, to_canon, rows);
+  return cudaGetLastError();
 }
 
 }  // namespace molc

@@ -26,9 +26,19 @@ struct HostPiece {
 
 }  // namespace
 
+TileShape tile_shape(const TileTables &t, int n_pairs, int np) {
+  TileShape sh;
+  sh.max_item_floats = t.max_item_floats;
+  sh.cd_entries = t.TS2p * t.GT;
+  sh.max_len = t.max_len;
+  sh.n_pairs = n_pairs;
+  sh.split_units = t.max_split_units * t.GT;
+  sh.np_exact = np;
+  return sh;
+}
+
 size_t tile_smem_bytes(const TileTables &t, int n_pairs, int np) {
-  return tile_sweep_smem(t.max_item_floats, t.TS2p, t.GT, t.max_len, n_pairs, np) +
-         (size_t)t.max_split_units * t.GT * kOutputs * sizeof(double);
+  return tile_sweep_smem(tile_shape(t, n_pairs, np), np);
 }
 
 namespace {
@@ -185,7 +195,8 @@ bool build(const TilePlanInput &in, int TS, int GT, const std::vector<int> &qp, 
       if (parts > 1) split_units += parts;
     }
     gm.n_units = (int)t.units.size() - gm.unit_off;
-    t.max_split_units = std::max(t.max_split_units, split_units);
+    // the kernel keeps the partial sums of every unit of a geometry that has split cells
+    if (split_units > 0) t.max_split_units = std::max(t.max_split_units, gm.n_units);
     // upstream geometries and wavefront step
     const int tx = gm.tile % t.ntx, ty = gm.tile / t.ntx;
     const int sx = (gm.q & 1) ? -1 : 1, sy = (gm.q & 2) ? -1 : 1;
@@ -246,6 +257,121 @@ bool build(const TilePlanInput &in, int TS, int GT, const std::vector<int> &qp, 
 
 }  // namespace
 
+bool check_tiles(const TilePlanInput &in, const TileTables &t, std::string &why) {
+  auto bad = [&](const char *what) {
+    why = std::string("tiled layout check failed: ") + what;
+    return false;
+  };
+  const std::vector<TileTrack> &tracks = *in.tracks;
+  const int64_t T = (int64_t)tracks.size();
+  const int TS = t.TS, nx = in.nx;
+  auto tile_of = [&](int c) { return (c / nx) / TS * t.ntx + (c % nx) / TS; };
+  auto local_of = [&](int c) { return ((c / nx) % TS) * TS + (c % nx) % TS; };
+  std::vector<int> qp((size_t)2 * in.n_pairs);
+  for (int j = 0; j < in.n_pairs; ++j) {
+    qp[2 * j] = quadrant_of(in.pair_c[j], in.pair_s[j]);
+    qp[2 * j + 1] = quadrant_of(-in.pair_c[j], -in.pair_s[j]);
+  }
+  // every slot of every geometry is written by exactly one (piece, step), with that segment's record
+  std::vector<uint8_t> seen(t.recs.size(), 0);
+  for (int64_t k = 0; k < T; ++k)
+    for (int sense = 0; sense < 2; ++sense) {
+      const TileTrack &tr = tracks[k];
+      const int64_t a = t.tpiece_off[2 * k + sense], z = t.tpiece_off[2 * k + sense + 1];
+      int step = 0;
+      for (int64_t i = a; i < z; ++i) {
+        const int4 tp = t.tpiece[i];
+        const TileGeom &gm = t.geoms[tp.x];
+        const int64_t gi = gm.piece_off + tp.y;
+        const int4 pc = t.pieces[gi];
+        const int len = pc.y >> 1;
+        if (pc.x != k || (pc.y & 1) != sense || tp.z != step) return bad("piece identity");
+        if (gm.q != qp[2 * tr.pair + sense]) return bad("piece quadrant");
+        for (int s = 0; s < len; ++s) {
+          const int st = step + s;
+          const int64_t seg = tr.seg_off + (sense ? tr.nseg - 1 - st : st);
+          const int c = in.seg_cell[seg];
+          if (tile_of(c) != gm.tile) return bad("segment outside its piece's tile");
+          const int64_t slot = gm.slot_base + t.Ptab[gm.P_off + s] + tp.y;
+          if (slot >= gm.slot_base + gm.n_slots || seen[slot]) return bad("record slot");
+          seen[slot] = 1;
+          const float lf = (float)in.seg_len[seg];
+          int lb;
+          std::memcpy(&lb, &lf, 4);
+          if (t.recs[slot].x != local_of(c) || t.recs[slot].y != lb) return bad("record contents");
+        }
+        // links: entering from the boundary or from the previous piece; leaving to the next piece
+        const int want_in = i == a ? -1 - (sense ? tr.entry_minus : tr.entry_plus) : (int)gi;
+        if (pc.z != want_in) return bad("piece entry link");
+        if (i + 1 < z) {
+          const int4 tn = t.tpiece[i + 1];
+          const TileGeom &gn = t.geoms[tn.x];
+          if (pc.w != (int)(gn.piece_off + tn.y)) return bad("piece exit link");
+          // the next tile lies one step along the direction: after this one in the quadrant's wavefront
+          const int dx = gn.tile % t.ntx - gm.tile % t.ntx, dy = gn.tile / t.ntx - gm.tile / t.ntx;
+          const int sx = (gm.q & 1) ? -1 : 1, sy = (gm.q & 2) ? -1 : 1;
+          if (!((dx == 0 || dx == sx) && (dy == 0 || dy == sy) && (dx != 0 || dy != 0)) || gn.q != gm.q)
+            return bad("consecutive pieces not in adjacent tiles along the direction");
+          if (gn.delta <= gm.delta) return bad("wavefront order");
+        } else if (pc.w != -1) {
+          return bad("last piece has an exit link");
+        }
+        step += len;
+      }
+      if (step != tr.nseg) return bad("pieces do not cover the characteristic");
+    }
+  for (size_t i = 0; i < seen.size(); ++i)
+    if (!seen[i]) return bad("unwritten record slot");
+  // moment entries: every slot once, in the cell of its record; units cover each cell's entries
+  std::fill(seen.begin(), seen.end(), 0);
+  for (const TileGeom &gm : t.geoms) {
+    const int TS2 = TS * TS;
+    int64_t covered = 0;
+    for (int cl = 0; cl < TS2; ++cl) {
+      const int2 cu = t.cell_units[gm.cu_off + cl];
+      int prev_end = -1;
+      for (int u = 0; u < cu.y; ++u) {
+        const int4 un = t.units[gm.unit_off + cu.x + u];
+        if (un.x != cl || (prev_end >= 0 && un.y != prev_end) || un.z <= un.y) return bad("moment units");
+        for (int e = un.y; e < un.z; ++e) {
+          const int2 en = t.ents[gm.ent_off + e];
+          const int slot = en.x & 0xFFFFFF;
+          if (slot >= gm.n_slots || seen[gm.slot_base + slot]) return bad("moment entry slot");
+          seen[gm.slot_base + slot] = 1;
+          if (t.recs[gm.slot_base + slot].x != cl) return bad("moment entry cell");
+          ++covered;
+        }
+        prev_end = un.z;
+      }
+    }
+    if (covered != gm.n_slots) return bad("moment entries do not cover the geometry");
+    // upstream geometries
+    const int tx = gm.tile % t.ntx, ty = gm.tile / t.ntx;
+    const int sx = (gm.q & 1) ? -1 : 1, sy = (gm.q & 2) ? -1 : 1;
+    const int ux = tx - sx, uy = ty - sy;
+    if (gm.up_x != (ux >= 0 && ux < t.ntx ? gm.q * t.n_tiles + ty * t.ntx + ux : -1)) return bad("upstream x");
+    if (gm.up_y != (uy >= 0 && uy < t.nty ? gm.q * t.n_tiles + uy * t.ntx + tx : -1)) return bad("upstream y");
+  }
+  // queue: every item once, each after its upstream items; state ranges disjoint and 16-byte aligned
+  std::vector<int> pos((size_t)t.n_items, -1);
+  for (size_t i = 0; i < t.queue.size(); ++i) {
+    if (t.queue[i] < 0 || t.queue[i] >= t.n_items || pos[t.queue[i]] >= 0) return bad("queue");
+    pos[t.queue[i]] = (int)i;
+  }
+  int64_t end = 0;
+  for (size_t i = 0; i < t.queue.size(); ++i) {
+    const int item = t.queue[i], gt = item / t.n_geoms, g = item % t.n_geoms;
+    const TileGeom &gm = t.geoms[g];
+    for (int up : {gm.up_x, gm.up_y})
+      if (up >= 0 && pos[gt * t.n_geoms + up] >= (int)i) return bad("queue order");
+    if (t.item_off[item] != end || t.item_off[item] % 4) return bad("state offsets");
+    const int gcount = std::min(t.GT, in.G - gt * t.GT);
+    end += ((int64_t)gm.n_slots * gcount * in.n_polar + 3) / 4 * 4;
+  }
+  if (end != t.state_floats) return bad("state size");
+  return true;
+}
+
 bool plan_tiles(const TilePlanInput &in, TileTables &t, std::string &why, int force_ts, int force_gt) {
   if (in.n_pairs > 256) {
     why = "more than 256 azimuth pairs";
@@ -270,7 +396,7 @@ bool plan_tiles(const TilePlanInput &in, TileTables &t, std::string &why, int fo
       if (!build(in, TS, GT, qp, t, why)) return false;
       if ((int64_t)t.max_split_units * t.GT > kTileMaxUnits) continue;
       if (tile_smem_bytes(t, in.n_pairs, np) > 227 * 1024) continue;
-      return true;
+      return check_tiles(in, t, why);
     }
   }
   why = "no tile size keeps a work item's state within the shared-memory budget";

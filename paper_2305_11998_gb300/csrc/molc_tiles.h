@@ -38,12 +38,20 @@ struct TileTables {     // host copies of a tiled layout
   std::vector<int64_t> tpiece_off; // [2 T + 1]: range of (track k, sense s) = [off[2k+s], off[2k+s+1])
 };
 
-// Shared memory of one tiled-sweep block for a layout (bytes), and whether a candidate fits one.
+// Shared-memory shape and bytes of one tiled-sweep block for a layout.
+TileShape tile_shape(const TileTables &t, int n_pairs, int np);
 size_t tile_smem_bytes(const TileTables &t, int n_pairs, int np);
 
 // Choose the tile size and groups per item (the largest tile whose items fit the shared-memory budget, then the
 // most groups per item that still fit) and build the tables.  force_ts / force_gt > 0 pin a choice (autotuner).
 // Returns false with a message when no candidate fits.
 bool plan_tiles(const TilePlanInput &in, TileTables &t, std::string &why, int force_ts = 0, int force_gt = 0);
+
+// Checks every invariant the tiled kernels rely on (run by plan_tiles on each layout it returns): each segment of
+// each sense is one record slot with its cell and length, pieces cover their characteristic in traversal order,
+// consecutive pieces lie in adjacent tiles along the direction and later in the quadrant's wavefront, links chain
+// them, moment entries and units cover every slot once in its record's cell, the queue lists every item after
+// its upstream items, and item states are disjoint 16-byte aligned ranges.  False with a message otherwise.
+bool check_tiles(const TilePlanInput &in, const TileTables &t, std::string &why);
 
 }  // namespace molc

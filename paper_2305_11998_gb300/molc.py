@@ -66,7 +66,8 @@ class _Info(C.Structure):
                 ("n_polar", C.c_int), ("n_tracks", C.c_int64), ("n_track_segments", C.c_int64),
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
                 ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int),
-                ("n_split_cells", C.c_int)]
+                ("n_split_cells", C.c_int), ("fp32_tile_cells", C.c_int), ("fp32_tile_groups", C.c_int),
+                ("fp32_tile_items", C.c_int), ("fp32_sweep_blocks", C.c_int)]
 
 
 class _SweepArgs(C.Structure):
@@ -189,6 +190,10 @@ class PlanInfo:
     fp32_sweep_depth: int
     n_faces: int
     n_split_cells: int
+    fp32_tile_cells: int
+    fp32_tile_groups: int
+    fp32_tile_items: int
+    fp32_sweep_blocks: int
 
 
 class Plan:

@@ -89,13 +89,15 @@ def test_invalid_arguments_are_rejected():
 
 @pytest.mark.parametrize("fine", [False, True])
 def test_split_cell_count_follows_the_entry_lists(fine):
-    # a cell's gather list holds one entry per (track segment, sense) crossing it, padded to a multiple of 4;
-    # lists longer than 256 entries are summed in parts (n_split_cells)
+    # the moment gather of the bundle sweep (plans that are not tiled: here MOLC_BALANCE): a cell's gather list holds
+    # one entry per (track segment, sense) crossing it, padded to a multiple of 4; lists longer than 256 entries are
+    # summed in parts (n_split_cells)
     wl = synth.Workload("paper8", 8, 8, 6.0, 17, 0.001, 100.0, 2, 16, 40, 1)
     q = wl.quadrature()
     h = 0.02 if fine else 0.5
     P = molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, h, "paper", False,
-                  host_only=True)
+                  host_only=True, balance=True)
+    assert P.info.fp32_tile_cells == 0
     cells = P.tracks()["cell"]
     entries = np.bincount(cells, minlength=wl.ncell) // wl.n_polar   # export: every polar cosine and sense
     padded = (entries + 3) // 4 * 4
