@@ -7,8 +7,9 @@ synthetic Fleck-Cummings-shaped workload with three tanh fronts.  The intensity 
 far larger than L2, so no cache flush is needed between steps.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle instead (double precision, all host
-cores, one group of the same workload per step).  Under torchrun every rank sweeps its own instance (seed =
-rank): weak scaling, no collective on the data path.
+cores, one group of the same workload per step).  Under torchrun the instance's groups are split into contiguous
+ranges, one per rank (strong scaling; no collective on the data path; an all-gather of the results for a consumer
+that needs all groups is timed separately).
 """
 from __future__ import annotations
 
@@ -66,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the sweeps (warmup + steps) in --precision, for profiler captures")
+    ap.add_argument("--tiled", action="store_true", help="--workload batch64: plans with the tiled FP32 sweep")
+    ap.add_argument("--no-batch", action="store_true", help="leave the batched pattern out of the default line")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the --kernel-only sweeps (fp64: also the device's FP64 FMA rate)")
     args = ap.parse_args()
@@ -238,10 +241,14 @@ def run_ours(args):
     import paper_2305_11998_gb300 as molc
 
     wl = synth.WORKLOADS[args.workload]
-    d = wl.inputs(seed=pdist.instance_seed(0, rank))
-    P = molc.Plan.from_workload(wl)
+    # one instance; with N > 1 ranks its groups are split into contiguous ranges, one per rank (no data exchange on
+    # the path: every group is swept independently)
+    groups = pdist.shard_groups(wl.G, ws, rank)
+    d = pdist.shard_inputs(wl.inputs(seed=0), groups)
+    P = molc.Plan.from_workload(wl, groups=groups if ws > 1 else None)
     info = P.info
-    G, ncell = wl.G, wl.ncell
+    G, ncell = len(groups), wl.ncell
+    updates_total = info.n_segments * wl.G     # every group costs the same updates
     k_h = torch.tensor(d["kappa"]).pin_memory()
     B_h = torch.tensor(d["B"]).pin_memory()
     bnd_h = torch.tensor(d["bnd"]).pin_memory()
@@ -284,13 +291,31 @@ def run_ours(args):
         sampler.mark(False)
     barrier()
     ms = pdist.max_over_ranks(e0.elapsed_time(e1), dev)
+    # a consumer that needs every group on every GPU (the grey closure of Eqs. 8-9) would all-gather the six moments
+    # and three factors once per step: timed here separately, after the sweeps
+    allgather = None
+    if ws > 1:
+        arrays = [mom[k] for k in ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")] + [fac[k] for k in ("fxx", "fxy", "fyy")]
+        for a in arrays:
+            pdist.gather_groups(a, wl.G, groups, ws)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            for a in arrays:
+                pdist.gather_groups(a, wl.G, groups, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ag_ms = pdist.max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
+        allgather = {"ms_per_step": ag_ms, "bytes_per_rank": 9 * wl.G * ncell * 8,
+                     "what": "NCCL all-gather of E, F, N and the Eddington factors of all groups, after the timed steps"}
     parts, kern_n = P.kernel_time_parts()
     kern_ms = parts["sweep"]
     P.kernel_timing(False)
     clocks = sampler.stop() if sampler else None
     status = P.device_status()
     ms_step = ms / args.steps
-    value = pdist.weak_scaling_rate(info.n_updates * args.steps, ws, ms / 1e3)
+    value = updates_total * args.steps / (ms / 1e3)    # the whole instance's updates over the slowest rank's time
 
     # roofline of the dominant kernel (the FP32 sweep): algorithmic bytes per launch / average launch time
     gc = info.fp32_groups_per_warp
@@ -387,14 +412,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         ems = pdist.max_over_ranks(e0.elapsed_time(e1), dev)
-        e2e = {"value": pdist.weak_scaling_rate(info.n_updates * args.steps, ws, ems / 1e3), "unit": "updates/s",
+        e2e = {"value": updates_total * args.steps / (ems / 1e3), "unit": "updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": ems / args.steps,
                "copies": "pinned host buffers, two copy streams pipelined against the sweeps (double-buffered)"}
 
     # the plain FP64 GPU sweep on the same workload (the speed-up denominator)
     fp64 = None
     if not args.no_fp64:
-        del I
+        I = None
         torch.cuda.empty_cache()
         I64 = P.new_intensity("fp64", dev)
         P.intensity_init("fp64", I64, B_d)
@@ -411,21 +436,44 @@ def run_ours(args):
                 "speedup_fp32_over_fp64": (info.n_updates / (ms_step / 1e3)) / (info.n_updates / (ms64 / 1e3))}
         del I64
 
+    # the batched production pattern (64 uneven instances, one molc_batch_sweep per step, 5 steps in a CUDA graph)
+    batch = None
+    if ws == 1 and not args.no_batch:
+        I = None     # the 512^2 state is no longer needed
+        torch.cuda.empty_cache()
+        _, bplans, _, bt, t_plan = batch_setup()
+        bms = batch_graph_ms(bt, 5, 2)
+        bupd = sum(Q.info.n_updates for Q in bplans)
+        bbytes = batch_alg_bytes(bplans)
+        batch = {"value": bupd * 5 / (bms / 1e3), "unit": "updates/s", "ms_per_step": bms / 5,
+                 "updates_per_step": bupd, "steps": 5, "plan_seconds_with_autotune": t_plan,
+                 "roofline": {"bound": "hbm", "achieved": bbytes * 5 / (bms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": bbytes * 5 / (bms / 1e3) / 1e9 / peak},
+                 "what": "64 seeded uneven instances (synth.batch_instances), molc_batch_sweep with factors, 5 steps "
+                         "in one CUDA graph after 2 eager ones"}
+        bt.close()
+        for Q in bplans:
+            Q.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(wl, d)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {G} groups, {wl.n_polar}x{wl.n_azim} "
-                                       f"directions, spacing h/{wl.spacing_div}, three fronts; one instance per GPU",
-                           "updates_per_step_per_gpu": info.n_updates,
+                "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, {wl.n_polar}x{wl.n_azim} "
+                                       f"directions, spacing h/{wl.spacing_div}, three fronts; one instance, its "
+                                       f"groups split over the GPUs",
+                           "updates_per_step": updates_total,
+                           "parallelism": f"groups over {ws} GPU(s): rank 0 sweeps groups {groups.start}-"
+                                          f"{groups.stop - 1}",
                            "l2": "no flush: the 5.8 GB intensity state streamed each step is ~45x L2",
                            "step": "molc_sweep_closure (FP32 sweep, moments and Eddington factors in one call)"},
                 "roofline": roofline, "roofline_step": roofline_step, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status}
+                "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "fp64_plain": fp64, "device_status": status,
+                "allgather": allgather, "batch": batch}
         print(json.dumps(line), flush=True)
     P.close()
     if ws > 1:
@@ -461,21 +509,16 @@ def run_kernel_only(args):
     P.close()
 
 
-def run_batch(args):
-    """The batched production pattern: 64 seeded uneven instances (cells per side 32-256, 8/17/32 groups, 2-4
-    polar x 16-64 azimuthal directions, spacing h/2 or h/4), autotuned plans, all instances stepped by one
-    molc_batch_sweep per step (sweep + Eddington factors), the K timed steps captured in one CUDA graph and
-    replayed once.  Compared with looping the per-instance FP32 sweep and the plain FP64 sweep over the
-    instances."""
+def batch_setup(tiled=False, autotune=True):
+    """The 64 seeded uneven instances of the batched pattern, their plans, bound arguments and the batch."""
     import torch
     import paper_2305_11998_gb300 as molc
     dev = torch.device("cuda")
     wls = synth.batch_instances(64)
     t0 = time.perf_counter()
-    plans = [molc.Plan.from_workload(wl, autotune=True) for wl in wls]
+    plans = [molc.Plan.from_workload(wl, autotune=autotune, tiled=tiled) for wl in wls]
     t_plan = time.perf_counter() - t0
-    n_upd = sum(P.info.n_updates for P in plans)
-    args_list, inputs = [], []
+    args_list = []
     for wl, P in zip(wls, plans):
         d = wl.inputs(seed=wl.extra["seed"])
         k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
@@ -483,31 +526,61 @@ def run_batch(args):
         P.intensity_init("fp32", I, B)
         f = {x: torch.empty((wl.G, wl.ncell), dtype=torch.float64, device=dev) for x in ("fxx", "fxy", "fyy")}
         args_list.append(dict(kappa=k, B=B, c=d["c"], dt=d["dt"], I=I, bnd=bnd, out=P.new_moments(dev), f=f))
-        inputs.append(d)
     batch = molc.Batch(plans)
     batch.bind(args_list)
-    for _ in range(max(args.warmup, 0)):
+    return wls, plans, args_list, batch, t_plan
+
+
+def batch_graph_ms(batch, steps, warmup, sampler=None):
+    """CUDA-event time of `steps` batched steps captured in one CUDA graph and replayed once (after `warmup`
+    eager steps)."""
+    import torch
+    for _ in range(max(warmup, 0)):
         batch.sweep()
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        for _ in range(args.steps):
+        for _ in range(steps):
             batch.sweep()
     torch.cuda.synchronize()
-    sampler = ClockSampler()
-    sampler.start()
-    time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler.mark(True)
+    if sampler:
+        sampler.mark(True)
     e0.record()
     g.replay()
     e1.record()
     torch.cuda.synchronize()
-    sampler.mark(False)
-    ms = e0.elapsed_time(e1)
+    if sampler:
+        sampler.mark(False)
+    del g
+    return e0.elapsed_time(e1)
+
+
+def batch_alg_bytes(plans):
+    """Algorithmic bytes of one batched step: every instance's FP32 state read and written (8 B per update), its
+    segment records walked by both senses, kappa and B read once, six moments and three factors written."""
+    return sum(8.0 * P.info.n_updates + 16.0 * P.info.n_track_segments + (16.0 + 72.0) * P.ncell * P.G
+               for P in plans)
+
+
+def run_batch(args):
+    """The batched production pattern: 64 seeded uneven instances (cells per side 32-256, 8/17/32 groups, 2-4
+    polar x 16-64 azimuthal directions, spacing h/2 or h/4), autotuned plans, all instances stepped by one
+    molc_batch_sweep per step (sweep + Eddington factors), the K timed steps captured in one CUDA graph and
+    replayed once.  Compared with looping the per-instance FP32 sweep and the plain FP64 sweep over the
+    instances.  --tiled: the tiled sweep's one persistent launch over the items of every instance."""
+    import torch
+    dev = torch.device("cuda")
+    wls, plans, args_list, batch, t_plan = batch_setup(tiled=args.tiled)
+    n_upd = sum(P.info.n_updates for P in plans)
+    sampler = ClockSampler()
+    sampler.start()
+    time.sleep(0.3)
+    ms = batch_graph_ms(batch, args.steps, args.warmup, sampler)
     clocks = sampler.stop()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     status = max(P.device_status() for P in plans)
     # the same steps as per-instance calls (FP32 sweep + closure per plan, no batching, no graph)
     e0.record()
@@ -522,7 +595,6 @@ def run_batch(args):
     for a in args_list:
         a["I"] = None
     batch.close()
-    del g
     torch.cuda.empty_cache()
     I64 = [P.new_intensity("fp64", dev) for P in plans]
     for P, a, I in zip(plans, args_list, I64):
@@ -543,11 +615,14 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batch64: 64 seeded uneven instances, cells per side 32-256, 8/17/32 groups, "
-                                   "2-4 x 16-64 directions, spacing h/2 or h/4",
+                                   "2-4 x 16-64 directions, spacing h/2 or h/4" + (", tiled sweep" if args.tiled else ""),
                        "updates_per_step": n_upd, "step": "molc_batch_sweep (FP32 sweep + Eddington factors), "
                                                           "K steps in one CUDA graph",
                        "state_gb": sum(P.intensity_bytes("fp32") for P in plans) / 1e9,
                        "plan_seconds_with_autotune": t_plan, "autotuned_depths": depths},
+            "roofline": {"bound": "hbm", "achieved": batch_alg_bytes(plans) * args.steps / (ms / 1e3) / 1e9,
+                         "peak": measured_peaks()[0], "unit": "GB/s",
+                         "frac": batch_alg_bytes(plans) * args.steps / (ms / 1e3) / 1e9 / measured_peaks()[0]},
             "per_instance_fp32": {"value": n_upd / (ms_loop32 / 1e3), "ms_per_step": ms_loop32},
             "fp64_plain_loop": {"value": n_upd / (ms64 / 1e3), "ms_per_step": ms64,
                                 "speedup_batch_over_fp64_loop": ms64 / (ms / args.steps)},

@@ -37,7 +37,9 @@ typedef enum {
   MOLC_ERR_OUT_OF_MEMORY = 2,    /* molc_create could not allocate the plan's device tables */
   MOLC_ERR_CUDA = 3,             /* a CUDA runtime call or kernel launch failed */
   MOLC_ERR_NONFINITE_INPUT = 4,  /* device status: kappa, B or the boundary held NaN/Inf or a negative value */
-  MOLC_ERR_TIMEOUT = 5,          /* reserved: a bounded device wait gave up */
+  MOLC_ERR_TIMEOUT = 5,          /* device status: a bounded wait of the tiled FP32 sweep gave up (an item's
+                                    upstream items or its staged data did not arrive within ~1 s); that step's
+                                    results are void */
   MOLC_ERR_INTERNAL = 6,
   MOLC_ERR_RANGE = 7             /* device status: a scaled value exceeds the range of an FP32 state (cannot
                                     happen for finite inputs: the state's power-of-two scale follows
@@ -66,6 +68,12 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 #define MOLC_BALANCE 16u    /* also evaluate the per-ray discrete balance of every sweep in FP64 (a check, not part
                                of the result; FP64 work per update, so sweeps are slower); read the largest
                                relative residual with molc_ray_balance.  Not with MOLC_FACES. */
+#define MOLC_TILED 32u      /* sweep FP32 with the tiled kernel: the characteristics cut into per-tile pieces, one
+                               persistent launch over (tile, quadrant, group tile) work items in wavefront order, the
+                               cell moments summed in shared memory (no second pass over the state).  Ignored with
+                               MOLC_FACES or MOLC_BALANCE, with more than 8 polar cosines, or when no tile keeps a work
+                               item within shared memory (molc_plan_info.fp32_tile_items == 0 then).  Same segment
+                               updates, bit for bit, as the default FP32 sweep; different moment summation order. */
 
 typedef struct {
   int nx, ny;               /* material cells (>= 1) */
@@ -117,7 +125,16 @@ typedef struct {
   int fp32_tile_groups;     /* tiled FP32 sweep: groups per work item */
   int fp32_tile_items;      /* tiled FP32 sweep: work items per step (tiles x 4 quadrants x group tiles) */
   int fp32_sweep_blocks;    /* tiled FP32 sweep: blocks of its persistent launch */
+  int fp32_block_threads;   /* tiled FP32 sweep: threads of one such block */
 } molc_plan_info;
+
+/* Configuration of a tiled FP32 sweep (no counterpart in the paper: how the sweep's work is cut for the GPU).
+ * tile_cells: tile side in cells (the characteristic pieces one work item stages in shared memory);
+ * tile_groups: groups per work item (rays per warp = 32 / tile_groups); block_threads: threads of a block of the
+ * persistent launch (a multiple of 32, at most 512).  0 in any field: the library's choice. */
+typedef struct {
+  int tile_cells, tile_groups, block_threads;
+} molc_tile_config;
 
 /* Gauss-Legendre (n_polar nodes on mu in (0,1), weights summing to 1) x Chebyshev (phi_j = (j-1/2) 2 pi / n_azim,
  * equal weights) product set, omega = 4 pi w_p / n_azim, direction order m = p * n_azim + j.  n_azim must be a
@@ -171,22 +188,26 @@ molc_status molc_sweep(molc_plan *plan, molc_precision prec, const double *kappa
 
 /* Allocation-free variant of molc_sweep (the paper has no counterpart: it is an engineering entry point).
  * Same arguments, semantics and results as molc_sweep, but the per-sweep workspace (the FP64 moment
- * accumulators and, for MOLC_FP32, the cell tables) comes from one fixed 16 MiB array compiled into the
- * library instead of from the plan.  It is meant for callers that must not allocate device memory, or must
+ * accumulators; for MOLC_FP32 the cell tables, and with a MOLC_TILED plan also the work-item flags, quadrant
+ * moment partials and the boundary buffer of the characteristic pieces) comes from one fixed 64 MiB array
+ * compiled into the library instead of from the plan.  It is meant for callers that must not allocate device memory, or must
  * know all of it in advance, once they are running: an embedding whose device memory is fully handed to
  * another allocator, or a time-stepping loop run under a fixed memory budget.  Neither this call nor its
  * set-up calls cudaMalloc, cudaFree or any other allocating routine.
  *  - Limit: the workspace is 48 bytes per (cell, group) for MOLC_FP64 (the accumulators) and 20 bytes per
- *    (cell, group) for MOLC_FP32 (the cell tables; groups padded to the plan's group chunk), each part rounded
- *    up to 256 bytes; a plan that needs more than 16 MiB (e.g. more than ~350k cell-groups in FP64, ~840k in
- *    FP32) is rejected with MOLC_ERR_INVALID_ARG and nothing is launched.  molc_sweep has no such limit.
+ *    (cell, group) for MOLC_FP32 (the cell tables; groups padded to the plan's group chunk); a MOLC_TILED plan
+ *    needs about 220 bytes per (cell, group) plus (polar cosines + 2) x 4 bytes per (characteristic piece,
+ *    group); each part is rounded up to 256 bytes.  A plan that needs more than 64 MiB (e.g. more than ~1.4M
+ *    cell-groups in FP64, ~3.3M in FP32, ~0.25M tiled) is rejected with MOLC_ERR_INVALID_ARG and nothing is
+ *    launched.  molc_sweep has no such limit.
  *  - Set-up: the first call on each device (with the plan's device current) looks up the array's device
  *    address with cudaGetSymbolAddress, which also loads the library's kernels on that device if that has
  *    not happened yet; later calls reuse the cached address.  Make that first call before any stream
  *    capture.
  *  - The FP64 accumulators must start at zero; every FP64 call clears them itself (cudaMemsetAsync on
  *    `stream`) before its kernels run, so nothing needs to be zeroed by the caller.  The FP32 cell tables are
- *    fully rewritten by every call.
+ *    fully rewritten by every call; a tiled FP32 call also clears its control words, work-item flags and
+ *    arrival counts (a few KB) before its kernels run.
  *  - There is ONE array per device, shared by every plan and stream in the process: calls that can overlap in
  *    time on the same device (different streams, or different host threads) race on it and give wrong
  *    results.  Serialise them, e.g. issue them all on one stream.
@@ -314,6 +335,14 @@ molc_status molc_tracks_export(const molc_plan *plan, int64_t *dir_ray_off, int6
 molc_status molc_kernel_timing(molc_plan *plan, int enable);
 molc_status molc_kernel_time(molc_plan *plan, double *total_ms, int *launches);
 molc_status molc_kernel_time_parts(molc_plan *plan, double *parts_ms, int *launches);
+
+/* Re-cut the tiled FP32 sweep of a plan (one created without MOLC_FACES / MOLC_BALANCE and with at most 8 polar
+ * cosines) with the given configuration, replacing its device tables (no counterpart in the paper).  The FP32
+ * intensity layout changes with the configuration: states made for the old one must be re-initialised
+ * (molc_intensity_init) or re-imported, and batches of the plan re-created.  Synchronises with the device.
+ * MOLC_ERR_INVALID_ARG if the configuration does not fit a block's shared memory (the plan then keeps the
+ * library's default configuration). */
+molc_status molc_plan_retile(molc_plan *plan, const molc_tile_config *cfg);
 
 /* FP64 fused multiply-add throughput of the current device, in FLOP/s (2 per FMA): the bound of the plain FP64
  * sweep's arithmetic (no counterpart in the paper; a measurement for the roofline).  Runs a kernel of independent

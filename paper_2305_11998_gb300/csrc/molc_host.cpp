@@ -120,6 +120,7 @@ struct molc_plan {
   TileShape tshape{};
   int np_class = 0;          // polar count the sweep kernel is compiled for (1, 2, 4, 8)
   int tgrid = 0;             // blocks of the persistent sweep launch
+  int tthreads = 256;        // threads of one of its blocks
   int64_t tstate_floats = 0;
   int64_t tn_pieces = 0;
   int n_tprep = 0;
@@ -453,7 +454,7 @@ molc_status autotune(molc_plan *p) {
 // Tiled FP32 sweep of a plan: cut its characteristic grid into per-tile pieces (tile size and groups per item
 // chosen by plan_tiles, or pinned by force_ts / force_gt), upload the tables, allocate the workspace (zeroed) and
 // fix the launch shape.  Replaces an earlier tiled build of the plan.
-molc_status build_tiled(molc_plan *p, int force_ts, int force_gt, bool *fits = nullptr) {
+molc_status build_tiled(molc_plan *p, int force_ts, int force_gt, bool *fits = nullptr, int threads = 0) {
   const int64_t T = (int64_t)p->tracks.size();
   std::vector<TileTrack> tt((size_t)T);
   for (int j = 0; j < p->n_pairs; ++j)
@@ -560,7 +561,11 @@ molc_status build_tiled(molc_plan *p, int force_ts, int force_gt, bool *fits = n
   p->n_tprep = (int)prep.size();
   p->np_class = p->n_polar <= 1 ? 1 : p->n_polar <= 2 ? 2 : p->n_polar <= 4 ? 4 : 8;
   p->tshape = tile_shape(tb, p->n_pairs, p->n_polar);
-  p->tgrid = tile_sweep_grid(p->np_class, tile_sweep_smem(p->tshape, p->np_class));
+  // block threads: as asked, else the fewer that still cover an item's (piece, group) tasks in one or two rounds
+  int max_tasks = 0;
+  for (const TileGeom &gm : tb.geoms) max_tasks = std::max(max_tasks, gm.n_pieces * tb.GT);
+  p->tthreads = threads > 0 ? threads : (max_tasks <= 2 * 128 ? 128 : 256);
+  p->tgrid = tile_sweep_grid(p->np_class, tile_sweep_smem(p->tshape, p->np_class), p->tthreads);
   return MOLC_OK;
 }
 
@@ -649,7 +654,7 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   if (groups->G < 1 || groups->G > 4096) return fail(MOLC_ERR_INVALID_ARG, "create: need 1 <= G <= 4096");
   if (!finite_pos(ray_spacing)) return fail(MOLC_ERR_INVALID_ARG, "create: ray_spacing must be > 0");
   if (layout != MOLC_RAYS_UNIFORM && layout != MOLC_RAYS_PAPER) return fail(MOLC_ERR_INVALID_ARG, "create: layout");
-  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE | MOLC_FACES | MOLC_BALANCE))
+  if (flags & ~(MOLC_AREA_RENORM | MOLC_HOST_ONLY | MOLC_AUTOTUNE | MOLC_FACES | MOLC_BALANCE | MOLC_TILED))
     return fail(MOLC_ERR_INVALID_ARG, "create: unknown flags");
   if ((flags & MOLC_BALANCE) && (flags & MOLC_FACES))
     return fail(MOLC_ERR_INVALID_ARG, "create: MOLC_BALANCE and MOLC_FACES cannot be combined");
@@ -894,9 +899,9 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   // by up to 32 lanes, and a sweep block (128 consecutive items) holds neighbouring parallel tracks of one
   // sense, which cross neighbouring cells at the same steps.  Blocks are launched longest first (block_order)
   // for load balance.
-  // FP32 plans without the face or balance reductions use the tiled sweep when a tile of one cell or more keeps a
-  // work item within shared memory; the others the bundle sweep and the moment gather below
-  p->tiled = p->n_polar <= kMaxPolarFP32 && !(flags & (MOLC_FACES | MOLC_BALANCE));
+  // MOLC_TILED plans without the face or balance reductions use the tiled sweep when a tile of one cell or more
+  // keeps a work item within shared memory; the others the bundle sweep and the moment gather below
+  p->tiled = (flags & MOLC_TILED) && p->n_polar <= kMaxPolarFP32 && !(flags & (MOLC_FACES | MOLC_BALANCE));
   if (p->tiled) {
     bool fits = true;
     const molc_status ts = build_tiled(p, 0, 0, &fits);
@@ -1179,6 +1184,7 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->fp32_tile_groups = p->tiled ? p->tv.GT : 0;
   info->fp32_tile_items = p->tiled ? p->tv.n_items : 0;
   info->fp32_sweep_blocks = p->tiled ? p->tgrid : 0;
+  info->fp32_block_threads = p->tiled ? p->tthreads : 0;
   return MOLC_OK;
 }
 
@@ -1252,7 +1258,8 @@ static cudaError_t tile_step(molc_plan *p, const SweepArgs &a, const TileView &t
   cudaError_t e = launch_tile_prep_one(ti, p->d_tinst, p->d_tprep, p->n_tprep, tv.ctrl, st);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
   if (e == cudaSuccess)
-    e = launch_tile_sweep(p->d_tinst, p->d_tqueue, tv.n_items, tv.ctrl, p->np_class, p->tshape, p->tgrid, st);
+    e = launch_tile_sweep(p->d_tinst, p->d_tqueue, tv.n_items, tv.ctrl, p->np_class, p->tshape, p->tgrid,
+                          p->tthreads, st);
   if (e == cudaSuccess && ev) {
     e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
@@ -1374,6 +1381,10 @@ molc_status molc_sweep_static_scratch(molc_plan *p, molc_precision prec, const d
     cudaError_t e = static_scratch_address(&base);
     if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: scratch address");
     tile_carve(tv, (char *)base, w);
+    // the control words, flags and counts start at zero on every call: other calls (an FP64 one, another plan's)
+    // leave other data in the array
+    e = cudaMemsetAsync(base, 0, w.ctrl + w.flags + w.cnt, st);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep_static_scratch: clear control words");
     SweepArgs a{};
     a.kappa = kappa;
     a.B = B;
@@ -1488,7 +1499,7 @@ struct molc_batch {
   int n_tprep = 0;
   int *d_ticket = nullptr;
   molc::TileShape shape{};
-  int np_max = 0, grid = 0;
+  int np_max = 0, grid = 0, threads = 0;
 };
 
 namespace {
@@ -1599,7 +1610,8 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
       batch_free(b);
       return cuda_fail(e, "batch_create");
     }
-    b->grid = tile_sweep_grid(b->np_max, tile_sweep_smem(sh, b->np_max));
+    for (int i = 0; i < n; ++i) b->threads = std::max(b->threads, plans[i]->tthreads);
+    b->grid = tile_sweep_grid(b->np_max, tile_sweep_smem(sh, b->np_max), b->threads);
     *out = b;
     return MOLC_OK;
   }
@@ -1736,7 +1748,8 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
     cudaError_t e = launch_update_scale_tiles(b->d_tinst, (int)b->plans.size(), st);
     if (e == cudaSuccess) e = launch_tile_prep(b->d_tinst, b->d_tprep, b->n_tprep, b->d_ticket, st);
     if (e == cudaSuccess)
-      e = launch_tile_sweep(b->d_tinst, b->d_tqueue, b->n_tqueue, b->d_ticket, b->np_max, b->shape, b->grid, st);
+      e = launch_tile_sweep(b->d_tinst, b->d_tqueue, b->n_tqueue, b->d_ticket, b->np_max, b->shape, b->grid,
+                            b->threads, st);
     return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "batch_sweep");
   }
   cudaError_t e = launch_update_scale_batch(b->d_inst, (int)b->plans.size(), st);
@@ -1923,6 +1936,27 @@ molc_status molc_kernel_time(molc_plan *p, double *total_ms, int *launches) {
   return s;
 }
 
+molc_status molc_plan_retile(molc_plan *p, const molc_tile_config *cfg) {
+  if (!p || !cfg) return fail(MOLC_ERR_INVALID_ARG, "plan_retile: NULL argument");
+  if (!p->tiled) return fail(MOLC_ERR_INVALID_ARG, "plan_retile: the plan has no tiled FP32 sweep");
+  if (cfg->tile_cells < 0 || cfg->tile_groups < 0 || cfg->block_threads < 0 || cfg->block_threads % 32 ||
+      cfg->block_threads > 512)
+    return fail(MOLC_ERR_INVALID_ARG, "plan_retile: bad configuration");
+  DeviceGuard dg(p->device);
+  if (!p->host_only) {
+    cudaError_t e = cudaDeviceSynchronize();   // the tables about to be replaced may be in use
+    if (e != cudaSuccess) return cuda_fail(e, "plan_retile");
+  }
+  bool fits = true;
+  const molc_status st = build_tiled(p, cfg->tile_cells, cfg->tile_groups, &fits, cfg->block_threads);
+  if (st != MOLC_OK && !fits) {   // keep a working layout: rebuild the default one
+    const std::string msg = g_last_error;
+    if (build_tiled(p, 0, 0) != MOLC_OK) return fail(MOLC_ERR_INTERNAL, "plan_retile: %s", msg.c_str());
+    return fail(MOLC_ERR_INVALID_ARG, "%s", msg.c_str());
+  }
+  return st;
+}
+
 molc_status molc_fp64_fma_rate(double *flops_per_s) {
   if (!flops_per_s) return fail(MOLC_ERR_INVALID_ARG, "fp64_fma_rate: NULL argument");
   cudaError_t e = fp64_fma_rate(flops_per_s);
@@ -1938,7 +1972,10 @@ molc_status molc_device_status(molc_plan *p, int *code) {
   if (e != cudaSuccess) return cuda_fail(e, "device_status");
   e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "device_status");
-  *code = (h & kStatusNonfinite) ? MOLC_ERR_NONFINITE_INPUT : (h & kStatusRange) ? MOLC_ERR_RANGE : MOLC_OK;
+  *code = (h & kStatusNonfinite) ? MOLC_ERR_NONFINITE_INPUT
+          : (h & kStatusRange)   ? MOLC_ERR_RANGE
+          : (h & kStatusTimeout) ? MOLC_ERR_TIMEOUT
+                                 : MOLC_OK;
   return MOLC_OK;
 }
 

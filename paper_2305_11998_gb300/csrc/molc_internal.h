@@ -204,7 +204,7 @@ cudaError_t fp64_fma_rate(double *flops_per_s);
 // tiles.  The item's previous-step state and cell table are staged in shared memory; its cell moments are summed
 // there, per quadrant, and the four quadrant partials of a (tile, group tile) are combined by whichever item of
 // the four finishes last.
-constexpr int kTileThreads = 256;                 // threads of a tiled-sweep block
+constexpr int kTileThreadCandidates[] = {128, 256};   // threads of a tiled-sweep block (autotuned)
 constexpr int kTileStateBytes = 88 * 1024;        // largest item state staged in shared memory
 constexpr int kTileUnitEntries = 64;              // moment entries one thread sums (longer cell lists are split)
 constexpr int kTileMaxUnits = 512;                // moment units of one item (shared-memory partials)
@@ -273,9 +273,10 @@ cudaError_t launch_tile_prep_one(const TileInst &ov, TileInst *dst, const int4 *
 // batched FP32 state scale update over tiled instances
 cudaError_t launch_update_scale_tiles(const TileInst *inst, int n, cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
-                              const TileShape &shape, int grid, cudaStream_t st);
+                              const TileShape &shape, int grid, int threads, cudaStream_t st);
 size_t tile_sweep_smem(const TileShape &shape, int np_max);
-int tile_sweep_grid(int np_max, size_t smem);
+// blocks of a persistent sweep launch: SMs x the blocks of `threads` threads and `smem` bytes one SM holds
+int tile_sweep_grid(int np_max, size_t smem, int threads);
 cudaError_t launch_tile_intensity_copy(const PlanView &v, const TileView &t, const int4 *tpiece,
                                        const int64_t *tpiece_off, float *I, const double *Bref,
                                        const double *scale, int g_begin, int g_count, double *canon, bool to_canon,

@@ -1496,10 +1496,12 @@ __host__ __device__ inline TileSmem tile_smem_layout(int max_item_floats, int TS
   return m;
 }
 
-// Bounded spin of one thread on a flag reaching `epoch`; false (and the status recorded) if it gave up.
+// Bounded spin of one thread on a flag reaching `epoch`; false (and the status recorded) if it gave up.  Once a
+// wait of the plan has given up, later ones do not wait at all (the step's results are void anyway).
 __device__ bool wait_flag(const int *flag, int epoch, int *status) {
   for (int it = 0; it < kTileWaitLimit; ++it) {
     if (ld_acquire_gpu(flag) >= epoch) return true;
+    if ((it & 255) == 255 && (*(volatile int *)status & kStatusTimeout)) return false;
     __nanosleep(it < 64 ? 32 : 256);
   }
   atomicOr(status, kStatusTimeout);
@@ -1585,31 +1587,39 @@ __device__ __forceinline__ void tile_unit_sums(const TileView &t, const TileGeom
     two_sum_add(hi[5], lo[5], (sf * sf) * P2);
   };
   const int2 *ent = t.ents + gm.ent_off;
-  for (int e = e0; e < e1; ++e) {
-    const int2 en = __ldg(ent + e);
-    const int slot = en.x & 0xFFFFFF, pr = (int)((unsigned)en.x >> 24);
-    if (pr != cur || run == kPairRun) {
-      flush();
-      cur = pr;
-      run = 0;
-      P0 = P1 = P2 = 0.f;
-    }
-    ++run;
-    const float *dv = sst + ((int64_t)slot * gcnt + gl) * np;
-    const float *c0 = dirt + pr * dstride;
-    float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+  constexpr int kBatch = 8;   // entries loaded together (their L2 latencies overlap)
+  for (int eb = e0; eb < e1; eb += kBatch) {
+    int2 enb[kBatch];
 #pragma unroll
-    for (int p = 0; p < NPM; ++p)
-      if (EXACT || p < np) {
-        const float x = dv[p];
-        S0 = fmaf(c0[p], x, S0);
-        S1 = fmaf(c0[np + p], x, S1);
-        S2 = fmaf(c0[2 * np + p], x, S2);
+    for (int b = 0; b < kBatch; ++b) enb[b] = eb + b < e1 ? __ldg(ent + eb + b) : make_int2(0, 0);
+#pragma unroll
+    for (int b = 0; b < kBatch; ++b) {
+      if (eb + b >= e1) break;
+      const int2 en = enb[b];
+      const int slot = en.x & 0xFFFFFF, pr = (int)((unsigned)en.x >> 24);
+      if (pr != cur || run == kPairRun) {
+        flush();
+        cur = pr;
+        run = 0;
+        P0 = P1 = P2 = 0.f;
       }
-    const float af = __int_as_float(en.y);
-    P0 = fmaf(af, S0, P0);
-    P1 = fmaf(af, S1, P1);
-    P2 = fmaf(af, S2, P2);
+      ++run;
+      const float *dv = sst + ((int64_t)slot * gcnt + gl) * np;
+      const float *c0 = dirt + pr * dstride;
+      float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+#pragma unroll
+      for (int p = 0; p < NPM; ++p)
+        if (EXACT || p < np) {
+          const float x = dv[p];
+          S0 = fmaf(c0[p], x, S0);
+          S1 = fmaf(c0[np + p], x, S1);
+          S2 = fmaf(c0[2 * np + p], x, S2);
+        }
+      const float af = __int_as_float(en.y);
+      P0 = fmaf(af, S0, P0);
+      P1 = fmaf(af, S1, P1);
+      P2 = fmaf(af, S2, P2);
+    }
   }
   flush();
 #pragma unroll
@@ -1636,11 +1646,17 @@ __global__ void __launch_bounds__(512) tile_sweep_kernel(const TileInst *inst, c
   __syncthreads();
   unsigned phase = 0;
   bool stored = false;   // a bulk store of this block may still be reading shared memory
+  int next_q = 0;        // thread 0: the ticket taken for the next item while this one runs
+  if (tid == 0) next_q = atomicAdd(ticket, 1);
   for (;;) {
-    if (tid == 0) s_q = atomicAdd(ticket, 1);
+    if (tid == 0) s_q = next_q;
     __syncthreads();
     const int qi = s_q;
     if (qi >= n_queue) break;
+    // Take the next ticket now (its latency overlaps this item).  Still no block waits on one that has not
+    // started: the smallest unfinished ticket is either some block's current item (its upstream items hold
+    // smaller tickets, all finished) or a block's next item whose current item, smaller still, is unfinished.
+    if (tid == 0) next_q = atomicAdd(ticket, 1);
     const int2 qe = queue[qi];
     const TileInst &I = inst[qe.x];
     const PlanView &v = I.v;
@@ -1691,14 +1707,20 @@ __global__ void __launch_bounds__(512) tile_sweep_kernel(const TileInst *inst, c
       if (gm.up_x >= 0) wait_flag(t.flags + base + gm.up_x, epoch, v.status);
       if (gm.up_y >= 0) wait_flag(t.flags + base + gm.up_y, epoch, v.status);
       int it = 0;
-      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) __nanosleep(32);
+      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) {
+        if ((it & 255) == 0 && (*(volatile int *)v.status & kStatusTimeout)) break;   // the step is void already
+        __nanosleep(32);
+      }
       if (it >= kTileWaitLimit) atomicOr(v.status, kStatusTimeout);
     }
     __syncthreads();
     // all threads observe the completed phase (the copies' data is visible to them after this wait)
     {
       int it = 0;
-      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) __nanosleep(32);
+      while (!mbar_try_wait(&bar, phase) && ++it < kTileWaitLimit) {
+        if ((it & 255) == 0 && (*(volatile int *)v.status & kStatusTimeout)) break;
+        __nanosleep(32);
+      }
     }
     phase ^= 1;
     // 2. walk the pieces
@@ -1925,17 +1947,29 @@ __global__ void tile_intensity_copy_kernel(PlanView v, TileView t, const int4 *t
   }
 }
 
+// Allow a kernel the device's largest dynamic shared memory (the opt-in limit less its static shared memory).
+cudaError_t allow_max_dynamic_smem(const void *fn) {
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) cudaGetLastError();   // do not leave the error for a later launch check
+  return e;
+}
+
 template <int NPM, bool EXACT>
 cudaError_t launch_tile_np(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, const TileSmem &lay,
-                           int grid, cudaStream_t st) {
-  static bool attr = false;   // allow the largest dynamic shared memory once per instantiation
+                           int grid, int threads, cudaStream_t st) {
+  static bool attr = false;   // once per instantiation
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tile_sweep_kernel<NPM, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         227 * 1024);
+    cudaError_t e = allow_max_dynamic_smem((const void *)tile_sweep_kernel<NPM, EXACT>);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  tile_sweep_kernel<NPM, EXACT><<<grid, kTileThreads, lay.total, st>>>(inst, queue, n_queue, ticket, lay);
+  tile_sweep_kernel<NPM, EXACT><<<grid, threads, lay.total, st>>>(inst, queue, n_queue, ticket, lay);
   return cudaGetLastError();
 }
 
@@ -1964,31 +1998,34 @@ cudaError_t launch_tile_prep_one(const TileInst &ov, TileInst *dst, const int4 *
 }
 
 cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
-                              const TileShape &sh, int grid, cudaStream_t st) {
+                              const TileShape &sh, int grid, int threads, cudaStream_t st) {
   const TileSmem lay = tile_smem_layout(sh.max_item_floats, sh.cd_entries, 1, sh.max_len, sh.n_pairs, np_max,
                                         sh.split_units);
   const bool exact = sh.np_exact == np_max;
   switch (np_max) {
-    case 1: return exact ? launch_tile_np<1, true>(inst, queue, n_queue, ticket, lay, grid, st)
-                         : launch_tile_np<1, false>(inst, queue, n_queue, ticket, lay, grid, st);
-    case 2: return exact ? launch_tile_np<2, true>(inst, queue, n_queue, ticket, lay, grid, st)
-                         : launch_tile_np<2, false>(inst, queue, n_queue, ticket, lay, grid, st);
-    case 3: case 4: return exact && np_max == 4 ? launch_tile_np<4, true>(inst, queue, n_queue, ticket, lay, grid, st)
-                                                : launch_tile_np<4, false>(inst, queue, n_queue, ticket, lay, grid, st);
-    default: return exact && np_max == 8 ? launch_tile_np<8, true>(inst, queue, n_queue, ticket, lay, grid, st)
-                                         : launch_tile_np<8, false>(inst, queue, n_queue, ticket, lay, grid, st);
+    case 1: return exact ? launch_tile_np<1, true>(inst, queue, n_queue, ticket, lay, grid, threads, st)
+                         : launch_tile_np<1, false>(inst, queue, n_queue, ticket, lay, grid, threads, st);
+    case 2: return exact ? launch_tile_np<2, true>(inst, queue, n_queue, ticket, lay, grid, threads, st)
+                         : launch_tile_np<2, false>(inst, queue, n_queue, ticket, lay, grid, threads, st);
+    case 3: case 4: return exact && np_max == 4 ? launch_tile_np<4, true>(inst, queue, n_queue, ticket, lay, grid, threads, st)
+                                                : launch_tile_np<4, false>(inst, queue, n_queue, ticket, lay, grid, threads, st);
+    default: return exact && np_max == 8 ? launch_tile_np<8, true>(inst, queue, n_queue, ticket, lay, grid, threads, st)
+                                         : launch_tile_np<8, false>(inst, queue, n_queue, ticket, lay, grid, threads, st);
   }
 }
 
-int tile_sweep_grid(int np_max, size_t smem) {
+int tile_sweep_grid(int np_max, size_t smem, int threads) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const void *fn = np_max <= 1 ? (const void *)tile_sweep_kernel<1, true>
                  : np_max <= 2 ? (const void *)tile_sweep_kernel<2, true>
                  : np_max <= 4 ? (const void *)tile_sweep_kernel<4, true> : (const void *)tile_sweep_kernel<8, true>;
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kTileThreads, smem) != cudaSuccess || per < 1) per = 1;
+  allow_max_dynamic_smem(fn);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
   return sms * per;
 }
 

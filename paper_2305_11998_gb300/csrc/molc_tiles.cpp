@@ -395,7 +395,7 @@ bool plan_tiles(const TilePlanInput &in, TileTables &t, std::string &why, int fo
       if ((size_t)slots * std::min(GT, in.G) * np * sizeof(float) > budget) continue;
       if (!build(in, TS, GT, qp, t, why)) return false;
       if ((int64_t)t.max_split_units * t.GT > kTileMaxUnits) continue;
-      if (tile_smem_bytes(t, in.n_pairs, np) > 227 * 1024) continue;
+      if (tile_smem_bytes(t, in.n_pairs, np) > 224 * 1024) continue;   // below the opt-in limit of a block
       return check_tiles(in, t, why);
     }
   }

@@ -1,9 +1,11 @@
-"""Host-side logic of the multi-GPU runs: one process per GPU, independent problems per rank.
+"""Host-side logic of the multi-GPU runs: one process per GPU, one instance split by contiguous group ranges.
 
-The sweep shards by independent problems: every group (and every whole instance) is swept without data from
-any other, so ranks never exchange data on the path.  The only collectives are the timing ones: a barrier
-around the timed region and the maximum of the per-rank times.  Works with any torch.distributed backend
-(NCCL on GPUs, gloo on CPU for the tests).
+The sweep shards by groups: every group is swept without data from any other (kappa_g, B_g, its boundary values,
+its intensity state and its moments touch no other group), so ranks never exchange data on the path.  A rank
+builds a plan over its own group range on the full characteristic grid and sweeps the group slices of the inputs.
+The collectives are the timing ones (a barrier around the timed region, the maximum of the per-rank times) and,
+for a consumer that needs every group on every GPU (the grey closure), an all-gather of the per-group results.
+Works with any torch.distributed backend (NCCL on GPUs, gloo on CPU for the tests).
 """
 from __future__ import annotations
 
@@ -31,6 +33,36 @@ def shard_groups(G: int, world: int, rank: int) -> range:
     return range(g0, g0 + q + (1 if rank < r else 0))
 
 
+def shard_inputs(d: dict, groups: range) -> dict:
+    """The group slices of a workload's inputs for one shard: kappa and B rows [g0, g1) of [G][cell], the boundary
+    columns [g0, g1) of [4][G] (copied contiguous); c and dt as they are."""
+    import numpy as np
+    g0, g1 = groups.start, groups.stop
+    out = dict(d)
+    out["kappa"] = np.ascontiguousarray(d["kappa"][g0:g1])
+    out["B"] = np.ascontiguousarray(d["B"][g0:g1])
+    out["bnd"] = np.ascontiguousarray(d["bnd"][:, g0:g1])
+    return out
+
+
+def gather_groups(local, G: int, groups: range, world: int, device=None):
+    """All-gather of a per-group array [g1 - g0][n] from every rank into the full [G][n] on every rank (ranks hold
+    contiguous, ordered group ranges of sizes differing by at most one: each contribution is padded to the largest
+    range for the collective)."""
+    import torch
+    import torch.distributed as dist
+    if world == 1:
+        return local
+    n = local.shape[1]
+    q, r = divmod(G, world)
+    rows = q + (1 if r else 0)
+    buf = torch.zeros((rows, n), dtype=local.dtype, device=local.device)
+    buf[: local.shape[0]] = local
+    parts = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(parts, buf)
+    return torch.cat([parts[k][: len(shard_groups(G, world, k))] for k in range(world)], 0)
+
+
 def max_over_ranks(value: float, device=None) -> float:
     """Maximum of a per-rank scalar (the timed region's duration) over all ranks; the value itself when not
     distributed."""
@@ -44,5 +76,6 @@ def max_over_ranks(value: float, device=None) -> float:
 
 
 def weak_scaling_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
-    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    """Whole-job throughput when every rank processes the same units: all ranks' units over the slowest rank's
+    time."""
     return units_per_rank * world / seconds_max

@@ -21,6 +21,7 @@ HOST_ONLY = 2
 AUTOTUNE = 4
 FACES = 8
 BALANCE = 16
+TILED = 32
 PREC = {"fp64": FP64, "fp32": FP32, FP64: FP64, FP32: FP32}
 LAYOUT = {"uniform": RAYS_UNIFORM, "paper": RAYS_PAPER, RAYS_UNIFORM: RAYS_UNIFORM, RAYS_PAPER: RAYS_PAPER}
 STATUS = {0: "MOLC_OK", 1: "MOLC_ERR_INVALID_ARG", 2: "MOLC_ERR_OUT_OF_MEMORY", 3: "MOLC_ERR_CUDA",
@@ -34,7 +35,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
             "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure",
-            "molc_ray_balance", "molc_fp64_fma_rate")
+            "molc_ray_balance", "molc_fp64_fma_rate", "molc_plan_retile")
 
 
 class MolcError(RuntimeError):
@@ -67,7 +68,11 @@ class _Info(C.Structure):
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
                 ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int),
                 ("n_split_cells", C.c_int), ("fp32_tile_cells", C.c_int), ("fp32_tile_groups", C.c_int),
-                ("fp32_tile_items", C.c_int), ("fp32_sweep_blocks", C.c_int)]
+                ("fp32_tile_items", C.c_int), ("fp32_sweep_blocks", C.c_int), ("fp32_block_threads", C.c_int)]
+
+
+class _TileConfig(C.Structure):
+    _fields_ = [("tile_cells", C.c_int), ("tile_groups", C.c_int), ("block_threads", C.c_int)]
 
 
 class _SweepArgs(C.Structure):
@@ -114,6 +119,7 @@ def load(build_if_needed: bool = True):
         "molc_kernel_time_parts": (C.c_int, [vp, C.POINTER(C.c_double), ip]),
         "molc_device_status": (C.c_int, [vp, ip]),
         "molc_fp64_fma_rate": (C.c_int, [dp]),
+        "molc_plan_retile": (C.c_int, [vp, C.POINTER(_TileConfig)]),
         "molc_last_error": (C.c_char_p, []),
         "molc_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
         "molc_batch_bind": (C.c_int, [vp, C.POINTER(_SweepArgs)]),
@@ -194,13 +200,15 @@ class PlanInfo:
     fp32_tile_groups: int
     fp32_tile_items: int
     fp32_sweep_blocks: int
+    fp32_block_threads: int
 
 
 class Plan:
     """molc_create / molc_sweep / molc_closure on torch tensors (float64, CUDA, contiguous)."""
 
     def __init__(self, nx, ny, lx, ly, mu, cos_phi, sin_phi, w, G, spacing, layout="uniform", renorm=True,
-                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False, faces=False, balance=False):
+                 x0=0.0, y0=0.0, edges=None, host_only=False, autotune=False, faces=False, balance=False,
+                 tiled=False):
         lib = load()
         self._lib = lib
         self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu, cos_phi, sin_phi, w)]
@@ -212,7 +220,7 @@ class Plan:
         _check(lib.molc_create(C.byref(grid), C.byref(quad), C.byref(groups), float(spacing), LAYOUT[layout],
                                (AREA_RENORM if renorm else 0) | (HOST_ONLY if host_only else 0) |
                                (AUTOTUNE if autotune else 0) | (FACES if faces else 0) |
-                               (BALANCE if balance else 0), C.byref(h)))
+                               (BALANCE if balance else 0) | (TILED if tiled else 0), C.byref(h)))
         self._h = h
         inf = _Info()
         _check(lib.molc_plan_get_info(h, C.byref(inf)))
@@ -222,11 +230,26 @@ class Plan:
 
     @classmethod
     def from_workload(cls, wl, quad=None, spacing=None, layout="uniform", renorm=True, host_only=False,
-                      autotune=False, faces=False, balance=False):
+                      autotune=False, faces=False, balance=False, tiled=False, groups=None):
+        """A plan for a synth.Workload; `groups` (a range) builds it over that contiguous group range only (a shard
+        of the instance: the same characteristic grid, those groups' edges)."""
         q = quad if quad is not None else wl.quadrature()
-        return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G,
-                   wl.spacing if spacing is None else spacing, layout, renorm, edges=wl.edges(), host_only=host_only,
-                   autotune=autotune, faces=faces, balance=balance)
+        edges = wl.edges()
+        G = wl.G
+        if groups is not None:
+            edges = edges[groups.start: groups.stop + 1]
+            G = len(groups)
+        return cls(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, G,
+                   wl.spacing if spacing is None else spacing, layout, renorm, edges=edges, host_only=host_only,
+                   autotune=autotune, faces=faces, balance=balance, tiled=tiled)
+
+    def retile(self, tile_cells=0, tile_groups=0, block_threads=0):
+        """molc_plan_retile: re-cut the tiled FP32 sweep (FP32 states must be re-initialised afterwards)."""
+        cfg = _TileConfig(int(tile_cells), int(tile_groups), int(block_threads))
+        _check(self._lib.molc_plan_retile(self._h, C.byref(cfg)))
+        inf = _Info()
+        _check(self._lib.molc_plan_get_info(self._h, C.byref(inf)))
+        self.info = PlanInfo(**{k: getattr(inf, k) for k, _ in _Info._fields_})
 
     def close(self):
         if getattr(self, "_h", None):

@@ -89,7 +89,7 @@ def test_invalid_arguments_are_rejected():
 
 @pytest.mark.parametrize("fine", [False, True])
 def test_split_cell_count_follows_the_entry_lists(fine):
-    # the moment gather of the bundle sweep (plans that are not tiled: here MOLC_BALANCE): a cell's gather list holds
+    # the moment gather of the bundle sweep (the default FP32 sweep; also with MOLC_BALANCE): a cell's gather list holds
     # one entry per (track segment, sense) crossing it, padded to a multiple of 4; lists longer than 256 entries are
     # summed in parts (n_split_cells)
     wl = synth.Workload("paper8", 8, 8, 6.0, 17, 0.001, 100.0, 2, 16, 40, 1)

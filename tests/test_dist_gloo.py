@@ -1,8 +1,9 @@
 """Multi-rank host logic on CPU: two gloo ranks on 127.0.0.1.
 
-The sweep shards by independent problems (groups, or whole instances per rank) with no data exchange; these
-tests check the host side of that: the timing collective (max over ranks), the whole-job rate, the group
-shards, and that sweeping group shards on separate ranks reproduces the unsharded sweep exactly (oracle, CPU).
+The sweep shards by groups (one instance split into contiguous group ranges, one per rank) with no data exchange
+on the path; these tests check the host side of that: the timing collective (max over ranks), the group shards
+and the slices of the inputs, that sweeping group shards on separate ranks reproduces the unsharded sweep exactly
+(oracle, CPU), and the all-gather that hands every rank all groups' results.
 """
 import os
 import socket
@@ -43,7 +44,9 @@ def _rank_main(rank, world, port, out_dir):
         groups = list(pdist.shard_groups(wl.G, ws, rk))
         r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="double",
                          want_I=False, threads=1)
-        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), t=t, groups=np.array(groups),
+        # all-gather of the per-group results into every rank (the grey closure's consumer of all groups)
+        gathered = pdist.gather_groups(torch.tensor(r["E"]), wl.G, pdist.shard_groups(wl.G, ws, rk), ws)
+        np.savez(os.path.join(out_dir, f"rank{rank}.npz"), t=t, groups=np.array(groups), gathered=gathered.numpy(),
                  **{k: r[k] for k in ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy")})
         dist.barrier()
     finally:
@@ -68,6 +71,7 @@ def test_two_gloo_ranks_shard_groups_and_reduce_time(tmp_path):
         g = x["groups"]
         for k in ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy"):
             assert np.array_equal(x[k], full[k][g]), k     # groups are independent: bit-identical
+        assert np.array_equal(x["gathered"], full["E"])   # every rank ends with all groups
 
 
 def test_shard_groups_cover_and_balance():
@@ -85,3 +89,12 @@ def test_weak_scaling_rate_and_local_reduction():
     assert pdist.weak_scaling_rate(1.0e9, 4, 2.0) == 2.0e9
     assert pdist.max_over_ranks(3.5) == 3.5      # not distributed: the value itself
     assert pdist.instance_seed(0, 3) == 3
+
+
+def test_shard_inputs_slice_groups():
+    import synth
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(0)
+    s = pdist.shard_inputs(d, range(1, 3))
+    assert np.array_equal(s["kappa"], d["kappa"][1:3]) and np.array_equal(s["B"], d["B"][1:3])
+    assert s["bnd"].shape == (4, 2) and s["bnd"].flags["C_CONTIGUOUS"] and np.array_equal(s["bnd"], d["bnd"][:, 1:3])

@@ -36,17 +36,24 @@ def test_ray_balance_holds_and_changes_nothing(molc, prec, tol, name, layout):
     wl = synth.WORKLOADS[name]
     spacing = wl.spacing if layout == "uniform" else wl.h / 1.5
     kw = dict(spacing=spacing, layout=layout, renorm=(layout == "uniform"))
+    # the check's plan, a plan with the face reductions and a plain plan sweep with the bundle FP32 kernel: the
+    # extra reductions must change nothing; the tiled plan makes the same segment updates
     P = molc.Plan.from_workload(wl, balance=True, **kw)
     R = molc.Plan.from_workload(wl, **kw)
+    T = molc.Plan.from_workload(wl, tiled=True, **kw)
     d = wl.inputs(1)
     k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
     I_p, I_r = P.new_intensity(prec).zero_(), R.new_intensity(prec).zero_()
+    I_t = T.new_intensity(prec)
     P.intensity_init(prec, I_p, B)
     R.intensity_init(prec, I_r, B)
+    T.intensity_init(prec, I_t, B)
     assert P.ray_balance() == 0.0
     for step in range(3):
         got = P.sweep(prec, k, B, d["c"], d["dt"], I_p, bnd)
         ref = R.sweep(prec, k, B, d["c"], d["dt"], I_r, bnd)
+        T.sweep(prec, k, B, d["c"], d["dt"], I_t, bnd)
+        assert torch.equal(P.intensity_export(prec, I_p), T.intensity_export(prec, I_t))   # same segment updates
         torch.cuda.synchronize()
         rel = P.ray_balance()
         assert 0.0 <= rel <= tol, (step, rel)
@@ -62,9 +69,10 @@ def test_ray_balance_holds_and_changes_nothing(molc, prec, tol, name, layout):
                     np.maximum(cE, 1e-30 * cE.max())
                 assert np.max(np.abs(a - b) / den) <= 1e-12, kk
         assert torch.equal(I_p, I_r)
-    assert P.device_status() == 0
+    assert P.device_status() == 0 and T.device_status() == 0
     P.close()
     R.close()
+    T.close()
 
 
 def test_ray_balance_needs_the_flag_and_stays_out_of_batches(molc):

@@ -30,12 +30,12 @@ SHAPES = [(16, 4, 2, 16, 2), (24, 17, 3, 24, 4), (32, 8, 4, 32, 2), (12, 32, 2, 
           (8, 17, 3, 8, 2)]
 
 
-def make_instances(molc, autotune=False):
+def make_instances(molc, autotune=False, tiled=False):
     out = []
     for i, (n, G, npol, naz, div) in enumerate(SHAPES):
         wl = synth.Workload(f"b{i}", n, n, 6.0, G, 0.001, 100.0, npol, naz, div, 1)
         d = wl.inputs(10 + i)
-        P = molc.Plan.from_workload(wl, autotune=autotune)
+        P = molc.Plan.from_workload(wl, autotune=autotune, tiled=tiled)
         out.append((wl, d, P))
     return out
 
@@ -67,8 +67,12 @@ def assert_same(a, b):
             assert torch.equal(a["f"][k], b["f"][k]), k
 
 
-def test_batch_matches_per_instance(molc):
-    inst = make_instances(molc)
+@pytest.mark.parametrize("tiled", [False, True])
+def test_batch_matches_per_instance(molc, tiled):
+    """Bit for bit: the bundle kernels (one launch per class) or the tiled sweep (one persistent launch over the
+    items of every instance, the longest wavefronts first)."""
+    inst = make_instances(molc, tiled=tiled)
+    assert all((P.info.fp32_tile_items > 0) == tiled for _, _, P in inst)
     ref = [new_args(P, wl, d, closure=(i % 2 == 0)) for i, (wl, d, P) in enumerate(inst)]
     got = [new_args(P, wl, d, closure=(i % 2 == 0)) for i, (wl, d, P) in enumerate(inst)]
     batch = molc.Batch([P for _, _, P in inst])

@@ -33,8 +33,14 @@ def plans(molc):
     yield "g37", wl, molc.Plan.from_workload(wl)
     wl = synth.Workload("paper8", 8, 8, 6.0, 17, 0.001, 100.0, 2, 16, 40, 1)
     q = wl.quadrature()
-    yield "paper8", wl, molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, 0.02, "paper",
-                                  False)
+    # tiled: ~270 moment entries per cell and quadrant, summed in parts of 64
+    yield "paper8_tiled", wl, molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, 0.02,
+                                        "paper", False, tiled=True)
+    # the bundle sweep: ~1100 entries per cell in the moment gather, parts of 256
+    yield "paper8_bundle", wl, molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, 0.02,
+                                         "paper", False)
+    yield "fc64_tiled", synth.WORKLOADS["fc64_g17_d128"], molc.Plan.from_workload(synth.WORKLOADS["fc64_g17_d128"],
+                                                                                   tiled=True)
 
 
 def close(a, b, c):
@@ -50,7 +56,7 @@ def close(a, b, c):
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_sweep_closure_matches_sweep_then_closure(molc, prec):
     for name, wl, P in plans(molc):
-        if name == "paper8":   # split cell lists: ~1100 segment entries per cell, parts of 256
+        if name == "paper8_bundle":   # split cell lists: ~1100 segment entries per cell, parts of 256
             assert P.info.n_split_cells == wl.ncell
         d = wl.inputs(5)
         k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])

@@ -1,5 +1,5 @@
-"""CPU: the tiled FP32 layout of the characteristic grid (Sec. 3) is built and checked by the library's planner on
-host-only plans of every shape the GPU tests sweep.  Plan creation fails unless every invariant the tiled kernels
+"""CPU: the tiled FP32 layout of the characteristic grid (Sec. 3, MOLC_TILED) is built and checked by the library's
+planner on host-only plans of every shape the GPU tests sweep.  Plan creation fails unless every invariant the tiled kernels
 rely on holds (each segment of each sense one record with its cell and length, pieces chained in traversal order
 through adjacent tiles along their direction and later in the quadrant's wavefront, moment entries covering every
 slot once in its record's cell, the work queue topologically ordered, item states disjoint)."""
@@ -35,7 +35,7 @@ def test_tiled_layout_of_variants(molc, vi):
     h = min(Lx / v["nx"], Ly / v["ny"])
     layout = v.get("layout", "uniform")
     P = molc.Plan(v["nx"], v["ny"], Lx, Ly, q.mu, q.cos_phi, q.sin_phi, q.w, v["G"], h / v["div"], layout,
-                  v.get("renorm", layout == "uniform"), host_only=True)
+                  v.get("renorm", layout == "uniform"), host_only=True, tiled=True)
     i = P.info
     assert i.fp32_tile_cells >= 1 and i.fp32_tile_groups >= 1
     n_tiles = -(-v["nx"] // i.fp32_tile_cells) * -(-v["ny"] // i.fp32_tile_cells)
@@ -45,7 +45,7 @@ def test_tiled_layout_of_variants(molc, vi):
 
 @pytest.mark.parametrize("name", ["fc16_g4_d32", "fc64_g17_d128"])
 def test_tiled_layout_of_workloads(molc, name):
-    P = molc.Plan.from_workload(synth.WORKLOADS[name], host_only=True)
+    P = molc.Plan.from_workload(synth.WORKLOADS[name], host_only=True, tiled=True)
     assert P.info.fp32_tile_items > 0
     P.close()
 
@@ -56,14 +56,14 @@ def test_paper_production_spacing_keeps_the_bundle_sweep(molc):
     wl = synth.Workload("fc10_paper", 10, 10, 6.0, 17, 0.001, 100.0, 4, 36, 600, 1)
     q = wl.quadrature()
     P = molc.Plan(wl.nx, wl.ny, wl.L, wl.L, q.mu, q.cos_phi, q.sin_phi, q.w, wl.G, 1e-3, "paper", False,
-                  host_only=True)
+                  host_only=True, tiled=True)
     assert P.info.fp32_tile_items == 0 and P.info.n_split_cells > 0
     P.close()
 
 
 def test_faces_and_balance_plans_are_not_tiled(molc):
     wl = synth.WORKLOADS["fc16_g4_d32"]
-    for kw in ({"faces": True}, {"balance": True}):
-        P = molc.Plan.from_workload(wl, host_only=True, **kw)
+    for kw in ({"faces": True}, {"balance": True}, {}):
+        P = molc.Plan.from_workload(wl, host_only=True, tiled=bool(kw), **kw)
         assert P.info.fp32_tile_cells == 0
         P.close()

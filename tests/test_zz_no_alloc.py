@@ -2,7 +2,8 @@
 
 Collected last (file name) so that it also runs after every other GPU test in the same process; it must pass
 alone in a fresh process as well.  Both entry points run the same kernels on the same inputs, so the carried
-intensity states must agree bit for bit; the moments differ at most by the order of FP64 additions.  After the
+intensity states must agree bit for bit; the moments differ at most by the order of FP64 additions (the FP64
+path's atomics; the FP32 sweep's sums are deterministic).  After the
 first call (which looks the array up), further calls must leave the device's free memory unchanged.
 """
 import numpy as np
@@ -44,11 +45,12 @@ def free_bytes():
     return torch.cuda.mem_get_info()[0]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_static_scratch_matches_sweep_two_calls_in_a_row(molc, prec):
+@pytest.mark.parametrize("prec,tiled", [("fp64", False), ("fp32", False), ("fp32", True)])
+def test_static_scratch_matches_sweep_two_calls_in_a_row(molc, prec, tiled):
     wl = synth.WORKLOADS["fc64_g17_d128"]      # 64^2 x 17 groups: within the array's size
     d = wl.inputs(2)
-    P = molc.Plan.from_workload(wl)
+    P = molc.Plan.from_workload(wl, tiled=tiled)
+    assert (P.info.fp32_tile_items > 0) == tiled
     k, B, bnd = dev(d["kappa"]), dev(d["B"]), dev(d["bnd"])
     I_ref = P.new_intensity(prec).zero_()     # zeroed so the padding bytes compare equal too
     I_new = P.new_intensity(prec).zero_()
@@ -117,13 +119,14 @@ def test_static_scratch_ray_balance(molc, prec):
     P.close()
 
 
-@pytest.mark.parametrize("prec,n", [("fp64", 256), ("fp32", 224)])
-def test_static_scratch_rejects_plans_beyond_its_size(molc, prec, n):
-    # FP64: 256^2 cells x 17 groups need 53 MB of accumulators; FP32: 224^2 x 17 cell-groups need 17.06 MB of cell
-    # tables (20 B each), just above the 16 MiB array.  Rejected on the host, nothing launched.
+@pytest.mark.parametrize("prec,n,tiled", [("fp64", 384, False), ("fp32", 512, False), ("fp32", 224, True)])
+def test_static_scratch_rejects_plans_beyond_its_size(molc, prec, n, tiled):
+    # FP64: 384^2 cells x 17 groups need 120 MB of accumulators; FP32: 512^2 x 17 cell-groups need 89 MB of cell
+    # tables (20 B each); tiled FP32: 224^2 x 17 cell-groups need ~0.2 GB of cell tables, quadrant partials and
+    # boundary buffer; all above the 64 MiB array.  Rejected on the host, nothing launched.
     wl = synth.Workload("big", n, n, 6.0, 17, 0.001, 100.0, 2, 8, 2, 1)
     d = wl.inputs(0)
-    P = molc.Plan.from_workload(wl)
+    P = molc.Plan.from_workload(wl, tiled=tiled)
     B = dev(d["B"])
     I = P.new_intensity(prec)
     P.intensity_init(prec, I, B)
