@@ -1500,12 +1500,16 @@ struct molc_batch {
   int *d_ticket = nullptr;
   molc::TileShape shape{};
   int np_max = 0, grid = 0, threads = 0;
+  // the scale update over several blocks per instance: int4 {instance, block, blocks of the instance, 0}
+  int4 *d_scale_map = nullptr;
+  int n_scale = 0;
 };
 
 namespace {
 void batch_free(molc_batch *b) {
   DeviceGuard dg(b->device);
-  for (void *q : {(void *)b->d_tinst, (void *)b->d_tqueue, (void *)b->d_tprep, (void *)b->d_ticket})
+  for (void *q : {(void *)b->d_tinst, (void *)b->d_tqueue, (void *)b->d_tprep, (void *)b->d_ticket,
+                  (void *)b->d_scale_map})
     if (q) cudaFree(q);
   if (b->d_inst) cudaFree(b->d_inst);
   if (b->d_prep) cudaFree(b->d_prep);
@@ -1556,6 +1560,19 @@ molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out) 
   auto b = new molc_batch();
   b->device = dev;
   b->plans.assign(plans, plans + n);
+  {
+    std::vector<int4> smap;
+    for (int i = 0; i < n; ++i) {
+      const int64_t cg = (int64_t)plans[i]->G * plans[i]->view.ncell;
+      const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(64, (cg + 16383) / 16384));
+      for (int k = 0; k < nb; ++k) smap.push_back(make_int4(i, k, nb, 0));
+    }
+    b->n_scale = (int)smap.size();
+    if (upload_vec(&b->d_scale_map, smap) != cudaSuccess) {
+      batch_free(b);
+      return fail(MOLC_ERR_CUDA, "batch_create: scale map");
+    }
+  }
   if (n_tiled) {
     // items of all instances, those with the longest remaining wavefront first (an item's upstream items have a
     // longer one, so they come earlier); prep blocks of all instances
@@ -1745,22 +1762,24 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
   DeviceGuard dg(b->device);
   cudaStream_t st = (cudaStream_t)stream;
   if (b->tiled) {
-    cudaError_t e = launch_update_scale_tiles(b->d_tinst, (int)b->plans.size(), st);
+    cudaError_t e = launch_update_scale_map(nullptr, b->d_tinst, b->d_scale_map, b->n_scale, st);
     if (e == cudaSuccess) e = launch_tile_prep(b->d_tinst, b->d_tprep, b->n_tprep, b->d_ticket, st);
     if (e == cudaSuccess)
       e = launch_tile_sweep(b->d_tinst, b->d_tqueue, b->n_tqueue, b->d_ticket, b->np_max, b->shape, b->grid,
                             b->threads, st);
     return e == cudaSuccess ? MOLC_OK : cuda_fail(e, "batch_sweep");
   }
-  cudaError_t e = launch_update_scale_batch(b->d_inst, (int)b->plans.size(), st);
+  cudaError_t e = launch_update_scale_map(b->d_inst, nullptr, b->d_scale_map, b->n_scale, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: scale");
   e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: prep");
-  for (auto &c : b->sweeps) {
+  // one launch per kernel class, in order on the caller's stream (classes launched on concurrent streams were
+  // slower: each class fills the GPU by itself)
+  for (const auto &c : b->sweeps) {
     e = launch_sweep_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.depth, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: sweep");
   }
-  for (auto &c : b->moments) {
+  for (const auto &c : b->moments) {
     e = launch_moments_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: moments");
   }

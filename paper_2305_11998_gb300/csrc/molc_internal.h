@@ -152,6 +152,8 @@ struct SweepArgs {
   double *fxx, *fxy, *fyy;   // Eddington factors [G][cell], written where the moments are assembled, or all null
 };
 
+struct TileInst;   // one instance of a tiled sweep launch (below)
+
 // One instance of a batched FP32 sweep, as the batched kernels read it (device memory).
 struct BatchInst {
   PlanView v;
@@ -183,7 +185,10 @@ cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const doubl
 // Sweep-time scale update of an FP32 state from max(B, boundary) (see update_scale in molc_kernels.cu).
 cudaError_t launch_update_scale(const PlanView &v, const double *B, const double *bnd, double *header,
                                 cudaStream_t st);
-cudaError_t launch_update_scale_batch(const BatchInst *inst, int n, cudaStream_t st);
+// batched, several blocks per instance: map int4 {instance, block of the instance, blocks of the instance, 0}
+// over `inst` (bundle batches) or `tinst` (tiled batches, when not null)
+cudaError_t launch_update_scale_map(const BatchInst *inst, const TileInst *tinst, const int4 *map, int blocks,
+                                    cudaStream_t st);
 cudaError_t launch_prep_batch(const BatchInst *inst, const int4 *map, int blocks, cudaStream_t st);
 cudaError_t launch_sweep_fp32_batch(const BatchInst *inst, const int2 *map, int blocks, int n_polar, int depth,
                                     cudaStream_t st);
@@ -270,8 +275,6 @@ cudaError_t launch_tile_prep(const TileInst *inst, const int4 *map, int blocks, 
 // one plan: `ov` (by value) is also stored at dst for the sweep launch that follows
 cudaError_t launch_tile_prep_one(const TileInst &ov, TileInst *dst, const int4 *map, int blocks, int *ticket,
                                  cudaStream_t st);
-// batched FP32 state scale update over tiled instances
-cudaError_t launch_update_scale_tiles(const TileInst *inst, int n, cudaStream_t st);
 cudaError_t launch_tile_sweep(const TileInst *inst, const int2 *queue, int n_queue, int *ticket, int np_max,
                               const TileShape &shape, int grid, int threads, cudaStream_t st);
 size_t tile_sweep_smem(const TileShape &shape, int np_max);

@@ -376,6 +376,37 @@ __device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
   }
 }
+// Warp-cooperative forms for NP not a multiple of 4: the 32 threads of a warp hold 32 x NP consecutive floats of
+// a bundle step slot (128 NP bytes, 16-byte aligned), moved as 8 NP pieces of 16 bytes by the first 8 NP lanes
+// (one instruction per lane for NP <= 4) instead of NP scalar or NP/2 paired accesses per thread.
+template <int NP>
+__device__ __forceinline__ void copy_warp_chunk_async(float *dst_smem, const float *src, int lane) {
+  constexpr int kPieces = 8 * NP;
+#pragma unroll
+  for (int j = 0; j < (kPieces + 31) / 32; ++j) {
+    const int k = lane + 32 * j;
+    if (k < kPieces)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(dst_smem + 4 * k)),
+                   "l"(src + 4 * k)
+                   : "memory");
+  }
+}
+template <int NP>
+__device__ __forceinline__ void store_warp_chunk(float *dst, const float *src_smem, int lane,
+                                                 unsigned long long pol) {
+  constexpr int kPieces = 8 * NP;
+#pragma unroll
+  for (int j = 0; j < (kPieces + 31) / 32; ++j) {
+    const int k = lane + 32 * j;
+    if (k < kPieces) {
+      const float4 t = *reinterpret_cast<const float4 *>(src_smem + 4 * k);
+      asm volatile("st.global.L1::no_allocate.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(dst + 4 * k),
+                   "f"(t.x), "f"(t.y), "f"(t.z), "f"(t.w), "l"(pol)
+                   : "memory");
+    }
+  }
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -408,6 +439,12 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
 // Group accounting: the prologue commits D-1 groups (deviations of steps 0..D-2, table entries of steps
 // 0..D-3) and step s commits one; step s's deviations are in group s and its table entry in group s+1 (group s
 // for s <= D-3), so waiting until at most D-2 groups are pending is enough.
+// For NP not a multiple of 4 the deviations of a step are copied for the whole warp by its first 8 NP lanes
+// (every lane then runs the warp's longest track's steps, the copies and commits warp-uniform, a __syncwarp
+// making the landed copies visible to the other lanes and ordering the reads of a slot before its refill); for
+// odd NP the new deviations also go back through the slot: each thread writes its own, the warp stores the
+// slot's chunk in 16-byte pieces.  A thread whose track has ended leaves its part of the slot as it was copied,
+// so the padding it stores back is unchanged.
 // What an FP32 sweep adds to the segment update: nothing, the face reductions of Eq. 16 (MOLC_FACES), or the
 // per-ray balance check (MOLC_BALANCE).
 enum SweepExtra { kSweepPlain = 0, kSweepFaces = 1, kSweepBalance = 2 };
@@ -416,6 +453,8 @@ template <int NP, int D, int EXTRA = kSweepPlain>
 __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle) {
   static_assert(D >= 3, "the staging depth needs D >= 3");
   constexpr bool FACES = EXTRA == kSweepFaces, BAL = EXTRA == kSweepBalance;
+  constexpr bool COOP = NP % 4 != 0;       // warp-cooperative copies of the deviations
+  constexpr bool COOP_ST = NP % 2 != 0;    // ... and stores
   constexpr int kSteps = D;
   __shared__ __align__(16) float sdev[kSteps][kSweepBlock * NP];
   __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
@@ -441,6 +480,9 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   // address through registers
   const int64_t stride = (int64_t)kSweepBlock * v.n_polar;
   float *I = (float *)a.I + (v.boff[bundle] * kSweepBlock + tid) * NP;
+  const int lane = tid & 31, wofs = (tid & ~31) * NP;   // this warp's chunk in a slot (COOP)
+  float *Iw = (float *)a.I + v.boff[bundle] * kSweepBlock * NP + wofs;
+  const int nlim = COOP ? nmax : nseg;   // steps this thread copies and commits for
   const int2 *rec = v.seg32 + (sense ? tr.seg_off + nseg - 1 : tr.seg_off);
   const int rstep = sense ? -1 : 1;
   const int64_t cbase = (int64_t)ch * v.ncell * L.gc + gi;
@@ -471,8 +513,11 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
   for (int k = 0; k < kSteps; ++k) recs[k] = k < nseg ? ld_record(rec + k * rstep) : make_int2(0, 0);
 #pragma unroll
   for (int k = 0; k < kSteps - 1; ++k) {
+    if constexpr (COOP) {
+      if (k < nmax) copy_warp_chunk_async<NP>(&sdev[k][wofs], Iw + k * stride, lane);
+    }
     if (k < nseg) {
-      copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride);
+      if constexpr (!COOP) copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride);
       if (k < kSteps - 2) {
         copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc);
         copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc);
@@ -495,10 +540,16 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
     for (int u = 0; u < kSteps; ++u) {
       const int s = s0 + u;
-      if (s < nseg) {
+      if (s < nlim) {
         // group s+D-1: deviations of step s+D-1, table entry of step s+D-2
-        if (s + kSteps - 1 < nseg)
-          copy_dev_async<NP>(&sdev[(u + kSteps - 1) % kSteps][tid * NP], I + (kSteps - 1) * stride);
+        if constexpr (COOP) {
+          __syncwarp();   // every lane is done with the slot refilled here (read at step s-1)
+          if (s + kSteps - 1 < nmax)
+            copy_warp_chunk_async<NP>(&sdev[(u + kSteps - 1) % kSteps][wofs], Iw + (kSteps - 1) * stride, lane);
+        } else {
+          if (s + kSteps - 1 < nseg)
+            copy_dev_async<NP>(&sdev[(u + kSteps - 1) % kSteps][tid * NP], I + (kSteps - 1) * stride);
+        }
         if (s + kSteps - 2 < nseg) {
           const int c2 = recs[(u + kSteps - 2) % kSteps].x;
           copy16_async(&stab[(u + kSteps - 2) % kSteps][tid], cd + (int64_t)c2 * L.gc);
@@ -506,85 +557,98 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
         }
         cp_async_commit();
         cp_async_wait<kSteps - 2>();   // deviations and table entry of step s have landed
-        float dv[NP];
-        if constexpr (NP % 4 == 0) {
+        if constexpr (COOP) __syncwarp();   // ... including the pieces other lanes copied
+        if (s < nseg) {
+          float dv[NP];
+          if constexpr (NP % 4 == 0) {
 #pragma unroll
-          for (int p = 0; p < NP; p += 4) {
-            const float4 t4 = *reinterpret_cast<const float4 *>(&sdev[u][tid * NP + p]);
-            dv[p] = t4.x;
-            dv[p + 1] = t4.y;
-            dv[p + 2] = t4.z;
-            dv[p + 3] = t4.w;
+            for (int p = 0; p < NP; p += 4) {
+              const float4 t4 = *reinterpret_cast<const float4 *>(&sdev[u][tid * NP + p]);
+              dv[p] = t4.x;
+              dv[p + 1] = t4.y;
+              dv[p + 2] = t4.z;
+              dv[p + 3] = t4.w;
+            }
+          } else {
+#pragma unroll
+            for (int p = 0; p < NP; ++p) dv[p] = sdev[u][tid * NP + p];
           }
-        } else {
+          const float4 q = stab[u][tid];
+          const float qy = q.y * rescale;   // rescale (a power of two) brings the stored deviations to this scale
+          const float dB = sdB[u][tid];
+          // step s
+          const float len = __int_as_float(recs[u].y);
+          const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
+          const float kl = q.x * len;
+          const float rkl = rcp_approx(kl);
 #pragma unroll
-          for (int p = 0; p < NP; ++p) dv[p] = sdev[u][tid * NP + p];
-        }
-        const float4 q = stab[u][tid];
-        const float qy = q.y * rescale;   // rescale (a power of two) brings the stored deviations to this scale
-        const float dB = sdB[u][tid];
-        // step s
-        const float len = __int_as_float(recs[u].y);
-        const float jump = (bhi_prev - q.z) + (blo_prev - q.w);
-        const float kl = q.x * len;
-        const float rkl = rcp_approx(kl);
+          for (int p = 0; p < NP; ++p) psi[p] += jump;
+          double bcell = 0.0;
+          if constexpr (BAL) {
+            jsum += fabs(f32_to_f64_exact(jump));
+            bcell = f32_to_f64_exact(q.z) + f32_to_f64_exact(q.w);
+            blast = bcell;
+          }
+          if constexpr (FACES) {
+            // the intensity entering the segment, in scaled units: psi (relative to this cell) + B of this cell
+            const float Bc = q.z + q.w;
+            float S0 = 0.f, S1 = 0.f, S2 = 0.f;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) psi[p] += jump;
-        double bcell = 0.0;
-        if constexpr (BAL) {
-          jsum += fabs(f32_to_f64_exact(jump));
-          bcell = f32_to_f64_exact(q.z) + f32_to_f64_exact(q.w);
-          blast = bcell;
-        }
-        if constexpr (FACES) {
-          // the intensity entering the segment, in scaled units: psi (relative to this cell) + B of this cell
-          const float Bc = q.z + q.w;
-          float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+            for (int p = 0; p < NP; ++p) {
+              const float t0 = wf[p] * (psi[p] + Bc);
+              S0 += t0;
+              const float t1 = t0 * sinz[p];
+              S1 += t1;
+              S2 = fmaf(t1, sinz[p], S2);
+            }
+            const int2 fc = __ldg(sface + s * rstep);
+            double *fa = v.facc + ((int64_t)ch * v.n_faces + (sense ? fc.y : fc.x)) * kOutputs * L.gc + gi;
+            S0 *= width;
+            S1 *= width;
+            S2 *= width;
+            atomicAdd(fa, f32_to_f64(S0));
+            atomicAdd(fa + L.gc, f32_to_f64(fx * S1));
+            atomicAdd(fa + 2 * L.gc, f32_to_f64(fy * S1));
+            atomicAdd(fa + 3 * L.gc, f32_to_f64(fx * fx * S2));
+            atomicAdd(fa + 4 * L.gc, f32_to_f64(fx * fy * S2));
+            atomicAdd(fa + 5 * L.gc, f32_to_f64(fy * fy * S2));
+          }
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
-            const float t0 = wf[p] * (psi[p] + Bc);
-            S0 += t0;
-            const float t1 = t0 * sinz[p];
-            S1 += t1;
-            S2 = fmaf(t1, sinz[p], S2);
-          }
-          const int2 fc = __ldg(sface + s * rstep);
-          double *fa = v.facc + ((int64_t)ch * v.n_faces + (sense ? fc.y : fc.x)) * kOutputs * L.gc + gi;
-          S0 *= width;
-          S1 *= width;
-          S2 *= width;
-          atomicAdd(fa, f32_to_f64(S0));
-          atomicAdd(fa + L.gc, f32_to_f64(fx * S1));
-          atomicAdd(fa + 2 * L.gc, f32_to_f64(fy * S1));
-          atomicAdd(fa + 3 * L.gc, f32_to_f64(fx * fx * S2));
-          atomicAdd(fa + 4 * L.gc, f32_to_f64(fx * fy * S2));
-          atomicAdd(fa + 5 * L.gc, f32_to_f64(fy * fy * S2));
+            float E1, om, ex;
+            bool thin;
+            const float ahalf = kl * half_inv_sinz[p];   // tau / 2
+            attenuation(ahalf, sinz[p] * rkl, E1, om, ex, thin);
+            const float d = fmaf(dv[p], qy, dB);
+            const float pin = psi[p];
+            const float x = pin - d;
+            dv[p] = fmaf(x, E1, d);
+            psi[p] = thin ? fmaf(-x, om, pin) : fmaf(x, ex, d);
+            if constexpr (BAL) {
+              const double tau = 2.0 * f32_to_f64_exact(ahalf), dd = f32_to_f64_exact(d),
+                           pb = f32_to_f64_exact(dv[p]);
+              rb[p] += tau * (dd - pb);
+              const double pi = f32_to_f64_exact(pin), po = f32_to_f64_exact(psi[p]);
+              sb[p] += fabs(bcell + pi) + fabs(bcell + po) + fabs(pi) + fabs(po) +
+                       tau * (fabs(bcell + dd) + fabs(bcell + pb));
+            }
         }
+        if constexpr (COOP_ST) {
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          float E1, om, ex;
-          bool thin;
-          const float ahalf = kl * half_inv_sinz[p];   // tau / 2
-          attenuation(ahalf, sinz[p] * rkl, E1, om, ex, thin);
-          const float d = fmaf(dv[p], qy, dB);
-          const float pin = psi[p];
-          const float x = pin - d;
-          dv[p] = fmaf(x, E1, d);
-          psi[p] = thin ? fmaf(-x, om, pin) : fmaf(x, ex, d);
-          if constexpr (BAL) {
-            const double tau = 2.0 * f32_to_f64_exact(ahalf), dd = f32_to_f64_exact(d),
-                         pb = f32_to_f64_exact(dv[p]);
-            rb[p] += tau * (dd - pb);
-            const double pi = f32_to_f64_exact(pin), po = f32_to_f64_exact(psi[p]);
-            sb[p] += fabs(bcell + pi) + fabs(bcell + po) + fabs(pi) + fabs(po) +
-                     tau * (fabs(bcell + dd) + fabs(bcell + pb));
-          }
+          for (int p = 0; p < NP; ++p) sdev[u][tid * NP + p] = dv[p];
+        } else {
+          store_dev<NP>(I, dv, pol_stream);
         }
-        store_dev<NP>(I, dv, pol_stream);
         bhi_prev = q.z;
         blo_prev = q.w;
         I += stride;
         if (s + kSteps < nseg) recs[u] = ld_record(rec + (s + kSteps) * rstep);
+        }
+        if constexpr (COOP_ST) {
+          __syncwarp();
+          store_warp_chunk<NP>(Iw, &sdev[u][wofs], lane, pol_stream);
+        }
+        Iw += stride;
       }
     }
   }
@@ -1041,28 +1105,44 @@ __global__ void __launch_bounds__(256) update_scale_kernel(const double *B, int6
   }
 }
 
-// Batched: one block per instance reduces max(B, boundary) and updates that instance's scale.
+// Batched, several blocks per instance: map[block] = {instance, block of the instance, blocks of the instance, 0}.
+// Each block folds its share of the instance's B (its block 0 also the boundary) into the instance's header[2] by
+// atomicMax; the last of the instance's blocks (counted in header[4]) updates that instance's scale, as
+// update_scale_kernel does for one plan.
 template <class Inst>
-__global__ void __launch_bounds__(256) update_scale_batch_kernel(const Inst *inst) {
+__global__ void __launch_bounds__(256) update_scale_map_kernel(const Inst *inst, const int4 *map) {
   __shared__ unsigned long long red[8];
-  const Inst &b = inst[blockIdx.x];
+  const int4 m = map[blockIdx.x];
+  const Inst &b = inst[m.x];
+  double *header = const_cast<double *>(b.a.scale);
+  unsigned long long *mx = reinterpret_cast<unsigned long long *>(header + 2);
+  unsigned int *cnt = reinterpret_cast<unsigned int *>(header + 4);
   const int64_t n = (int64_t)b.v.G * b.v.ncell;
-  unsigned long long m = 0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  unsigned long long v = 0;
+  for (int64_t i = (int64_t)m.y * blockDim.x + threadIdx.x; i < n; i += (int64_t)m.z * blockDim.x) {
     const double x = b.a.B[i];
-    if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
+    if (x >= 0.0 && isfinite(x)) v = max(v, (unsigned long long)__double_as_longlong(x));
   }
-  for (int i = threadIdx.x; i < 4 * b.v.G; i += blockDim.x) {
-    const double x = b.a.bnd[i];
-    if (x >= 0.0 && isfinite(x)) m = max(m, (unsigned long long)__double_as_longlong(x));
-  }
+  if (m.y == 0)
+    for (int i = threadIdx.x; i < 4 * b.v.G; i += blockDim.x) {
+      const double x = b.a.bnd[i];
+      if (x >= 0.0 && isfinite(x)) v = max(v, (unsigned long long)__double_as_longlong(x));
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
-    update_scale(m, const_cast<double *>(b.a.scale));
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = max(v, red[w]);
+    if (v) atomicMax(mx, v);
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == (unsigned)m.z - 1) {   // last block of this instance
+      __threadfence();
+      const unsigned long long all = atomicMax(mx, 0ull);
+      update_scale(all, header);
+      *mx = 0;
+      *cnt = 0;
+    }
   }
 }
 
@@ -1230,9 +1310,13 @@ cudaError_t launch_update_scale(const PlanView &v, const double *B, const double
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_scale_batch(const BatchInst *inst, int n, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  update_scale_batch_kernel<BatchInst><<<n, 256, 0, st>>>(inst);
+cudaError_t launch_update_scale_map(const BatchInst *inst, const TileInst *tinst, const int4 *map, int blocks,
+                                    cudaStream_t st) {
+  if (blocks <= 0) return cudaSuccess;
+  if (tinst)
+    update_scale_map_kernel<TileInst><<<blocks, 256, 0, st>>>(tinst, map);
+  else
+    update_scale_map_kernel<BatchInst><<<blocks, 256, 0, st>>>(inst, map);
   return cudaGetLastError();
 }
 
@@ -1977,11 +2061,6 @@ cudaError_t launch_tile_np(const TileInst *inst, const int2 *queue, int n_queue,
 
 size_t tile_sweep_smem(const TileShape &sh, int np_max) {
   return tile_smem_layout(sh.max_item_floats, sh.cd_entries, 1, sh.max_len, sh.n_pairs, np_max, sh.split_units).total;
-}
-
-cudaError_t launch_update_scale_tiles(const TileInst *inst, int n, cudaStream_t st) {
-  update_scale_batch_kernel<TileInst><<<n, 256, 0, st>>>(inst);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_tile_prep(const TileInst *inst, const int4 *map, int blocks, int *ticket, cudaStream_t st) {

@@ -1,8 +1,9 @@
 """GPU: batched FP32 sweep over uneven instances (one launch per kernel class), CUDA-graph replay, autotuner.
 
 The batched kernels run the same per-instance arithmetic as molc_sweep + molc_closure, and the FP32 path is
-deterministic (no atomics), so every result is compared bit for bit with the per-instance calls; the
-per-instance path itself is checked against the oracle in test_gpu_parity.py.
+deterministic (no atomics), so every result is compared bit for bit with the per-instance calls.  A batch of
+instances with 1-4 polar cosines is also followed step by step by the binary128 oracle through the parity gate
+of the per-instance tests (tests/parity.py).
 """
 import numpy as np
 import pytest
@@ -140,4 +141,44 @@ def test_batch_rejects_bad_arguments(molc):
     args[1]["c"] = -1.0
     with pytest.raises(molc.MolcError):
         batch.bind(args)
+    batch.close()
+
+
+# one instance per polar count 1-4 (NP not a multiple of 4 takes the warp-cooperative state copies), G = 37 over
+# two group chunks, and an instance with twice the ray density
+ORACLE_SHAPES = [(16, 5, 1, 16, 2), (20, 6, 2, 24, 2), (24, 4, 3, 32, 4), (16, 37, 3, 16, 2), (12, 8, 4, 16, 2)]
+
+
+def test_batched_instances_vs_binary128(molc):
+    """Every instance of a batch against the binary128 oracle, over three steps with the state carried (the
+    oracle carries its deviations and the bound of the path's state), through the same gate as the per-instance
+    parity tests; the factors the batch forms in its moment assembly against N / (c E) of its own moments."""
+    import oracle
+    import parity
+    inst = []
+    for i, (n, G, npol, naz, div) in enumerate(ORACLE_SHAPES):
+        wl = synth.Workload(f"o{i}", n, n, 6.0, G, 0.001, 100.0, npol, naz, div, 1)
+        inst.append((wl, wl.inputs(20 + i), molc.Plan.from_workload(wl)))
+    args = [new_args(P, wl, d, closure=True) for wl, d, P in inst]
+    batch = molc.Batch([P for _, _, P in inst])
+    batch.bind(args)
+    carried = [(None, None)] * len(inst)
+    for _ in range(3):
+        batch.sweep()
+        torch.cuda.synchronize()
+        for j, ((wl, d, P), a) in enumerate(zip(inst, args)):
+            geom = oracle.Geometry.from_workload(wl)
+            dev_prev, err_prev = carried[j]
+            ref = parity.reference(geom, d, "fp32", wl.n_polar, I_prev=dev_prev, I_err=err_prev, want_I=True)
+            carried[j] = (ref["I"], ref["I_err"])
+            got = {k: v.cpu().numpy() for k, v in a["out"].items()}
+            parity.compare(got, ref, "fp32", d["c"])
+            cE = d["c"] * got["E"]
+            for k, nm in (("fxx", "Nxx"), ("fxy", "Nxy"), ("fyy", "Nyy")):
+                f = a["f"][k].cpu().numpy()
+                want = got[nm] / cE
+                assert np.all(np.abs(f - want) <= 8 * 2.0 ** -53 * np.abs(want) + 1e-300), (j, k)
+    for _, _, P in inst:
+        assert P.device_status() == 0
+        P.close()
     batch.close()

@@ -90,7 +90,7 @@ def test_small_multistep_vs_binary128(molc, prec):
 
 
 def test_fp32_ten_steps_64x64_sampled_groups(molc):
-    """configs[1]-shaped: 64^2 cells, 17 groups, 4 x 32 directions, h/4, ten steps with the state carried; the
+    """The 64^2 workload: 64^2 cells, 17 groups, 4 x 32 directions, h/4, ten steps with the state carried; the
     GPU sweeps all groups, three are followed by the binary128 oracle with the carried state bound."""
     wl = synth.WORKLOADS["fc64_g17_d128"]
     d = wl.inputs(0)

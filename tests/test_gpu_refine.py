@@ -40,10 +40,10 @@ def test_refinement_multistep_fp32_against_fp64():
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_refinement_steps_against_binary128(prec):
-    """The same cold start and temperature sequence (configs[4]'s physics at 24^2, 6 groups, h/2), each step of the
-    GPU path against the binary128 oracle fed the same kappa and B.  B changes between steps: the oracle's carried
-    deviations are re-referenced to the new B in double (that rounding joins the state bound), and the path's
-    stored deviations refer to the previous step's B (the error model's B_ref)."""
+    """The same cold start and temperature sequence (the refinement stress's physics at 24^2, 6 groups, h/2),
+    each step of the GPU path against the binary128 oracle fed the same kappa and B.  B changes between steps:
+    the oracle's carried deviations are re-referenced to the new B in double (that rounding joins the state
+    bound), and the path's stored deviations refer to the previous step's B (the error model's B_ref)."""
     import paper_2305_11998_gb300 as molc
     from paper_2305_11998_gb300 import multistep
     wl = synth.Workload("refine_small", 24, 24, 6.0, 6, 0.001, 100.0, 2, 16, 2, 4, cold_start=True)
