@@ -62,9 +62,14 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 #define MOLC_FACES 8u       /* also accumulate the face moments of Eq. 16 in every molc_sweep (device memory for
                                6 FP64 sums per (face, group); FP64 reductions per segment, so sweeps are slower);
                                read them with molc_face_moments */
-#define MOLC_AUTOTUNE 4u    /* time the FP32 sweep's compiled staging depths on this plan during molc_create
-                               (temporary device memory of about one FP32 state) and keep the fastest; the
-                               choice changes no result, only speed (molc_plan_info.fp32_sweep_depth) */
+#define MOLC_AUTOTUNE 4u    /* time launch configurations of the FP32 sweep on this plan during molc_create and
+                               keep the fastest: the compiled staging depths of the bundle sweep
+                               (molc_plan_info.fp32_sweep_depth), or for a tiled plan the planner's tile side,
+                               groups per work item and block size and their neighbours (fp32_tile_cells,
+                               fp32_tile_groups, fp32_block_threads).  Temporary device memory of about one FP32
+                               state.  The choice changes no segment update, only speed (a tiled plan's moment
+                               summation order follows its tiles).  With a tuning cache set (molc_tune_cache) a
+                               recorded choice is applied without timing. */
 #define MOLC_BALANCE 16u    /* also evaluate the per-ray discrete balance of every sweep in FP64 (a check, not part
                                of the result; FP64 work per update, so sweeps are slower); read the largest
                                relative residual with molc_ray_balance.  Not with MOLC_FACES. */
@@ -126,6 +131,7 @@ typedef struct {
   int fp32_tile_items;      /* tiled FP32 sweep: work items per step (tiles x 4 quadrants x group tiles) */
   int fp32_sweep_blocks;    /* tiled FP32 sweep: blocks of its persistent launch */
   int fp32_block_threads;   /* tiled FP32 sweep: threads of one such block */
+  int tuned_from_cache;     /* MOLC_AUTOTUNE: 1 when the configuration came from the tuning cache (nothing timed) */
 } molc_plan_info;
 
 /* Configuration of a tiled FP32 sweep (no counterpart in the paper: how the sweep's work is cut for the GPU).
@@ -343,6 +349,17 @@ molc_status molc_kernel_time_parts(molc_plan *plan, double *parts_ms, int *launc
  * MOLC_ERR_INVALID_ARG if the configuration does not fit a block's shared memory (the plan then keeps the
  * library's default configuration). */
 molc_status molc_plan_retile(molc_plan *plan, const molc_tile_config *cfg);
+
+/* Tuning cache of MOLC_AUTOTUNE (no counterpart in the paper), process-wide: from this call on, molc_create with
+ * MOLC_AUTOTUNE first looks the plan up in the JSON file `path` (host path, read during the call; later plans
+ * reread and rewrite it).  An entry for the same plan signature (grid, directions, groups, ray spacing, layout
+ * and the flags that change the sweep), the same kind of device (name, SM count, compute capability) and the same
+ * library build is applied without timing (molc_plan_info.tuned_from_cache = 1); otherwise the plan is tuned and
+ * its entry added, the file rewritten whole through a temporary file and a rename (a file that cannot be
+ * written leaves the plan tuned and the file unchanged).  The file need not exist.  path = NULL or "" switches the
+ * cache off.  *n_entries (may be NULL) receives the number of entries read.  MOLC_ERR_INVALID_ARG, with the
+ * earlier setting kept, if the file exists but cannot be read or is not a cache this library wrote. */
+molc_status molc_tune_cache(const char *path, int *n_entries);
 
 /* FP64 fused multiply-add throughput of the current device, in FLOP/s (2 per FMA): the bound of the plain FP64
  * sweep's arithmetic (no counterpart in the paper; a measurement for the roofline).  Runs a kernel of independent

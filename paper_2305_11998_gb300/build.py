@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libmolc.so")
-SOURCES = ["molc_host.cpp", "molc_tiles.cpp", "molc_kernels.cu"]
+SOURCES = ["molc_host.cpp", "molc_tiles.cpp", "molc_tune.cpp", "molc_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the host planner defines the characteristic grid by plain double evaluation: no FMA contraction there
 PER_FILE = {"molc_host.cpp": ["-Xcompiler", "-ffp-contract=off"], "molc_tiles.cpp": ["-Xcompiler", "-ffp-contract=off"]}
@@ -32,11 +32,26 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_id() -> str:
+    """Identifier of this build: the first 16 hex digits of the SHA-256 of the sources and the header (the tuning
+    cache keeps a configuration for the build it was timed on)."""
+    import hashlib
+    h = hashlib.sha256()
+    paths = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(ROOT, "include", "molc.h")]
+    for path in paths:
+        if os.path.isfile(path):
+            h.update(os.path.basename(path).encode())
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+    return "b" + h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), *ARCH]
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), *ARCH,
+              f"-DMOLC_BUILD_ID={build_id()}"]   # one identifier token, made a string in the source
     if verbose:
         common += ["-Xptxas", "-v"]
 

@@ -5,6 +5,7 @@
 // the + sense walks them forward, the - sense backward, and all polar cosines of the pair share them (the
 // in-plane track depends only on the azimuth; the 3D path length is l / sin(zeta), Eq. 13).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +17,7 @@
 
 #include "molc_internal.h"
 #include "molc_tiles.h"
+#include "molc_tune.h"
 
 using namespace molc;
 
@@ -131,6 +133,8 @@ struct molc_plan {
   int64_t *d_tpiece_off = nullptr;
   std::vector<void *> tdev;  // every tiled allocation (freed with the plan)
   // benchmark timing of the sweep kernel
+  std::string tune_key;      // MOLC_AUTOTUNE: the plan's signature in the tuning cache
+  bool tuned_from_cache = false;
   bool timing = false;
   std::vector<cudaEvent_t> ev;   // pairs
   int n_timed = 0;
@@ -387,7 +391,7 @@ double *header_ptr(const molc_plan *p, molc_precision prec, void *I);
 // launches of the sweep kernel each, on temporary inputs: kappa = B = boundary = 0, c = dt = 1, an FP32 state
 // initialised from B) and keeps the fastest.  The depth changes no arithmetic, only the timing.  Allocates its
 // temporaries for the duration of the call.
-molc_status autotune(molc_plan *p) {
+molc_status autotune(molc_plan *p, double *best_ms_out) {
   DeviceGuard dg(p->device);
   const int64_t cg = (int64_t)p->G * p->view.ncell;
   void *I = nullptr;
@@ -401,6 +405,7 @@ molc_status autotune(molc_plan *p) {
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   int best = p->view.sweep_depth;
+  float best_ms = 0;
   if (e == cudaSuccess) {
     SweepArgs a{};
     a.kappa = in;
@@ -420,7 +425,6 @@ molc_status autotune(molc_plan *p) {
     if (e == cudaSuccess) e = cudaMemcpy(a.Bref, a.B, cg * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = launch_set_scale(p->view, MOLC_FP32, a.B, const_cast<double *>(a.scale), nullptr);
     if (e == cudaSuccess) e = launch_prep(p->view, MOLC_FP32, a, nullptr);
-    float best_ms = 0;
     for (int d : kSweepDepths) {
       if (e != cudaSuccess) break;
       PlanView v = p->view;
@@ -445,6 +449,7 @@ molc_status autotune(molc_plan *p) {
   if (I) cudaFree(I);
   if (e != cudaSuccess) return cuda_fail(e, "create: autotune");
   p->view.sweep_depth = best;
+  if (best_ms_out) *best_ms_out = best_ms / 3.0;
   int code = 0;
   cudaMemcpy(&code, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemset(p->d_status, 0, sizeof(int));   // the temporaries' checks leave no trace
@@ -569,9 +574,60 @@ molc_status build_tiled(molc_plan *p, int force_ts, int force_gt, bool *fits = n
   return MOLC_OK;
 }
 
+// Build identifier in the tuning cache: the build script defines MOLC_BUILD_ID as one token (a hash of the
+// sources); made a string here.
+#ifndef MOLC_BUILD_ID
+#define MOLC_BUILD_ID unversioned
+#endif
+#define MOLC_STRINGIFY2(x) #x
+#define MOLC_STRINGIFY(x) MOLC_STRINGIFY2(x)
+const char *const kBuildId = MOLC_STRINGIFY(MOLC_BUILD_ID);
+
+// Signature of a plan in the tuning cache: what molc_create was given that decides the plan's kernels and their
+// launch shapes (grid, directions, groups, ray spacing and layout, the flags that change the sweep), readable
+// sizes followed by a 64-bit FNV-1a hash of the exact values.
+std::string plan_signature(const molc_grid &g, const molc_quadrature *q, int G, double spacing, int layout,
+                           unsigned flags) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](const void *data, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  const unsigned f = flags & (MOLC_AREA_RENORM | MOLC_FACES | MOLC_BALANCE | MOLC_TILED);
+  const double gd[4] = {g.x0, g.y0, g.lx, g.ly};
+  const int gi[5] = {g.nx, g.ny, q->n, G, layout};
+  mix(gd, sizeof gd);
+  mix(gi, sizeof gi);
+  mix(&spacing, sizeof spacing);
+  mix(&f, sizeof f);
+  for (const double *a : {q->mu, q->cos_phi, q->sin_phi, q->w}) mix(a, sizeof(double) * (size_t)q->n);
+  char buf[200];
+  std::snprintf(buf, sizeof buf, "%dx%d cells, %d groups, %d directions, spacing %.6g, layout %d, flags %u, %016llx",
+                g.nx, g.ny, G, q->n, spacing, layout, f, (unsigned long long)h);
+  return buf;
+}
+
+// The kind of device a tuned configuration holds for: name, SM count, compute capability.
+std::string device_signature(int dev) {
+  cudaDeviceProp pr{};
+  if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return "unknown device";
+  }
+  char buf[320];
+  std::snprintf(buf, sizeof buf, "%s, %d SMs, sm_%d%d", pr.name, pr.multiProcessorCount, pr.major, pr.minor);
+  return buf;
+}
+
 }  // namespace
 
 extern "C" {
+
+// MOLC_AUTOTUNE at the end of molc_create (defined below, after the tiled step)
+static molc_status tune_plan(molc_plan *p);
 
 const char *molc_last_error(void) { return g_last_error.c_str(); }
 
@@ -1149,8 +1205,9 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   v.mmulti = p->d_mmulti;
   v.n_mmulti = (int)mmulti.size();
   v.mscratch = p->d_mscratch;
-  if ((flags & MOLC_AUTOTUNE) && nch32) {
-    st = autotune(p);
+  p->tune_key = plan_signature(g, quad, p->G, ray_spacing, layout, flags);
+  if ((flags & MOLC_AUTOTUNE) && !p->host_only && (nch32 || p->tiled)) {
+    st = tune_plan(p);
     if (st != MOLC_OK) {
       free_device(p);
       delete p;
@@ -1185,6 +1242,7 @@ molc_status molc_plan_get_info(const molc_plan *p, molc_plan_info *info) {
   info->fp32_tile_items = p->tiled ? p->tv.n_items : 0;
   info->fp32_sweep_blocks = p->tiled ? p->tgrid : 0;
   info->fp32_block_threads = p->tiled ? p->tthreads : 0;
+  info->tuned_from_cache = p->tuned_from_cache ? 1 : 0;
   return MOLC_OK;
 }
 
@@ -1265,6 +1323,136 @@ static cudaError_t tile_step(molc_plan *p, const SweepArgs &a, const TileView &t
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
   }
   return e;
+}
+
+// Autotuner of the tiled FP32 sweep: the planner's configuration and its neighbours (half and twice the tile
+// side, half and twice the groups per work item, the other block size), each laid out and timed (one warm-up and
+// two timed steps of prep + persistent sweep on temporary zero inputs, an FP32 state of that layout); the fastest
+// is laid out again and kept.  Configurations the planner rejects (a work item beyond shared memory) are skipped.
+// The configuration changes no segment update and no output beyond the moment summation order.
+static molc_status autotune_tiled(molc_plan *p, double *best_ms_out) {
+  DeviceGuard dg(p->device);
+  const int ts0 = p->tv.TS, gt0 = p->tv.GT, th0 = p->tthreads;
+  std::vector<std::array<int, 3>> cand = {{ts0, gt0, th0}, {ts0, gt0, th0 == 128 ? 256 : 128}};
+  if (ts0 / 2 >= 2) cand.push_back({ts0 / 2, gt0, th0});
+  cand.push_back({2 * ts0, gt0, th0});
+  if (gt0 / 2 >= 1) cand.push_back({ts0, gt0 / 2, th0});
+  if (2 * gt0 <= std::min(p->G, 32)) cand.push_back({ts0, 2 * gt0, th0});
+  const int64_t cg = (int64_t)p->G * p->view.ncell;
+  double *in = nullptr, *mom = nullptr;   // kappa, B [G][cell], bnd [4][G]; 6 x [G][cell]
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc((void **)&in, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&mom, 6 * cg * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(in, 0, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::array<int, 3> best = cand[0];
+  float best_ms = 0;
+  molc_status st = MOLC_OK;
+  for (const auto &c : cand) {
+    if (e != cudaSuccess || st != MOLC_OK) break;
+    bool fits = true;
+    st = build_tiled(p, c[0], c[1], &fits, c[2]);
+    if (st != MOLC_OK) {
+      if (fits) break;   // a device failure, not a rejected configuration
+      st = MOLC_OK;
+      g_last_error.clear();
+      continue;
+    }
+    void *I = nullptr;
+    e = cudaMalloc(&I, state_bytes_fp32(p));
+    if (e != cudaSuccess) break;
+    SweepArgs a{};
+    a.kappa = in;
+    a.B = in + cg;
+    a.bnd = in + 2 * cg;
+    a.c = a.dt = 1.0;
+    a.inv_c = a.inv_cdt = 1.0;
+    a.I = I;
+    a.Bref = bref_ptr(p, MOLC_FP32, I);
+    a.scale = header_ptr(p, MOLC_FP32, I);
+    a.out = molc_moments{mom, mom + cg, mom + 2 * cg, mom + 3 * cg, mom + 4 * cg, mom + 5 * cg};
+    e = cudaMemset(I, 0, state_bytes_fp32(p));
+    if (e == cudaSuccess) e = cudaMemcpy(a.Bref, a.B, cg * sizeof(double), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = launch_set_scale(p->view, MOLC_FP32, a.B, const_cast<double *>(a.scale), nullptr);
+    if (e == cudaSuccess) e = tile_step(p, a, p->tv, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < 2 && e == cudaSuccess; ++r) e = tile_step(p, a, p->tv, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaFree(I);
+    if (e == cudaSuccess && (best_ms == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = {p->tv.TS, p->tv.GT, p->tthreads};
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (mom) cudaFree(mom);
+  if (in) cudaFree(in);
+  if (st != MOLC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "create: autotune (tiled)");
+  st = build_tiled(p, best[0], best[1], nullptr, best[2]);
+  if (st != MOLC_OK) return st;
+  if (best_ms_out) *best_ms_out = best_ms / 2.0;
+  int code = 0;
+  cudaMemcpy(&code, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemset(p->d_status, 0, sizeof(int));   // the temporaries' checks leave no trace
+  return code == kStatusTimeout ? fail(MOLC_ERR_TIMEOUT, "create: autotune (tiled): a bounded wait gave up")
+                                : MOLC_OK;
+}
+
+// MOLC_AUTOTUNE: the configuration recorded in the tuning cache for this plan, device and build when there is
+// one (nothing timed), else the autotuner's choice, then recorded.  A cache that cannot be written leaves the
+// plan tuned and the file as it was.
+static molc_status tune_plan(molc_plan *p) {
+  const std::string dev = device_signature(p->device);
+  TuneRecord rec;
+  if (tune_cache_enabled() && tune_cache_lookup(p->tune_key, dev, kBuildId, rec)) {
+    bool applied = false;
+    if (p->tiled && rec.tile_cells > 0) {
+      bool fits = true;
+      const molc_status st = build_tiled(p, rec.tile_cells, rec.tile_groups, &fits, rec.block_threads);
+      if (st != MOLC_OK && fits) return st;
+      applied = st == MOLC_OK;
+      if (!applied) g_last_error.clear();
+    } else if (!p->tiled) {
+      for (int d : kSweepDepths)
+        if (d == rec.sweep_depth) applied = true;
+      if (applied) p->view.sweep_depth = rec.sweep_depth;
+    }
+    if (applied) {
+      p->tuned_from_cache = true;
+      return MOLC_OK;
+    }
+  }
+  double ms = 0;
+  const molc_status st = p->tiled ? autotune_tiled(p, &ms) : autotune(p, &ms);
+  if (st != MOLC_OK) return st;
+  if (tune_cache_enabled()) {
+    rec = TuneRecord{};
+    rec.key = p->tune_key;
+    rec.device = dev;
+    rec.build = kBuildId;
+    rec.sweep_depth = p->tiled ? 0 : p->view.sweep_depth;
+    rec.tile_cells = p->tiled ? p->tv.TS : 0;
+    rec.tile_groups = p->tiled ? p->tv.GT : 0;
+    rec.block_threads = p->tiled ? p->tthreads : 0;
+    rec.best_ms = ms;
+    std::string why;
+    tune_cache_store(rec, why);
+  }
+  return MOLC_OK;
+}
+
+molc_status molc_tune_cache(const char *path, int *n_entries) {
+  std::string why;
+  const int n = tune_cache_set(path, why);
+  if (n < 0) return fail(MOLC_ERR_INVALID_ARG, "tune_cache: %s", why.c_str());
+  if (n_entries) *n_entries = n;
+  return MOLC_OK;
 }
 
 // molc_sweep, and with factor outputs molc_sweep_closure (`who` names the entry point in error messages).

@@ -35,7 +35,7 @@ EXPORTED = ("molc_quadrature_product", "molc_create", "molc_plan_get_info", "mol
             "molc_device_status", "molc_last_error", "molc_destroy", "molc_sweep_static_scratch",
             "molc_kernel_time_parts", "molc_batch_create", "molc_batch_bind", "molc_batch_sweep",
             "molc_batch_destroy", "molc_grey_coefficients", "molc_face_moments", "molc_sweep_closure",
-            "molc_ray_balance", "molc_fp64_fma_rate", "molc_plan_retile")
+            "molc_ray_balance", "molc_fp64_fma_rate", "molc_plan_retile", "molc_tune_cache")
 
 
 class MolcError(RuntimeError):
@@ -68,7 +68,8 @@ class _Info(C.Structure):
                 ("n_segments", C.c_int64), ("n_updates", C.c_int64), ("fp32_groups_per_warp", C.c_int),
                 ("device_bytes", C.c_size_t), ("fp32_sweep_depth", C.c_int), ("n_faces", C.c_int),
                 ("n_split_cells", C.c_int), ("fp32_tile_cells", C.c_int), ("fp32_tile_groups", C.c_int),
-                ("fp32_tile_items", C.c_int), ("fp32_sweep_blocks", C.c_int), ("fp32_block_threads", C.c_int)]
+                ("fp32_tile_items", C.c_int), ("fp32_sweep_blocks", C.c_int), ("fp32_block_threads", C.c_int),
+                ("tuned_from_cache", C.c_int)]
 
 
 class _TileConfig(C.Structure):
@@ -120,6 +121,7 @@ def load(build_if_needed: bool = True):
         "molc_device_status": (C.c_int, [vp, ip]),
         "molc_fp64_fma_rate": (C.c_int, [dp]),
         "molc_plan_retile": (C.c_int, [vp, C.POINTER(_TileConfig)]),
+        "molc_tune_cache": (C.c_int, [C.c_char_p, ip]),
         "molc_last_error": (C.c_char_p, []),
         "molc_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
         "molc_batch_bind": (C.c_int, [vp, C.POINTER(_SweepArgs)]),
@@ -171,6 +173,14 @@ def fp64_fma_rate() -> float:
     return r.value
 
 
+def tune_cache(path) -> int:
+    """molc_tune_cache: use the JSON file `path` as the process-wide MOLC_AUTOTUNE cache (None: off); returns the
+    number of entries read."""
+    n = C.c_int(0)
+    _check(load().molc_tune_cache(None if path is None else os.fsencode(path), C.byref(n)))
+    return n.value
+
+
 def quadrature_product(n_polar: int, n_azim: int):
     """Gauss-Legendre x Chebyshev product set from the library: (mu, cos_phi, sin_phi, w) numpy arrays."""
     n = n_polar * n_azim
@@ -201,6 +211,7 @@ class PlanInfo:
     fp32_tile_items: int
     fp32_sweep_blocks: int
     fp32_block_threads: int
+    tuned_from_cache: int
 
 
 class Plan:
