@@ -1962,7 +1962,7 @@ molc_status molc_batch_sweep(molc_batch *b, molc_stream stream) {
   e = launch_prep_batch(b->d_inst, b->d_prep, b->n_prep, st);
   if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: prep");
   // one launch per kernel class, in order on the caller's stream (classes launched on concurrent streams were
-  // slower: each class fills the GPU by itself)
+  // slower: each class fills the GPU by itself; so was one persistent launch over all classes' bundles)
   for (const auto &c : b->sweeps) {
     e = launch_sweep_fp32_batch(b->d_inst, c.d_map, c.n, c.n_polar, c.depth, st);
     if (e != cudaSuccess) return cuda_fail(e, "batch_sweep: sweep");

@@ -449,16 +449,26 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
 // per-ray balance check (MOLC_BALANCE).
 enum SweepExtra { kSweepPlain = 0, kSweepFaces = 1, kSweepBalance = 2 };
 
+// Shared memory of one FP32 sweep block: D staged steps of its 128 threads' deviations, cell-table entries and
+// B_ref differences.
+template <int NP, int D>
+struct __align__(16) SweepSmem {
+  float dev[D][kSweepBlock * NP];
+  float4 tab[D][kSweepBlock];
+  float dB[D][kSweepBlock];
+};
+
 template <int NP, int D, int EXTRA = kSweepPlain>
-__device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle) {
+__device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepArgs &a, const Layout &L, int bundle,
+                                                SweepSmem<NP, D> &sm) {
   static_assert(D >= 3, "the staging depth needs D >= 3");
   constexpr bool FACES = EXTRA == kSweepFaces, BAL = EXTRA == kSweepBalance;
   constexpr bool COOP = NP % 4 != 0;       // warp-cooperative copies of the deviations
   constexpr bool COOP_ST = NP % 2 != 0;    // ... and stores
   constexpr int kSteps = D;
-  __shared__ __align__(16) float sdev[kSteps][kSweepBlock * NP];
-  __shared__ __align__(16) float4 stab[kSteps][kSweepBlock];
-  __shared__ __align__(16) float sdB[kSteps][kSweepBlock];
+  auto &sdev = sm.dev;
+  auto &stab = sm.tab;
+  auto &sdB = sm.dB;
   const int tid = threadIdx.x;
   const int64_t item = (int64_t)bundle * kSweepBlock + tid;
   const bool live = item < a.n_items;
@@ -675,15 +685,17 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 
 template <int NP, int D, int EXTRA = kSweepPlain>
 __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
-  sweep_fp32_body<NP, D, EXTRA>(v, a, L, v.block_order[blockIdx.x]);
+  __shared__ SweepSmem<NP, D> sm;
+  sweep_fp32_body<NP, D, EXTRA>(v, a, L, v.block_order[blockIdx.x], sm);
 }
 
 // Batched: block j sweeps bundle map[j].y of instance map[j].x (blocks of all instances, longest first).
 template <int NP, int D>
 __global__ void __launch_bounds__(kSweepBlock) sweep_fp32_batch_kernel(const BatchInst *inst, const int2 *map) {
+  __shared__ SweepSmem<NP, D> sm;
   const int2 m = map[blockIdx.x];
   const BatchInst &b = inst[m.x];
-  sweep_fp32_body<NP, D>(b.v, b.a, b.L, m.y);
+  sweep_fp32_body<NP, D>(b.v, b.a, b.L, m.y, sm);
 }
 
 // FP32 path, cell moments: one thread per (chunk, cell, group), consecutive groups of a cell in consecutive
