@@ -1,6 +1,6 @@
-"""Host logic of bench.py's clock record: nvidia-smi rows are summarised over the samples taken inside the timed
-region (one sampling interval of slack), throttle reasons are collected from those rows, and rows outside the
-region are used only when none falls inside."""
+"""Host logic of bench.py: the clock record (nvidia-smi rows are summarised over the samples taken inside the
+timed region, one sampling interval of slack, throttle reasons are collected from those rows, and rows outside
+the region are used only when none falls inside) and the key of the recorded DRAM traffic figure."""
 import datetime
 import os
 import sys
@@ -34,3 +34,18 @@ def test_all_rows_when_none_falls_inside_and_bad_rows_skipped():
     assert s["sm_mhz"] == 1900.0
     assert s["reasons"] == ["hw_slowdown"]
     assert bench.summarize_clocks([], t0, t0) is None
+
+
+def test_traffic_figure_is_keyed_to_the_kernel_source(tmp_path, monkeypatch):
+    """bench.py reports the recorded DRAM bytes per update only for the kernel source they were taken on."""
+    import hashlib
+    src = tmp_path / "kernels.cu"
+    src.write_text("// kernel source\n")
+    h = hashlib.sha256(src.read_bytes()).hexdigest()
+    monkeypatch.setattr(bench, "KERNEL_SOURCE", str(src))
+    monkeypatch.setattr(bench, "SWEEP_FP32_TRAFFIC", {"kernel_source_sha256": h, "dram_bytes_per_update": 8.5})
+    assert bench.traffic_per_update() == 8.5
+    src.write_text("// kernel source, changed\n")
+    assert bench.traffic_per_update() is None
+    monkeypatch.setattr(bench, "KERNEL_SOURCE", str(tmp_path / "missing.cu"))
+    assert bench.traffic_per_update() is None
