@@ -85,6 +85,7 @@ __device__ __forceinline__ void prep_tiles(const PlanView &v, const SweepArgs &a
   for (int tile = tile0; tile < n_tiles; tile += tstride) {
     const int c0 = tile * kPrepCells;
     const int nc = min(kPrepCells, v.ncell - c0);
+#pragma unroll 4
     for (int k = threadIdx.x; k < kPrepCells * gcount; k += blockDim.x) {
       const int gl = k / kPrepCells, c = k - gl * kPrepCells;
       if (c >= nc) continue;
@@ -805,16 +806,26 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
     two_sum_add(hi[4], lo[4], (cf * sf) * P2);
     two_sum_add(hi[5], lo[5], (sf * sf) * P2);
   };
-  for (int e = 0; e < ne; e += kGatherBatch) {
-    int4 en[kGatherBatch];
+  // the entries of the next batch are loaded while this batch's state loads are in flight
+  int4 en[kGatherBatch];
+  if (ne > 0) {
 #pragma unroll
-    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + b);
+    for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + b);
+  }
+  for (int e = 0; e < ne; e += kGatherBatch) {
     float dv[kGatherBatch][NP];
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) load_dev_cg<NP>(I + gather_slot(en[b].x, en[b].y, gi) * NP, dv[b]);
+    int2 zw[kGatherBatch];
+#pragma unroll
+    for (int b = 0; b < kGatherBatch; ++b) zw[b] = make_int2(en[b].z, en[b].w);
+    if (e + kGatherBatch < ne) {
+#pragma unroll
+      for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + kGatherBatch + b);
+    }
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) {
-      const int pr = en[b].w >> 1;
+      const int pr = zw[b].y >> 1;
       if (pr != cur || run == kPairRun) {
         flush();
         cur = pr;
@@ -830,9 +841,9 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
         S1 = fmaf(c0[NP + p], dv[b][p], S1);
         S2 = fmaf(c0[2 * NP + p], dv[b][p], S2);
       }
-      const float af = __int_as_float(en[b].z);
+      const float af = __int_as_float(zw[b].x);
       P0 = fmaf(af, S0, P0);
-      P1 = fmaf((en[b].w & 1) ? -af : af, S1, P1);
+      P1 = fmaf((zw[b].y & 1) ? -af : af, S1, P1);
       P2 = fmaf(af, S2, P2);
     }
   }
@@ -879,15 +890,18 @@ __global__ void __launch_bounds__(128) moments_combine_batch_kernel(const BatchI
   moments_combine_body(b.v, b.a, b.L, m.y, (int64_t)m.z * blockDim.x);
 }
 
+// blocks per SM: 7 up to 3 polar cosines, 6 at 4 (80 registers: the next batch's entries are loaded while the
+// current batch's state loads are in flight), 5 beyond
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
+__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 6 : 5)
+    moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
   moments_fp32_body<NP>(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
 }
 
 // Batched: block j handles threads 128 map[j].z .. of chunk map[j].y of instance map[j].x.
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 4 ? 8 : 5) moments_fp32_batch_kernel(const BatchInst *inst,
-                                                                                 const int4 *map) {
+__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 6 : 5)
+    moments_fp32_batch_kernel(const BatchInst *inst, const int4 *map) {
   const int4 m = map[blockIdx.x];
   const BatchInst &b = inst[m.x];
   moments_fp32_body<NP>(b.v, b.a, b.L, m.y, (int64_t)m.z * blockDim.x);
