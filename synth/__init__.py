@@ -325,6 +325,10 @@ WORKLOADS = {
     "fc512_g17_d128": Workload("fc512_g17_d128", 512, 512, 6.0, 17, 0.001, 100.0, 4, 32, 2, 1, n_fronts=3),
     # profiling size of the production workload (same generators; 3.3 GB FP32 state, accumulators > L2)
     "fc384_g17_d128": Workload("fc384_g17_d128", 384, 384, 6.0, 17, 0.001, 100.0, 4, 32, 2, 1, n_fronts=3),
+    # profiling sizes of the batched pattern's smaller polar counts: 256x256, 17 groups, spacing h/2, one front,
+    # 3 polar x 48 azimuths and 2 polar x 64 azimuths
+    "fc256_g17_p3x48": Workload("fc256_g17_p3x48", 256, 256, 6.0, 17, 0.001, 100.0, 3, 48, 2, 1),
+    "fc256_g17_p2x64": Workload("fc256_g17_p2x64", 256, 256, 6.0, 17, 0.001, 100.0, 2, 64, 2, 1),
     # refinement stress base grid: 128x128, 17 groups, 8 x 64 directions, cold start (spacing set per run)
     "fc128_g17_d512": Workload("fc128_g17_d512", 128, 128, 6.0, 17, 0.001, 100.0, 8, 64, 2, 50,
                                cold_start=True),
