@@ -387,10 +387,13 @@ size_t state_bytes_fp32(const molc_plan *p);
 double *bref_ptr(const molc_plan *p, molc_precision prec, void *I);
 double *header_ptr(const molc_plan *p, molc_precision prec, void *I);
 
-// Autotuner of the FP32 sweep: times each compiled staging depth on this plan (one warm-up and three timed
-// launches of the sweep kernel each, on temporary inputs: kappa = B = boundary = 0, c = dt = 1, an FP32 state
-// initialised from B) and keeps the fastest.  The depth changes no arithmetic, only the timing.  Allocates its
-// temporaries for the duration of the call.
+// Autotuner of the FP32 sweep: times each compiled staging depth on this plan and keeps the fastest.  The
+// temporary inputs have about one optical depth per cell (kappa = 1/min(hx, hy), B = boundary = 1, c = dt = 1),
+// so that both branches of the attenuation run; the FP32 state starts from B.  Each depth is warmed up once,
+// then timed over enough launches to fill about half a millisecond, in two rounds that alternate the depths;
+// a depth's time is its better round.  The default depth is kept unless another is at least 2 % faster (the
+// depths differ by a few percent, less than one short timing's noise).  The depth changes no arithmetic, only
+// the timing.  Allocates its temporaries for the duration of the call.
 molc_status autotune(molc_plan *p, double *best_ms_out) {
   DeviceGuard dg(p->device);
   const int64_t cg = (int64_t)p->G * p->view.ncell;
@@ -401,11 +404,17 @@ molc_status autotune(molc_plan *p, double *best_ms_out) {
   cudaError_t e = cudaMalloc(&I, state_bytes_fp32(p));
   if (e == cudaSuccess) e = cudaMalloc((void **)&in, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void **)&mom, 6 * cg * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(in, 0, (2 * cg + 4 * (int64_t)p->G) * sizeof(double));
+  if (e == cudaSuccess) {
+    std::vector<double> h((size_t)(2 * cg + 4 * (int64_t)p->G), 1.0);
+    std::fill(h.begin(), h.begin() + cg, 1.0 / std::min(p->hx, p->hy));
+    e = cudaMemcpy(in, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  int best = p->view.sweep_depth;
-  float best_ms = 0;
+  constexpr int kDefault = 4;
+  const int nd = (int)(sizeof(kSweepDepths) / sizeof(kSweepDepths[0]));
+  std::vector<float> t(nd, 0.f);   // best time per launch of each depth
+  int reps = 2;
   if (e == cudaSuccess) {
     SweepArgs a{};
     a.kappa = in;
@@ -425,22 +434,29 @@ molc_status autotune(molc_plan *p, double *best_ms_out) {
     if (e == cudaSuccess) e = cudaMemcpy(a.Bref, a.B, cg * sizeof(double), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess) e = launch_set_scale(p->view, MOLC_FP32, a.B, const_cast<double *>(a.scale), nullptr);
     if (e == cudaSuccess) e = launch_prep(p->view, MOLC_FP32, a, nullptr);
-    for (int d : kSweepDepths) {
-      if (e != cudaSuccess) break;
+    auto timed = [&](int d, int n, float &ms) {
       PlanView v = p->view;
       v.sweep_depth = d;
-      e = launch_sweep_fp32(v, a, nullptr);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
-      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_sweep_fp32(v, a, nullptr);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && (best_ms == 0 || ms < best_ms)) {
-        best_ms = ms;
-        best = d;
-      }
+      cudaError_t r = cudaEventRecord(e0, nullptr);
+      for (int k = 0; k < n && r == cudaSuccess; ++k) r = launch_sweep_fp32(v, a, nullptr);
+      if (r == cudaSuccess) r = cudaEventRecord(e1, nullptr);
+      if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+      if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+      return r;
+    };
+    float one = 0.f;
+    for (int i = 0; i < nd && e == cudaSuccess; ++i) {   // warm-up; the default depth's launch sets the count
+      float ms = 0.f;
+      e = timed(kSweepDepths[i], 1, ms);
+      if (kSweepDepths[i] == kDefault) one = ms;
     }
+    if (one > 0.f) reps = std::max(2, std::min(20, (int)std::ceil(0.5f / one)));
+    for (int round = 0; round < 2 && e == cudaSuccess; ++round)
+      for (int i = 0; i < nd && e == cudaSuccess; ++i) {
+        float ms = 0.f;
+        e = timed(kSweepDepths[i], reps, ms);
+        if (e == cudaSuccess && (t[i] == 0.f || ms / reps < t[i])) t[i] = ms / reps;
+      }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -448,8 +464,17 @@ molc_status autotune(molc_plan *p, double *best_ms_out) {
   if (in) cudaFree(in);
   if (I) cudaFree(I);
   if (e != cudaSuccess) return cuda_fail(e, "create: autotune");
+  int best = kDefault;
+  float t_def = 0.f, t_best = 0.f;
+  for (int i = 0; i < nd; ++i)
+    if (kSweepDepths[i] == kDefault) t_def = t_best = t[i];
+  for (int i = 0; i < nd; ++i)
+    if (t[i] > 0.f && t[i] < 0.98f * t_def && t[i] < t_best) {
+      t_best = t[i];
+      best = kSweepDepths[i];
+    }
   p->view.sweep_depth = best;
-  if (best_ms_out) *best_ms_out = best_ms / 3.0;
+  if (best_ms_out) *best_ms_out = t_best;
   int code = 0;
   cudaMemcpy(&code, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemset(p->d_status, 0, sizeof(int));   // the temporaries' checks leave no trace

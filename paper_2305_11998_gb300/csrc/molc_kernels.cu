@@ -377,9 +377,9 @@ __device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
   }
 }
-// Warp-cooperative forms for NP not a multiple of 4: the 32 threads of a warp hold 32 x NP consecutive floats of
-// a bundle step slot (128 NP bytes, 16-byte aligned), moved as 8 NP pieces of 16 bytes by the first 8 NP lanes
-// (one instruction per lane for NP <= 4) instead of NP scalar or NP/2 paired accesses per thread.
+// Warp-cooperative forms for odd NP: the 32 threads of a warp hold 32 x NP consecutive floats of a bundle step
+// slot (128 NP bytes, 16-byte aligned), moved as 8 NP pieces of 16 bytes by the first 8 NP lanes (one
+// instruction per lane for NP <= 4) instead of NP scalar accesses per thread.
 template <int NP>
 __device__ __forceinline__ void copy_warp_chunk_async(float *dst_smem, const float *src, int lane) {
   constexpr int kPieces = 8 * NP;
@@ -440,11 +440,10 @@ __device__ __forceinline__ int2 ld_record(const int2 *p) {
 // Group accounting: the prologue commits D-1 groups (deviations of steps 0..D-2, table entries of steps
 // 0..D-3) and step s commits one; step s's deviations are in group s and its table entry in group s+1 (group s
 // for s <= D-3), so waiting until at most D-2 groups are pending is enough.
-// For NP not a multiple of 4 the deviations of a step are copied for the whole warp by its first 8 NP lanes
-// (every lane then runs the warp's longest track's steps, the copies and commits warp-uniform, a __syncwarp
-// making the landed copies visible to the other lanes and ordering the reads of a slot before its refill); for
-// odd NP the new deviations also go back through the slot: each thread writes its own, the warp stores the
-// slot's chunk in 16-byte pieces.  A thread whose track has ended leaves its part of the slot as it was copied,
+// For odd NP the deviations of a step are copied for the whole warp by its first 8 NP lanes (every lane then
+// runs the warp's longest track's steps, the copies and commits warp-uniform, a __syncwarp making the landed
+// copies visible to the other lanes and ordering the reads of a slot before its refill), and the new deviations
+// go back through the slot: each thread writes its own, the warp stores the slot's chunk in 16-byte pieces.  A thread whose track has ended leaves its part of the slot as it was copied,
 // so the padding it stores back is unchanged.
 // What an FP32 sweep adds to the segment update: nothing, the face reductions of Eq. 16 (MOLC_FACES), or the
 // per-ray balance check (MOLC_BALANCE).
@@ -464,8 +463,8 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
                                                 SweepSmem<NP, D> &sm) {
   static_assert(D >= 3, "the staging depth needs D >= 3");
   constexpr bool FACES = EXTRA == kSweepFaces, BAL = EXTRA == kSweepBalance;
-  constexpr bool COOP = NP % 4 != 0;       // warp-cooperative copies of the deviations
-  constexpr bool COOP_ST = NP % 2 != 0;    // ... and stores
+  constexpr bool COOP = NP % 2 != 0;       // warp-cooperative copies and stores of the deviations (odd NP; even NP
+  constexpr bool COOP_ST = COOP;           // already copies 8 or 16 bytes per thread, and NP = 2 measured slower)
   constexpr int kSteps = D;
   auto &sdev = sm.dev;
   auto &stab = sm.tab;

@@ -144,7 +144,7 @@ def test_batch_rejects_bad_arguments(molc):
     batch.close()
 
 
-# one instance per polar count 1-4 (NP not a multiple of 4 takes the warp-cooperative state copies), G = 37 over
+# one instance per polar count 1-4 (odd NP takes the warp-cooperative state copies), G = 37 over
 # two group chunks, and an instance with twice the ray density
 ORACLE_SHAPES = [(16, 5, 1, 16, 2), (20, 6, 2, 24, 2), (24, 4, 3, 32, 4), (16, 37, 3, 16, 2), (12, 8, 4, 16, 2)]
 
