@@ -18,11 +18,6 @@ def env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def instance_seed(base: int, rank: int) -> int:
-    """Seed of the instance a rank sweeps in a weak-scaling run (each rank its own seeded instance)."""
-    return base + rank
-
-
 def shard_groups(G: int, world: int, rank: int) -> range:
     """Contiguous group range of a rank when one instance is split by groups: sizes differ by at most one
     (every group costs the same number of updates), lower ranks take the extra groups."""
@@ -73,9 +68,3 @@ def max_over_ranks(value: float, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
-
-
-def weak_scaling_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
-    """Whole-job throughput when every rank processes the same units: all ranks' units over the slowest rank's
-    time."""
-    return units_per_rank * world / seconds_max

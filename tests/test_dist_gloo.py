@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out_dir):
         import oracle
         import synth
         wl = synth.WORKLOADS["fc16_g4_d32"]
-        d = wl.inputs(pdist.instance_seed(3, 0))      # every rank holds the same instance here
+        d = wl.inputs(3)      # every rank holds the same instance here
         geom = oracle.Geometry.from_workload(wl)
         groups = list(pdist.shard_groups(wl.G, ws, rk))
         r = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], groups=groups, precision="double",
@@ -64,7 +64,7 @@ def test_two_gloo_ranks_shard_groups_and_reduce_time(tmp_path):
     import synth
     wl = synth.WORKLOADS["fc16_g4_d32"]
     assert sorted(covered.tolist()) == list(range(wl.G))
-    d = wl.inputs(pdist.instance_seed(3, 0))
+    d = wl.inputs(3)
     full = oracle.sweep(oracle.Geometry.from_workload(wl), d["kappa"], d["B"], d["c"], d["dt"], d["bnd"],
                         precision="double", want_I=False, threads=1)
     for x in res:
@@ -85,10 +85,10 @@ def test_shard_groups_cover_and_balance():
         pdist.shard_groups(4, 2, 2)
 
 
-def test_weak_scaling_rate_and_local_reduction():
-    assert pdist.weak_scaling_rate(1.0e9, 4, 2.0) == 2.0e9
+def test_local_reduction_and_gather():
     assert pdist.max_over_ranks(3.5) == 3.5      # not distributed: the value itself
-    assert pdist.instance_seed(0, 3) == 3
+    local = torch.arange(6.0).reshape(2, 3)
+    assert pdist.gather_groups(local, 2, range(0, 2), 1) is local
 
 
 def test_shard_inputs_slice_groups():
