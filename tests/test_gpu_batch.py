@@ -182,3 +182,44 @@ def test_batched_instances_vs_binary128(molc):
         assert P.device_status() == 0
         P.close()
     batch.close()
+
+
+def test_batch64_at_full_size_sampled_vs_binary128(molc):
+    """The batched pattern at its benchmark size: the 64 seeded instances of synth.batch_instances (38.6 GB of FP32
+    state) stepped once by molc_batch_sweep; for the largest instance with 2 and with 3 polar cosines (4: the 512^2
+    test of test_gpu_misc.py), the group holding the Planck peak of the hot region (1 keV) is checked against the
+    binary128 oracle, the floor of the relative metric taken over all groups of that instance's GPU output.
+    (Default staging depths: the autotuner's choice changes no arithmetic.)"""
+    import oracle
+    import parity
+    wls = synth.batch_instances(64)
+    plans = [molc.Plan.from_workload(wl) for wl in wls]
+    ins = [wl.inputs(seed=wl.extra["seed"]) for wl in wls]
+    args = [new_args(P, wl, d, closure=False) for wl, d, P in zip(wls, ins, plans)]
+    batch = molc.Batch(plans)
+    batch.bind(args)
+    batch.sweep()
+    torch.cuda.synchronize()
+    assert all(P.device_status() == 0 for P in plans)
+    assert sum(P.info.n_updates for P in plans) > 9e9
+    largest = {}
+    for i, (wl, P) in enumerate(zip(wls, plans)):
+        if wl.n_polar not in largest or P.info.n_updates > plans[largest[wl.n_polar]].info.n_updates:
+            largest[wl.n_polar] = i
+    assert sorted(largest) == [2, 3, 4]
+    results = {}
+    del largest[4]
+    for npol, i in largest.items():
+        results[i] = {k: v.cpu().numpy() for k, v in args[i]["out"].items()}
+    batch.close()
+    for P in plans:
+        P.close()
+    del args
+    torch.cuda.empty_cache()
+    for npol, i in sorted(largest.items()):
+        wl, d, got = wls[i], ins[i], results[i]
+        edges = wl.edges()
+        g = int(np.searchsorted(edges, 2.8, side="right") - 1)     # group of the 1 keV Planck peak (2.82 kT)
+        ref = parity.reference(oracle.Geometry.from_workload(wl), d, "fp32", wl.n_polar, groups=[g])
+        fm = {k: float(np.abs(v).max()) for k, v in got.items()}
+        parity.compare({k: v[[g]] for k, v in got.items()}, ref, "fp32", d["c"], floor_max=fm)
