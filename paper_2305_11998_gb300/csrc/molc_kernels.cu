@@ -805,20 +805,26 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
     two_sum_add(hi[4], lo[4], (cf * sf) * P2);
     two_sum_add(hi[5], lo[5], (sf * sf) * P2);
   };
-  // the entries of the next batch are loaded while this batch's state loads are in flight
+  // up to 3 polar cosines the entries of the next batch are loaded while this batch's state loads are in flight;
+  // at 4 that costs the occupancy it buys (measured with the factors formed here), so each batch loads its own
+  constexpr bool kPrefetch = NP <= 3;
   int4 en[kGatherBatch];
-  if (ne > 0) {
+  if (kPrefetch && ne > 0) {
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + b);
   }
   for (int e = 0; e < ne; e += kGatherBatch) {
+    if constexpr (!kPrefetch) {
+#pragma unroll
+      for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + b);
+    }
     float dv[kGatherBatch][NP];
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) load_dev_cg<NP>(I + gather_slot(en[b].x, en[b].y, gi) * NP, dv[b]);
     int2 zw[kGatherBatch];
 #pragma unroll
     for (int b = 0; b < kGatherBatch; ++b) zw[b] = make_int2(en[b].z, en[b].w);
-    if (e + kGatherBatch < ne) {
+    if (kPrefetch && e + kGatherBatch < ne) {
 #pragma unroll
       for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + kGatherBatch + b);
     }
@@ -889,17 +895,17 @@ __global__ void __launch_bounds__(128) moments_combine_batch_kernel(const BatchI
   moments_combine_body(b.v, b.a, b.L, m.y, (int64_t)m.z * blockDim.x);
 }
 
-// blocks per SM: 7 up to 3 polar cosines, 6 at 4 (80 registers: the next batch's entries are loaded while the
-// current batch's state loads are in flight), 5 beyond
+// blocks per SM: 7 up to 3 polar cosines (72 registers: the next batch's entries are loaded while the current
+// batch's state loads are in flight), 8 at 4, 5 beyond
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 6 : 5)
+__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 8 : 5)
     moments_fp32_kernel(PlanView v, SweepArgs a, Layout L) {
   moments_fp32_body<NP>(v, a, L, blockIdx.y, (int64_t)blockIdx.x * blockDim.x);
 }
 
 // Batched: block j handles threads 128 map[j].z .. of chunk map[j].y of instance map[j].x.
 template <int NP>
-__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 6 : 5)
+__global__ void __launch_bounds__(128, NP <= 3 ? 7 : NP == 4 ? 8 : 5)
     moments_fp32_batch_kernel(const BatchInst *inst, const int4 *map) {
   const int4 m = map[blockIdx.x];
   const BatchInst &b = inst[m.x];
