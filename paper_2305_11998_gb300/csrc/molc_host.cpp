@@ -6,12 +6,14 @@
 // in-plane track depends only on the azimuth; the 3D path length is l / sin(zeta), Eq. 13).
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -153,6 +155,28 @@ struct DeviceGuard {
     if (changed) cudaSetDevice(prev);
   }
 };
+
+// f(i) for i in [0, n) on up to the host's hardware threads (each index once, in no fixed order); the planner's
+// independent loops (one azimuth pair, one chunk's entries) write disjoint outputs, so the plan is the same as
+// from a serial loop.
+// Small plans (threaded = false) run the loop serially: starting the threads would cost more than the work.
+template <class F>
+void parallel_for(int64_t n, F f, bool threaded = true) {
+  const int64_t nt =
+      threaded ? std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)std::thread::hardware_concurrency())) : 1;
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next(0);
+  std::vector<std::thread> th;
+  th.reserve((size_t)nt);
+  for (int64_t k = 0; k < nt; ++k)
+    th.emplace_back([&]() {
+      for (int64_t i; (i = next.fetch_add(1)) < n;) f(i);
+    });
+  for (auto &x : th) x.join();
+}
 
 // Offsets (along n = (-s, c)) and widths of the characteristics of one azimuth, ordered by offset.
 void characteristic_offsets(const molc_grid &g, double c, double s, double spacing, molc_layout layout,
@@ -835,31 +859,67 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
 
   // ---- characteristics and segments, pair by pair
   const int ncell = g.nx * g.ny;
-  std::vector<double> t, wv;
-  std::vector<int> cells;
-  std::vector<double> lens, lens_lo, seg_len_lo;
-  p->pair_track_off.push_back(0);
-  for (int j = 0; j < p->n_pairs; ++j) {
+  // each pair traced on its own (in parallel), then concatenated in pair order
+  struct PairTracks {
+    std::vector<HostTrack> tracks;   // seg_off relative to this pair's first segment
+    std::vector<int> cell;
+    std::vector<double> len, afrac, len_lo;
+    bool too_long = false;
+  };
+  std::vector<PairTracks> per_pair((size_t)p->n_pairs);
+  const bool big = (int64_t)ncell * p->n_pairs >= ((int64_t)1 << 17);   // threads pay off (from ~1e5 cell-pairs)
+  parallel_for(p->n_pairs, [&](int64_t j) {
+    PairTracks &o = per_pair[(size_t)j];
+    std::vector<double> t, wv, lens, lens_lo;
+    std::vector<int> cells;
     const double c = p->pairs[j].c, s = p->pairs[j].s;
     characteristic_offsets(g, c, s, ray_spacing, layout, t, wv);
     for (size_t k = 0; k < t.size(); ++k) {
       int ep, em;
       if (!cut_characteristic(g, p->hx, p->hy, c, s, t[k], cells, lens, lens_lo, ep, em)) continue;
       if (cells.size() > (size_t)1 << 30) {
-        delete p;
-        return fail(MOLC_ERR_INVALID_ARG, "create: characteristic too long");
+        o.too_long = true;
+        return;
       }
-      HostTrack ht{wv[k], ep, em, (int64_t)p->seg_cell.size(), (int)cells.size()};
-      p->tracks.push_back(ht);
+      o.tracks.push_back(HostTrack{wv[k], ep, em, (int64_t)o.cell.size(), (int)cells.size()});
       for (size_t q = 0; q < cells.size(); ++q) {
-        p->seg_cell.push_back(cells[q]);
-        p->seg_len.push_back(lens[q]);
-        p->seg_afrac.push_back(lens[q] * wv[k]);  // A for now
-        seg_len_lo.push_back(lens_lo[q]);
+        o.cell.push_back(cells[q]);
+        o.len.push_back(lens[q]);
+        o.afrac.push_back(lens[q] * wv[k]);  // A for now
+        o.len_lo.push_back(lens_lo[q]);
       }
     }
-    p->pair_track_off.push_back((int64_t)p->tracks.size());
+  }, big);
+  // offsets of each pair's tracks and segments, then every pair copied into place (in parallel)
+  std::vector<int64_t> seg_base((size_t)p->n_pairs + 1, 0);
+  p->pair_track_off.assign((size_t)p->n_pairs + 1, 0);
+  for (int j = 0; j < p->n_pairs; ++j) {
+    const PairTracks &o = per_pair[(size_t)j];
+    if (o.too_long) {
+      delete p;
+      return fail(MOLC_ERR_INVALID_ARG, "create: characteristic too long");
+    }
+    p->pair_track_off[(size_t)j + 1] = p->pair_track_off[(size_t)j] + (int64_t)o.tracks.size();
+    seg_base[(size_t)j + 1] = seg_base[(size_t)j] + (int64_t)o.cell.size();
   }
+  std::vector<double> seg_len_lo((size_t)seg_base[(size_t)p->n_pairs]);
+  p->tracks.resize((size_t)p->pair_track_off[(size_t)p->n_pairs]);
+  p->seg_cell.resize(seg_len_lo.size());
+  p->seg_len.resize(seg_len_lo.size());
+  p->seg_afrac.resize(seg_len_lo.size());
+  parallel_for(p->n_pairs, [&](int64_t j) {
+    PairTracks &o = per_pair[(size_t)j];
+    const int64_t t0 = p->pair_track_off[(size_t)j], s0 = seg_base[(size_t)j];
+    for (size_t k = 0; k < o.tracks.size(); ++k) {
+      p->tracks[(size_t)t0 + k] = o.tracks[k];
+      p->tracks[(size_t)t0 + k].seg_off += s0;
+    }
+    std::copy(o.cell.begin(), o.cell.end(), p->seg_cell.begin() + s0);
+    std::copy(o.len.begin(), o.len.end(), p->seg_len.begin() + s0);
+    std::copy(o.afrac.begin(), o.afrac.end(), p->seg_afrac.begin() + s0);
+    std::copy(o.len_lo.begin(), o.len_lo.end(), seg_len_lo.begin() + s0);
+    o = PairTracks{};   // released as they are copied
+  }, big);
   const int64_t T = (int64_t)p->tracks.size();
   const int64_t S = (int64_t)p->seg_cell.size();
   if (T == 0) {
@@ -873,13 +933,15 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
   // the paper's layout it is ~1e-15 (double band edges), and N_xy's B part, sum_j W_xy(j) e_ij, is a small
   // sum that must not carry the rounding of sum_j W_xy(j) (which is exactly zero for a symmetric set).
   const bool renorm = flags & MOLC_AREA_RENORM;
-  std::vector<double> asum(ncell);
-  std::vector<Acc2> asum_dd(ncell);
   std::vector<Acc2> g0(ncell), gxx(ncell), gxy(ncell), gyy(ncell);
   Acc2 w0_all, wxx_all, wxy_all, wyy_all;
-  for (int j = 0; j < p->n_pairs; ++j) {
-    std::fill(asum.begin(), asum.end(), 0.0);
-    std::fill(asum_dd.begin(), asum_dd.end(), Acc2());
+  // per pair (in parallel): the area sums of its characteristics per cell, the area fractions, and without
+  // renormalisation the area defects e_ij; a pair that misses a cell records the first such cell
+  std::vector<std::vector<double>> defect(renorm ? 0 : (size_t)p->n_pairs);
+  std::vector<int> missed((size_t)p->n_pairs, -1);
+  parallel_for(p->n_pairs, [&](int64_t j) {
+    std::vector<double> asum(ncell, 0.0);
+    std::vector<Acc2> asum_dd(renorm ? 0 : ncell);
     const int64_t s0 = p->tracks[p->pair_track_off[j]].seg_off;
     const int64_t s1 = p->pair_track_off[j + 1] < T ? p->tracks[p->pair_track_off[j + 1]].seg_off : S;
     for (int64_t k = p->pair_track_off[j]; k < p->pair_track_off[j + 1]; ++k) {
@@ -887,23 +949,38 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
       for (int64_t q = p->tracks[k].seg_off; q < p->tracks[k].seg_off + p->tracks[k].nseg; ++q) {
         const int i = p->seg_cell[q];
         asum[i] += p->seg_afrac[q];
-        const double pa = p->seg_len[q] * w;
-        asum_dd[i].add(pa);
-        asum_dd[i].add(std::fma(p->seg_len[q], w, -pa));
-        asum_dd[i].add(seg_len_lo[q] * w);
+        if (!renorm) {
+          const double pa = p->seg_len[q] * w;
+          asum_dd[i].add(pa);
+          asum_dd[i].add(std::fma(p->seg_len[q], w, -pa));
+          asum_dd[i].add(seg_len_lo[q] * w);
+        }
       }
     }
     if (renorm) {
       for (int i = 0; i < ncell; ++i)
         if (!(asum[i] > 0)) {
-          delete p;
-          return fail(MOLC_ERR_INVALID_ARG,
-                      "create: cell %d is crossed by no characteristic of azimuth pair %d; reduce ray_spacing", i, j);
+          missed[(size_t)j] = i;
+          return;
         }
       for (int64_t q = s0; q < s1; ++q) p->seg_afrac[q] /= asum[p->seg_cell[q]];
     } else {
       for (int64_t q = s0; q < s1; ++q) p->seg_afrac[q] /= p->V;
+      std::vector<double> &e = defect[(size_t)j];
+      e.resize(ncell);
+      for (int i = 0; i < ncell; ++i) e[i] = ((asum_dd[i].hi - p->V) + asum_dd[i].lo) / p->V;
     }
+  }, big);
+  for (int j = 0; j < p->n_pairs; ++j)
+    if (missed[(size_t)j] >= 0) {
+      const int i = missed[(size_t)j];
+      delete p;
+      return fail(MOLC_ERR_INVALID_ARG,
+                  "create: cell %d is crossed by no characteristic of azimuth pair %d; reduce ray_spacing", i, j);
+    }
+  // in pair order: the pairs' angular weights and, without renormalisation, the defect terms of the geometric
+  // moments
+  for (int j = 0; j < p->n_pairs; ++j) {
     // sum over the pair's directions of omega (times Omega components)
     double w0 = 0, wxx = 0, wxy = 0, wyy = 0;
     const double c = p->pairs[j].c, s = p->pairs[j].s;
@@ -919,14 +996,16 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     wxx_all.add(wxx);
     wxy_all.add(wxy);
     wyy_all.add(wyy);
-    if (!renorm)
+    if (!renorm) {
+      const std::vector<double> &e = defect[(size_t)j];
       for (int i = 0; i < ncell; ++i) {
-        const double e = ((asum_dd[i].hi - p->V) + asum_dd[i].lo) / p->V;
-        g0[i].add(w0 * e);
-        gxx[i].add(wxx * e);
-        gxy[i].add(wxy * e);
-        gyy[i].add(wyy * e);
+        g0[i].add(w0 * e[i]);
+        gxx[i].add(wxx * e[i]);
+        gxy[i].add(wxy * e[i]);
+        gyy[i].add(wyy * e[i]);
       }
+      std::vector<double>().swap(defect[(size_t)j]);
+    }
   }
   for (int i = 0; i < ncell; ++i) {
     g0[i].add(w0_all.value());
@@ -1061,45 +1140,61 @@ molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, cons
     for (int i = 0; i < ncell; ++i) cell_off[i + 1] = cell_off[i] + (cnt[i] + kGatherPad - 1) / kGatherPad * kGatherPad;
     gent.assign((size_t)cell_off[ncell], make_int4(0, 0, 0, 0));
     std::vector<int64_t> pos(cell_off.begin(), cell_off.end() - 1);
-    for (int64_t k = 0; k < T; ++k) {
-      const TrackDev &t = td[k];
-      for (int j = 0; j < t.nseg; ++j) {
-        const int64_t q = t.seg_off + j;
-        const float af = (float)p->seg_afrac[q];
-        int afb;
-        std::memcpy(&afb, &af, 4);
-        const int c = p->seg_cell[q];
-        gent[pos[c]++] = make_int4(t.pos[0], j, afb, 2 * t.pair);
-        gent[pos[c]++] = make_int4(t.pos[1], t.nseg - 1 - j, afb, 2 * t.pair + 1);
+    // in parallel over ranges of cells: every range scans all tracks in order and writes its own cells' entries,
+    // so each list is in track order as from one serial scan
+    const int64_t n_ranges = std::min<int64_t>(ncell, 4 * (int64_t)std::max(1u, std::thread::hardware_concurrency()));
+    parallel_for(n_ranges, [&](int64_t r) {
+      const int c_lo = (int)(ncell * r / n_ranges), c_hi = (int)(ncell * (r + 1) / n_ranges);
+      for (int64_t k = 0; k < T; ++k) {
+        const TrackDev &t = td[k];
+        for (int j = 0; j < t.nseg; ++j) {
+          const int64_t q = t.seg_off + j;
+          const int c = p->seg_cell[q];
+          if (c < c_lo || c >= c_hi) continue;
+          const float af = (float)p->seg_afrac[q];
+          int afb;
+          std::memcpy(&afb, &af, 4);
+          gent[pos[c]++] = make_int4(t.pos[0], j, afb, 2 * t.pair);
+          gent[pos[c]++] = make_int4(t.pos[1], t.nseg - 1 - j, afb, 2 * t.pair + 1);
+        }
       }
-    }
-    for (int i = 0; i < ncell; ++i)
-      for (int64_t e = pos[i]; e < cell_off[i + 1]; ++e) {
-        gent[e] = gent[pos[i] - 1];
-        gent[e].z = 0;   // zero area
-      }
+      for (int i = c_lo; i < c_hi; ++i)
+        for (int64_t e = pos[i]; e < cell_off[i + 1]; ++e) {
+          gent[e] = gent[pos[i] - 1];
+          gent[e].z = 0;   // zero area
+        }
+    }, big);
     // Per chunk, the (item position, step) of each entry becomes the state slot of the chunk's group 0 plus the
     // bundle length and lane (gather_slot); chunks 1.. are written from the chunk-0 list first, chunk 0 last,
     // in place.
     const int64_t n_ent = cell_off[ncell];
     gent.resize((size_t)(n_ent * nch32));
+    std::atomic<bool> too_large(false);
     for (int ch = nch32 - 1; ch >= 0; --ch) {
       const int gcount = std::min(gc32, p->G - ch * gc32);
       const int64_t item_base = (int64_t)ch * 2 * T * gc32;
-      for (int64_t e = 0; e < n_ent; ++e) {
-        int4 r = gent[e];
-        const int64_t item = item_base + (int64_t)r.x * gcount;
-        const int64_t b = item / kSweepBlock;
-        const int lane = (int)(item % kSweepBlock);
-        const int64_t slot = (boff[b] + r.y) * kSweepBlock + lane;
-        const int64_t blen = boff[b + 1] - boff[b];
-        if ((slot >> (32 + (32 - kGatherSlotHiShift))) != 0 || blen > (int64_t)kGatherBlenMask) {
-          delete p;
-          return fail(MOLC_ERR_INVALID_ARG, "create: FP32 state too large for the moment-gather entries");
+      const int64_t n_blocks = (n_ent + 65535) / 65536;   // entries in blocks of 64 Ki, in parallel
+      parallel_for(n_blocks, [&](int64_t blk) {
+        const int64_t e1 = std::min(n_ent, (blk + 1) * 65536);
+        for (int64_t e = blk * 65536; e < e1; ++e) {
+          int4 r = gent[e];
+          const int64_t item = item_base + (int64_t)r.x * gcount;
+          const int64_t b = item / kSweepBlock;
+          const int lane = (int)(item % kSweepBlock);
+          const int64_t slot = (boff[b] + r.y) * kSweepBlock + lane;
+          const int64_t blen = boff[b + 1] - boff[b];
+          if ((slot >> (32 + (32 - kGatherSlotHiShift))) != 0 || blen > (int64_t)kGatherBlenMask) {
+            too_large = true;
+            return;
+          }
+          r.x = (int)(uint32_t)(slot & 0xffffffffLL);
+          r.y = (int)(((uint32_t)(slot >> 32) << kGatherSlotHiShift) | ((uint32_t)blen << 7) | (uint32_t)lane);
+          gent[(size_t)(ch * n_ent + e)] = r;
         }
-        r.x = (int)(uint32_t)(slot & 0xffffffffLL);
-        r.y = (int)(((uint32_t)(slot >> 32) << kGatherSlotHiShift) | ((uint32_t)blen << 7) | (uint32_t)lane);
-        gent[(size_t)(ch * n_ent + e)] = r;
+      }, big);
+      if (too_large) {
+        delete p;
+        return fail(MOLC_ERR_INVALID_ARG, "create: FP32 state too large for the moment-gather entries");
       }
     }
   }
