@@ -151,8 +151,10 @@ molc_status molc_quadrature_product(int n_polar, int n_azim, double *mu, double 
                                     double *w);
 
 /* Build the characteristic grid on the host (Sec. 3) and upload it to the current CUDA device.
- * ray_spacing: h_moc in cm (> 0).  flags: MOLC_AREA_RENORM or 0.  groups->G fixes the group count of every
- * later call.  On success *out owns device memory until molc_destroy(). */
+ * ray_spacing: h_moc in cm (> 0).  flags: MOLC_AREA_RENORM, MOLC_HOST_ONLY, MOLC_AUTOTUNE, MOLC_FACES, MOLC_BALANCE,
+ * MOLC_TILED (see above) or 0.  groups->G fixes the group count of every later call.  Larger grids are planned on
+ * up to one host thread per hardware thread (the threads end before the call returns; the plan is the same as
+ * from one thread).  On success *out owns device memory until molc_destroy(). */
 molc_status molc_create(const molc_grid *grid, const molc_quadrature *quad, const molc_groups *groups,
                         double ray_spacing, molc_layout layout, unsigned flags, molc_plan **out);
 
