@@ -815,6 +815,10 @@ __device__ __forceinline__ void moments_fp32_body(const PlanView &v, const Sweep
   }
   for (int e = 0; e < ne; e += kGatherBatch) {
     if constexpr (!kPrefetch) {
+      // the line holding the entries two batches ahead is fetched into L2 now (no registers held): the entry
+      // loads below then hit in cache instead of waiting on DRAM before the state loads that depend on them
+      if (e + 2 * kGatherBatch < ne)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ep + e + 2 * kGatherBatch));
 #pragma unroll
       for (int b = 0; b < kGatherBatch; ++b) en[b] = __ldg(ep + e + b);
     }
