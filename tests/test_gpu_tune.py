@@ -112,3 +112,20 @@ def test_tiled_configuration_recorded_and_reused(molc, path):
         assert np.array_equal(m_t[k], m_t2[k]), k
     for P in (T, T2, R):
         P.close()
+
+
+def test_unwritable_cache_leaves_plans_tuned(molc, tmp_path):
+    """A cache path whose directory does not exist reads as an empty cache; tuning still runs and the plan is
+    created, the entry is simply not recorded."""
+    path = tmp_path / "no_such_dir" / "tune.json"
+    try:
+        assert molc.tune_cache(str(path)) == 0
+        P = molc.Plan.from_workload(WL, autotune=True)
+        assert P.info.tuned_from_cache == 0 and P.info.fp32_sweep_depth in (3, 4, 6)
+        assert not path.exists()
+        Q = molc.Plan.from_workload(WL, autotune=True)          # nothing recorded: tuned again
+        assert Q.info.tuned_from_cache == 0
+        P.close()
+        Q.close()
+    finally:
+        molc.tune_cache(None)
