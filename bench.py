@@ -195,6 +195,13 @@ def cpu_oracle_sample(wl, d, max_seconds=12.0):
                       f"({done_updates:.3e} updates, {dt:.1f} s, characteristic grid rebuilt per call)"}
 
 
+def workload_name(wl):
+    """The workload string both arms print in `config`."""
+    fronts = {1: "one front", 3: "three fronts"}.get(wl.n_fronts, f"{wl.n_fronts} fronts")
+    return (f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, {wl.n_polar}x{wl.n_azim} directions, spacing "
+            f"h/{wl.spacing_div}, {fronts}; one instance, its groups split over the GPUs")
+
+
 def run_reference(args):
     ws, rank, _ = pdist.env()
     if rank != 0:
@@ -220,10 +227,8 @@ def run_reference(args):
     value = nseg * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, "
-                                   f"{wl.n_polar}x{wl.n_azim} directions, spacing h/{wl.spacing_div}",
-                       "sample_per_step": "one group of one sweep (groups rotate)"},
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(wl), "sample_per_step": "one group of one sweep (groups rotate)"},
             "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
                              "sample": f"one of {wl.G} groups per step, {nseg:.3e} updates per step"},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -465,9 +470,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} cells, {wl.G} groups, {wl.n_polar}x{wl.n_azim} "
-                                       f"directions, spacing h/{wl.spacing_div}, three fronts; one instance, its "
-                                       f"groups split over the GPUs",
+                "config": {"workload": workload_name(wl),
                            "updates_per_step": updates_total,
                            "parallelism": f"groups over {ws} GPU(s): rank 0 sweeps groups {groups.start}-"
                                           f"{groups.stop - 1}",
