@@ -8,7 +8,7 @@
 //
 // Everything is templated on the real type R and instantiated twice: R = double, and R = IEEE binary128
 // (__float128 with libquadmath on x86-64, long double on AArch64).  The binary128 instance is the reference
-// the GPU paths are judged against; the double instance is the timed CPU baseline.
+// the GPU paths are checked against; the double instance is the timed CPU baseline.
 //
 // What it computes, in the paper's order and notation (Sec. 3):
 //   * characteristic grid: for each direction, parallel characteristics of width w_k, cut into segments at
