@@ -27,13 +27,15 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
 
 
-CASES = [("fc16_g4_d32", "uniform"), ("fc16_g4_d32", "paper"), ("fc64_g17_d128", "uniform")]
+# three polar cosines: the sweeps' odd-NP path (warp-cooperative state copies) with the balance check
+EXTRA = {"np3_20": synth.Workload("np3_20", 20, 20, 6.0, 5, 0.001, 100.0, 3, 16, 2, 1)}
+CASES = [("fc16_g4_d32", "uniform"), ("fc16_g4_d32", "paper"), ("fc64_g17_d128", "uniform"), ("np3_20", "uniform")]
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 4e-6)])
 @pytest.mark.parametrize("name,layout", CASES)
 def test_ray_balance_holds_and_changes_nothing(molc, prec, tol, name, layout):
-    wl = synth.WORKLOADS[name]
+    wl = EXTRA[name] if name in EXTRA else synth.WORKLOADS[name]
     spacing = wl.spacing if layout == "uniform" else wl.h / 1.5
     kw = dict(spacing=spacing, layout=layout, renorm=(layout == "uniform"))
     # the check's plan, a plan with the face reductions and a plain plan sweep with the bundle FP32 kernel: the

@@ -51,6 +51,27 @@ def test_full_size_512_sampled_groups(molc):
     parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp32", d["c"], floor_max=fm)
 
 
+def test_full_size_512_fp64_sampled_group(molc):
+    """The plain FP64 sweep (the speed-up denominator of the benchmark) at the production size in the launch
+    configuration the benchmark times, the group holding the Planck peak of the hot region against the binary128
+    oracle at the FP64 tolerance."""
+    wl = synth.WORKLOADS["fc512_g17_d128"]
+    d = wl.inputs(0)
+    P = molc.Plan.from_workload(wl)
+    B = dev(d["B"])
+    I = P.new_intensity("fp64")
+    P.intensity_init("fp64", I, B)
+    got = host(P.sweep("fp64", dev(d["kappa"]), B, d["c"], d["dt"], I, dev(d["bnd"])))
+    assert P.device_status() == 0
+    P.close()
+    del I
+    torch.cuda.empty_cache()
+    groups = [11]
+    ref = parity.reference(oracle.Geometry.from_workload(wl), d, "fp64", wl.n_polar, groups=groups)
+    fm = {k: float(np.abs(v).max()) for k, v in got.items()}
+    parity.compare({k: v[groups] for k, v in got.items()}, ref, "fp64", d["c"], floor_max=fm)
+
+
 def test_closure_and_grey_average(molc):
     wl = synth.WORKLOADS["fc16_g4_d32"]
     d = wl.inputs(3)
