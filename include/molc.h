@@ -227,11 +227,13 @@ molc_status molc_sweep_static_scratch(molc_plan *plan, molc_precision prec, cons
                                       const molc_moments *out, molc_stream stream);
 
 /* ---- Batched FP32 sweep of many independent instances (Eqs. 7, 11-15 for each; plans of any sizes, group counts
- * and quadratures on one device): every step runs as one launch of each kernel over the work of all instances (one
- * sweep launch per distinct (polar count, staging depth) and one moment launch per polar count), with the sweep
- * blocks of all instances scheduled longest first. Built for many uneven problems in one time-stepping loop, where
- * per-instance launches would leave most of the GPU idle. The paper sweeps one problem; this is the production
- * packaging of the same per-instance sweep (results are bit-identical to molc_sweep + molc_closure per instance). */
+ * and quadratures on one device): every step runs as one launch of each kernel over the work of all instances (the
+ * scale update over several blocks per instance, one prep launch, one sweep launch per distinct (polar count,
+ * staging depth) and one moment launch per polar count, in order on the caller's stream), with the sweep blocks of
+ * all instances scheduled longest first; batches of MOLC_TILED plans run one prep and one persistent tiled sweep
+ * launch instead.  Built for many uneven problems in one time-stepping loop, where per-instance launches would
+ * leave most of the GPU idle. The paper sweeps one problem; this is the production packaging of the same
+ * per-instance sweep (results are bit-identical to molc_sweep + molc_closure per instance). */
 typedef struct molc_batch molc_batch;
 
 /* Per-instance arguments, as for molc_sweep (device pointers) plus optional Eddington factors. */
@@ -245,9 +247,9 @@ typedef struct {
 } molc_sweep_args;
 
 /* Builds a batch (no counterpart in the paper: block maps over the instances). plans: host array of n (>= 1) plans
- * created on the current device (not MOLC_HOST_ONLY, MOLC_FACES or MOLC_BALANCE, at most 8 polar cosines;
- * MOLC_ERR_INVALID_ARG otherwise); the batch keeps pointers to them (destroy the batch first). Builds the block
- * maps (device). */
+ * created on the current device (not MOLC_HOST_ONLY, MOLC_FACES or MOLC_BALANCE, at most 8 polar cosines, either
+ * all tiled or none; MOLC_ERR_INVALID_ARG otherwise); the batch keeps pointers to them (destroy the batch first).
+ * Builds the block maps (device). */
 molc_status molc_batch_create(molc_plan *const *plans, int n, molc_batch **out);
 
 /* Record the per-instance arguments of Eqs. 11-15 (and 7) (host array of n, copied to the device synchronously).
