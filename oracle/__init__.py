@@ -53,9 +53,11 @@ class _ErrModel(C.Structure):
 
 
 def _load():
+    """The oracle library: the one build() makes, or the prebuilt library named by MOLC_ORACLE_LIB (the mutation
+    test loads copies of the oracle with a planted mistake this way, in subprocesses of its own)."""
     global _lib
     if _lib is None:
-        lib = C.CDLL(build())
+        lib = C.CDLL(os.environ.get("MOLC_ORACLE_LIB") or build())
         i64p = C.POINTER(C.c_int64)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int)

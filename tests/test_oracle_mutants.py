@@ -1,0 +1,91 @@
+"""The oracle's pins catch plausible mistakes (CPU, no GPU).
+
+Each mutant is a copy of oracle/molc_oracle.cpp with one planted mistake of the kind a restatement of Sec. 3
+could make: a dropped term, a wrong sign, a transposed component, a wrong index.  Every mutant is compiled on its
+own and the pin suites (tests/test_oracle_pins.py, tests/test_golden_single_ray.py) run against it in a
+subprocess (MOLC_ORACLE_LIB); each must fail at least one pin.  A control copy with no mistake, compiled and run
+the same way, must pass them all, so a failure is the mistake's and not the harness's.
+"""
+import os
+import platform
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "molc_oracle.cpp")
+PINS = ["tests/test_oracle_pins.py", "tests/test_golden_single_ray.py"]
+
+# name -> (exact text in the oracle, the mistaken text)
+MUTANTS = {
+    # Eq. 11: the backward-Euler source without its time term I^{n-1}/(c dt)
+    "source_without_time_term": ("const R Q = kap_i * B_i + inv_cdt * Iprev;", "const R Q = kap_i * B_i;"),
+    # Eq. 11: kappa~ without 1/(c dt)
+    "kappa_tilde_without_time_term": ("const R kt = kap_i + inv_cdt;", "const R kt = kap_i;"),
+    # Eq. 13: the optical thickness multiplied by sin(zeta) instead of divided
+    "tau_times_sin_zeta": ("const R tau = kt * r.len[s] / sinz;", "const R tau = kt * r.len[s] * sinz;"),
+    # Eq. 12: the weights of the segment average swapped
+    "alpha_swapped": ("const R Ibar = alpha * I + (R(1) - alpha) * Iout;",
+                      "const R Ibar = (R(1) - alpha) * I + alpha * Iout;"),
+    # Eq. 15: F_x accumulated with the y component of Omega
+    "Fx_with_Omega_y": ("a[MOM_FX * ncell + i] += wA * Ox * Ibar;", "a[MOM_FX * ncell + i] += wA * Oy * Ibar;"),
+    # Eq. 15: N_xy accumulated with Omega_x Omega_x
+    "Nxy_with_Omega_x_squared": ("a[MOM_NXY * ncell + i] += wA * Ox * Oy * Ibar;",
+                                 "a[MOM_NXY * ncell + i] += wA * Ox * Ox * Ibar;"),
+    # Eq. 14: the segment area without the characteristic's width
+    "area_without_width": ("ray.area.push_back((b - a) * width);", "ray.area.push_back((b - a));"),
+    # boundary condition: the incoming intensity of every characteristic read from the first edge
+    "boundary_from_one_edge": ("R I = bnd[r.entry * G + gsel];", "R I = bnd[gsel];"),
+    # the in-plane direction with the sign of its y component flipped
+    "Omega_y_sign": ("const R Ox = sinz * d.dx, Oy = sinz * d.dy;", "const R Ox = sinz * d.dx, Oy = -sinz * d.dy;"),
+    # Eq. 14 with MOLC_AREA_RENORM's reading: the per-(cell, pair) renormalisation of the areas skipped
+    "renormalisation_skipped": ("if (g.renorm) {", "if (false && g.renorm) {"),
+    # Eq. 12: 1 - e^-tau written as e^tau - 1
+    "one_minus_e_sign": ("const R one_m_e = -Fn<R>::expm1(-tau);", "const R one_m_e = Fn<R>::expm1(tau);"),
+    # the zz component of the Eddington tensor with mu once instead of squared
+    "Nzz_mu_once": ("a[MOM_NZZ * ncell + i] += wA * mu * mu * Ibar;", "a[MOM_NZZ * ncell + i] += wA * mu * Ibar;"),
+    # Eq. 16: the face sums take the intensity leaving the segment instead of the one entering at its upwind face
+    "face_downstream_intensity": ("fa[MOM_D * nf + f] += ww * I;", "fa[MOM_D * nf + f] += ww * Iout;"),
+    # Eq. 16: the face F_x with the y component of Omega
+    "face_Fx_with_Omega_y": ("fa[MOM_FX * nf + f] += ww * Ox * I;", "fa[MOM_FX * nf + f] += ww * Oy * I;"),
+}
+
+
+def _compile(src_text, out_dir, name):
+    cpp = os.path.join(out_dir, name + ".cpp")
+    so = os.path.join(out_dir, name + ".so")
+    with open(cpp, "w") as f:
+        f.write(src_text)
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread", "-o", so, cpp]
+    if platform.machine() in ("x86_64", "AMD64"):
+        cmd.append("-lquadmath")
+    subprocess.run(cmd, check=True, capture_output=True)
+    return so
+
+
+def _run_pins(so):
+    env = dict(os.environ, MOLC_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=ROOT,
+                       env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.mark.timeout(900)
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    src = open(SRC).read()
+    variants = {"control": src}
+    for name, (old, new) in MUTANTS.items():
+        assert src.count(old) == 1, name       # the text to mutate is where the pins expect it, once
+        variants[name] = src.replace(old, new)
+    workers = max(1, min(len(variants), os.cpu_count() or 1))
+    with ThreadPoolExecutor(workers) as ex:
+        libs = dict(zip(variants, ex.map(lambda kv: _compile(kv[1], str(tmp_path), kv[0]), variants.items())))
+        results = dict(zip(libs, ex.map(_run_pins, libs.values())))
+    rc, out = results.pop("control")
+    assert rc == 0, "the unmutated oracle must pass the pins:\n" + out
+    survivors = [name for name, (rc, _) in results.items() if rc == 0]
+    assert not survivors, f"mistakes no pin catches: {survivors}"
+    # the pins failed (exit 1), they did not error out (exit 2+: collection or internal errors)
+    assert all(rc == 1 for rc, _ in results.values()), {n: r[0] for n, r in results.items()}

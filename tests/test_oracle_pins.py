@@ -456,3 +456,59 @@ def test_face_moments_equilibrium_closed_form():
             for g in range(G):
                 got = r[k][g, faces] / Bv[g]
                 assert np.max(np.abs(got - e)) <= 1e-13 * ww.sum(), (k, g)
+
+
+@pytest.mark.parametrize("nx,ny,naz,npol", [(2, 1, 4, 2), (2, 2, 8, 1), (3, 2, 8, 2)])
+def test_face_moments_brute_force(nx, ny, naz, npol):
+    """Eq. 16 away from equilibrium: every characteristic walked with the brute-force geometry and RK4 transport;
+    the intensity entering each segment is added, with weight omega w Omega..Omega, to the face it enters through
+    (the entry point's grid line: x first, so a vertex counts on the x-face), then averaged over the face length
+    (E also divided by c).  Catches a face sum that takes another intensity or another component."""
+    rng = np.random.default_rng(7 * nx + 5 * ny + naz + npol)
+    lx, ly, sp = 1.0, 0.8, 0.35
+    q = synth.product_quadrature(npol, naz)
+    geom = make_geom(nx, ny, lx, ly, q, sp)
+    G, ncell = 2, nx * ny
+    kappa = rng.uniform(0.2, 3.0, (G, ncell))
+    B = rng.uniform(0.1, 1.0, (G, ncell))
+    bnd = rng.uniform(0.0, 2.0, (4, G))
+    c, dt = 1.5, 0.5
+    r = oracle.sweep(geom, kappa, B, c, dt, bnd, precision="quad", want_I=False, want_faces=True)
+    hx, hy = lx / nx, ly / ny
+    nxf = (nx + 1) * ny
+    nf = nxf + nx * (ny + 1)
+    acc = np.zeros((6, G, nf))
+    tol = 1e-9 * max(lx, ly)
+    for m in range(q.n):
+        cphi, sphi = bf.unit(q.cos_phi[m], q.sin_phi[m])
+        sinz = math.sqrt(1 - q.mu[m] ** 2)
+        Om = (1.0, sinz * cphi, sinz * sphi)
+        fac = (1.0, Om[1], Om[2], Om[1] * Om[1], Om[1] * Om[2], Om[2] * Om[2])
+        ts, ws = bf.uniform_offsets(lx, ly, cphi, sphi, sp)
+        for t, w in zip(ts, ws):
+            segs, edge = bf.ray_segments(nx, ny, lx, ly, cphi, sphi, t)
+            I = bnd[edge].copy()
+            for cell, L, u in segs:
+                px, py = -t * sphi + u * cphi, t * cphi + u * sphi
+                ix, iy = cell % nx, cell // nx
+                xi = round(px / hx)
+                if abs(px - xi * hx) < tol:
+                    f = iy * (nx + 1) + xi                       # x-face (line xi, row iy)
+                else:
+                    f = nxf + round(py / hy) * nx + ix           # y-face (line, column ix)
+                for k in range(6):
+                    acc[k, :, f] += q.w[m] * w * fac[k] * I
+                for g in range(G):
+                    kt = kappa[g, cell] + 1 / (c * dt)
+                    Q = kappa[g, cell] * B[g, cell] + B[g, cell] / (c * dt)   # I^{n-1} = B
+                    I[g], _ = bf.rk4_segment(I[g], Q, kt, L / sinz)
+    flen = np.where(np.arange(nf) < nxf, hy, hx)
+    names = ("face_E", "face_Fx", "face_Fy", "face_Nxx", "face_Nxy", "face_Nyy")
+    scale = np.abs(acc[0]) / flen
+    for k, name in enumerate(names):
+        want = acc[k] / flen / (c if k == 0 else 1.0)
+        got = r[name]
+        if k == 0:
+            assert np.allclose(got, want, rtol=1e-9, atol=0), name
+        else:
+            assert np.all(np.abs(got - want) <= 1e-9 * scale + 1e-300), name
