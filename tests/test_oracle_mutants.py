@@ -1,13 +1,15 @@
 """The oracle's pins catch plausible mistakes (CPU, no GPU).
 
-Each mutant is a copy of oracle/molc_oracle.cpp with one planted mistake of the kind a restatement of Sec. 3
-could make: a dropped term, a wrong sign, a transposed component, a wrong index.  Every mutant is compiled on its
-own and the pin suites (tests/test_oracle_pins.py, tests/test_golden_single_ray.py) run against it in a
-subprocess (MOLC_ORACLE_LIB); each must fail at least one pin.  A control copy with no mistake, compiled and run
-the same way, must pass them all, so a failure is the mistake's and not the harness's.
+Each mutant is a copy of the oracle with one planted mistake of the kind a restatement of Secs. 2-3 could make: a
+dropped term, a wrong sign, a transposed component, a wrong index or weight.  Mutants of oracle/molc_oracle.cpp
+are compiled on their own and the pin suites (tests/test_oracle_pins.py, tests/test_golden_single_ray.py) run
+against them in a subprocess (MOLC_ORACLE_LIB); mutants of oracle/__init__.py (the closure and grey averages) run
+the same suites from a copied tree.  Each must fail at least one pin.  Control copies with no mistake, built and
+run the same ways, must pass them all, so a failure is the mistake's and not the harness's.
 """
 import os
 import platform
+import shutil
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -50,6 +52,31 @@ MUTANTS = {
     "face_downstream_intensity": ("fa[MOM_D * nf + f] += ww * I;", "fa[MOM_D * nf + f] += ww * Iout;"),
     # Eq. 16: the face F_x with the y component of Omega
     "face_Fx_with_Omega_y": ("fa[MOM_FX * nf + f] += ww * Ox * I;", "fa[MOM_FX * nf + f] += ww * Oy * I;"),
+    # Sec. 3 grid: the uniform layout's characteristics at the band edges instead of their centres
+    "offsets_not_centred": ("t.push_back(tmin + ((double)k + 0.5) * wk);", "t.push_back(tmin + (double)k * wk);"),
+    # Sec. 3 grid: the paper layout's bands split into one more piece at a time instead of halved
+    "bands_not_halved": ("while (gap / (double)pieces > g.spacing) pieces *= 2;",
+                         "while (gap / (double)pieces > g.spacing) pieces += 1;"),
+    # Eq. 11: 1/(c dt) with c left out
+    "time_term_without_c": ("const R inv_cdt = R(1) / (R(c) * R(dt));", "const R inv_cdt = R(1) / R(dt);"),
+}
+
+# the same for the oracle's Python part (oracle/__init__.py): name -> (exact text, the mistaken text)
+PY_MUTANTS = {
+    # Eq. 7: f_xy = N_xy / E, without c
+    "closure_without_c": ("fxy = np.asarray(Nxy) / cE", "fxy = np.asarray(Nxy) / np.asarray(E)"),
+    # Eq. 8 with u = f: the groups' factors averaged without the E weights
+    "grey_eddington_unweighted": ("out.append(np.where(se > 0, (f * E).sum(0) / np.where(se > 0, se, 1.0), 0.0))",
+                                  "out.append(np.where(se > 0, f.sum(0) / E.shape[0], 0.0))"),
+    # Eq. 9: K_R weighted by the signed flux instead of |F|
+    "KR_signed_flux": ("kE, kB, kx, ky = avg(E), avg(B), avg(np.abs(Fx)), avg(np.abs(Fy))",
+                       "kE, kB, kx, ky = avg(E), avg(B), avg(Fx), avg(Fy)"),
+    # Eq. 9: <kappa>_B weighted by E
+    "kappa_B_weighted_by_E": ("kE, kB, kx, ky = avg(E), avg(B), avg(np.abs(Fx)), avg(np.abs(Fy))",
+                              "kE, kB, kx, ky = avg(E), avg(E), avg(np.abs(Fx)), avg(np.abs(Fy))"),
+    # Eq. 9: eta_x formed with K_R's y component
+    "eta_x_with_KRy": ("ex = np.where(se > 0, ((kappa - kx) * Fx).sum(0) / safe, 0.0)",
+                       "ex = np.where(se > 0, ((kappa - ky) * Fx).sum(0) / safe, 0.0)"),
 }
 
 
@@ -65,11 +92,24 @@ def _compile(src_text, out_dir, name):
     return so
 
 
-def _run_pins(so):
+def _run_pins(so, root=ROOT):
     env = dict(os.environ, MOLC_ORACLE_LIB=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=ROOT,
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=root,
                        env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
+
+
+def _py_tree(py_text, out_dir, name):
+    """A copy of what the pin suites import (tests/, synth/, the oracle package) with this oracle/__init__.py."""
+    root = os.path.join(out_dir, name)
+    ignore = shutil.ignore_patterns("__pycache__", "_build")
+    for sub in ("tests", "synth"):
+        shutil.copytree(os.path.join(ROOT, sub), os.path.join(root, sub), ignore=ignore)
+    os.makedirs(os.path.join(root, "oracle"))
+    shutil.copy(SRC, os.path.join(root, "oracle"))
+    with open(os.path.join(root, "oracle", "__init__.py"), "w") as f:
+        f.write(py_text)
+    return root
 
 
 @pytest.mark.timeout(900)
@@ -83,8 +123,17 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     with ThreadPoolExecutor(workers) as ex:
         libs = dict(zip(variants, ex.map(lambda kv: _compile(kv[1], str(tmp_path), kv[0]), variants.items())))
         results = dict(zip(libs, ex.map(_run_pins, libs.values())))
-    rc, out = results.pop("control")
-    assert rc == 0, "the unmutated oracle must pass the pins:\n" + out
+        # the Python mutants run against the control's library from trees of their own
+        py_src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
+        trees = {}
+        for name, (old, new) in PY_MUTANTS.items():
+            assert py_src.count(old) == 1, name
+            trees[name] = _py_tree(py_src.replace(old, new), str(tmp_path), name)
+        trees["py_control"] = _py_tree(py_src, str(tmp_path), "py_control")
+        results.update(zip(trees, ex.map(lambda r: _run_pins(libs["control"], r), trees.values())))
+    for control in ("control", "py_control"):
+        rc, out = results.pop(control)
+        assert rc == 0, f"the unmutated oracle ({control}) must pass the pins:\n" + out
     survivors = [name for name, (rc, _) in results.items() if rc == 0]
     assert not survivors, f"mistakes no pin catches: {survivors}"
     # the pins failed (exit 1), they did not error out (exit 2+: collection or internal errors)

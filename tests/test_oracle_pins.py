@@ -71,7 +71,8 @@ def test_time_term_closed_form():
 #    line against every cell box, entry edges, and (paper layout) A = l w equal to the exact band-cell area.
 # ------------------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("layout", [0, 1])
-@pytest.mark.parametrize("nx,ny,lx,ly,sp", [(3, 3, 3.0, 3.0, 0.45), (5, 4, 2.5, 1.0, 0.13), (2, 1, 1.0, 0.7, 0.3)])
+@pytest.mark.parametrize("nx,ny,lx,ly,sp", [(3, 3, 3.0, 3.0, 0.45), (5, 4, 2.5, 1.0, 0.13), (2, 1, 1.0, 0.7, 0.3),
+                                             (2, 2, 2.0, 2.0, 0.04)])   # bands halved several times
 def test_tracks_match_brute_force(layout, nx, ny, lx, ly, sp):
     q = synth.product_quadrature(1, 12)
     geom = make_geom(nx, ny, lx, ly, q, sp, layout=layout, renorm=0)
@@ -356,6 +357,18 @@ def test_grey_coefficients_special_cases():
     r1 = oracle.grey_coefficients(E[:1], Fx[:1], Fy[:1], kg[:1], B[:1])
     assert np.allclose(r1["kappa_E"], kg[0], rtol=2e-16, atol=0)
     assert np.all(np.abs(r1["eta_y"]) <= 4e-16 * kg[0] * np.abs(Fy[0]) / E[0])
+
+
+def test_grey_coefficients_hand_worked():
+    """Eqs. 8-9 on one cell with three groups whose B, E and flux spectra differ (worked by hand): kappa = (2, 5, 7),
+    B only in group 0, E only in group 1, F_x = (1, 0, -3), F_y = (0, -2, 0).  <kappa>_B = 2, <kappa>_E = 5;
+    K_Rx = (2 * 1 + 7 * 3) / 4 = 5.75, K_Ry = 5; eta_x = (2 * 1 - 7 * 3 - 5.75 * (1 - 3)) / 4 = -1.875, eta_y = 0.
+    Every weight tells the averages apart, so one taken with another group's weights fails here."""
+    col = lambda *v: np.array(v, dtype=np.float64)[:, None]
+    r = oracle.grey_coefficients(col(0, 4, 0), col(1, 0, -3), col(0, -2, 0), col(2, 5, 7), col(1, 0, 0))
+    want = dict(kappa_B=2.0, kappa_E=5.0, KRx=5.75, KRy=5.0, eta_x=-1.875, eta_y=0.0)
+    for k, v in want.items():
+        assert r[k][0] == v, (k, r[k][0], v)
 
 
 def test_grey_eddington_average_special_cases():
