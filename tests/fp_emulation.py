@@ -4,8 +4,8 @@ They restate, in numpy, the arithmetic of a sweep that carries the deviation psi
 characteristic (Sec. 3, Eqs. 11-13 rewritten exactly: Ibar = S + (I_s - S) E1, I_{s+1} = S + (I_s - S) e^-tau):
 
 * `emulate(..., "fp32")`: every operation rounded to IEEE binary32 in the order a GB300 FP32 path evaluates it,
-  with 2^x and 1/x correctly rounded (the hardware approximations are bounded separately), B split in two
-  FP32 words, and the state in units scaled by a power of two;
+  with 2^x and 1/x correctly rounded or (`approx`) given a relative error up to the hardware approximations'
+  stated accuracy, B split in two FP32 words, and the state in units scaled by a power of two;
 * `emulate(..., "fp64")`: every operation in binary64, with numpy's exp/expm1.
 
 They walk the oracle's own characteristic grid in its canonical order and return the segment-average
@@ -43,9 +43,11 @@ def _fma64(a, b, c):
     return s + (t + e)
 
 
-def emulate(tr, mu, kappa, B, c, dt, bnd, prec, dev_prev=None, Bref=None):
+def emulate(tr, mu, kappa, B, c, dt, bnd, prec, dev_prev=None, Bref=None, approx=None):
     """One sweep; tr = oracle.tracks(geometry); mu [ndir]; kappa, B [G][ncell]; bnd [4][G]; dev_prev: canonical
-    [nseg][G] stored deviations from Bref (None: 0, i.e. I^{n-1} = B); Bref [G][ncell] (None: B).  Returns the new
+    [nseg][G] stored deviations from Bref (None: 0, i.e. I^{n-1} = B); Bref [G][ncell] (None: B).  approx (FP32
+    only): (rel_ex2, rel_rcp, seed) to give every 2^x and 1/x a relative error of +-rel (seeded signs) before
+    its rounding to binary32, as the hardware approximations may; None: correctly rounded.  Returns the new
     canonical deviations from B (float64 array of the path's values)."""
     kappa = np.asarray(kappa, np.float64)
     B = np.asarray(B, np.float64)
@@ -67,6 +69,13 @@ def emulate(tr, mu, kappa, B, c, dt, bnd, prec, dev_prev=None, Bref=None):
         dB = (_r32((Bref - B) * sc) * r).astype(f32)
         minus_log2e = f32(-1.4426950408889634)
         c5040, c120, c6 = f32(1.0 / 5040.0), f32(1.0 / 120.0), f32(1.0 / 6.0)
+    if approx is not None:
+        rel_ex2, rel_rcp, seed = approx
+        rng = np.random.default_rng(seed)
+        perturb = lambda v, rel: v * (1.0 + rel * rng.choice((-1.0, 1.0), size=np.shape(v)))
+    else:
+        perturb = lambda v, rel: v
+        rel_ex2 = rel_rcp = 0.0
     seg = 0
     for m in range(mu.size):
         sinz = np.sqrt(1.0 - mu[m] * mu[m])
@@ -91,10 +100,10 @@ def emulate(tr, mu, kappa, B, c, dt, bnd, prec, dev_prev=None, Bref=None):
                 if prec == "fp32":
                     jump = (_r32(bh_prev - bhi[:, i]) + _r32(bl_prev - blo[:, i])).astype(f32)
                     kl = (kt[:, i] * _r32(tr["len"][q])).astype(f32)
-                    rkl = _r32(1.0 / kl.astype(np.float64))
+                    rkl = _r32(perturb(1.0 / kl.astype(np.float64), rel_rcp))
                     psi = (psi + jump).astype(f32)
                     a = (kl * half_inv_sinz).astype(f32)
-                    h = _r32(np.exp2((a * minus_log2e).astype(np.float64)))
+                    h = _r32(perturb(np.exp2((a * minus_log2e).astype(np.float64)), rel_ex2))
                     ex = (h * h).astype(f32)
                     y = (a * a).astype(f32)
                     p = _fma32(y, c5040, c120)

@@ -39,6 +39,26 @@ def test_bound_holds_for_emulated_path_over_two_steps(prec, name, seed):
     assert max(used) > 1e-3, used
 
 
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bound_holds_with_the_hardware_approximations_at_their_allowances(seed):
+    """The FP32 path computes 2^x with ex2.approx and 1/x with rcp.approx; the bound allows them relative errors of
+    2^-21 and 2^-22 (above the accuracies the PTX ISA gives them).  The emulation with every 2^x and 1/x off by those
+    allowances (seeded signs) must stay within it over two steps; a bound that left the approximations' error out
+    is exceeded here (by a quarter, measured on a mutant of the oracle)."""
+    wl, d, geom = _case("fc16_g4_d32", 3)
+    tr = oracle.tracks(geom)
+    em = error_model.model("fp32", wl.n_polar, d["B"], d["bnd"])
+    dev_o = dev_e = err = None
+    for step in range(2):
+        ref = oracle.sweep(geom, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], I_prev=dev_o, I_as_deviation=True,
+                           I_prev_is_deviation=True, errmodel=em, I_err=err)
+        emu = fp_emulation.emulate(tr, geom.mu, d["kappa"], d["B"], d["c"], d["dt"], d["bnd"], "fp32",
+                                   dev_prev=dev_e, approx=(2.0 ** -21, 2.0 ** -22, 100 * seed + step))
+        e = np.abs(emu - ref["I"])
+        assert np.all(e <= ref["I_err"]), (step, float(np.max(e / np.maximum(ref["I_err"], 1e-300))))
+        dev_o, dev_e, err = ref["I"], emu, ref["I_err"]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_bound_with_too_small_unit_roundoff_is_violated(prec):
     """A planted mistake in the model (u 64 times too small, the intrinsic errors likewise) must be caught by the

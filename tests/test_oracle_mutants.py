@@ -3,8 +3,9 @@
 Each mutant is a copy of the oracle with one planted mistake of the kind a restatement of Secs. 2-3 could make: a
 dropped term, a wrong sign, a transposed component, a wrong index or weight.  Mutants of oracle/molc_oracle.cpp
 are compiled on their own and the pin suites (tests/test_oracle_pins.py, tests/test_golden_single_ray.py) run
-against them in a subprocess (MOLC_ORACLE_LIB); mutants of oracle/__init__.py (the closure and grey averages) run
-the same suites from a copied tree.  Each must fail at least one pin.  Control copies with no mistake, built and
+against them in a subprocess (MOLC_ORACLE_LIB); mutants of its running error bound run against the bound's pins
+(tests/test_error_bound.py); mutants of oracle/__init__.py (the closure and grey averages) run the pin suites
+from a copied tree.  Each must fail at least one pin.  Control copies with no mistake, built and
 run the same ways, must pass them all, so a failure is the mistake's and not the harness's.
 """
 import os
@@ -61,6 +62,23 @@ MUTANTS = {
     "time_term_without_c": ("const R inv_cdt = R(1) / (R(c) * R(dt));", "const R inv_cdt = R(1) / R(dt);"),
 }
 
+# mistakes in the oracle's running error bound (oracle_errmodel) that make the bound too small, run against
+# its pins (tests/test_error_bound.py: emulations of the paths' arithmetic must stay within it)
+PINS_ERR = ["tests/test_error_bound.py"]
+ERR_MUTANTS = {
+    # the error a segment average inherits from the intensity entering the segment left out
+    "bar_without_carried_error": ("b.bar = E1 * eps_in + (1 - E1) * eps_d", "b.bar = (1 - E1) * eps_d"),
+    # the entering intensity's error not transmitted to the outgoing one (thin segments)
+    "out_without_incoming_error": ("const double out_thin = e * eps_in + om * eps_d",
+                                   "const double out_thin = om * eps_d"),
+    # the stored state's error not carried into the next step's source
+    "state_error_not_carried": (
+        "? u * (3 * std::fabs(dstate * rr) + 5 * std::fabs((Br - Bc) * rr) + std::fabs(dd)) + rr * eps_state",
+        "? u * (3 * std::fabs(dstate * rr) + 5 * std::fabs((Br - Bc) * rr) + std::fabs(dd))"),
+    # the error of the hardware 2^x approximation left out of e^-tau
+    "ex2_error_ignored": ("const double rh = 3.5 * u * tau + em.e_exp;", "const double rh = 3.5 * u * tau;"),
+}
+
 # the same for the oracle's Python part (oracle/__init__.py): name -> (exact text, the mistaken text)
 PY_MUTANTS = {
     # Eq. 7: f_xy = N_xy / E, without c
@@ -92,9 +110,9 @@ def _compile(src_text, out_dir, name):
     return so
 
 
-def _run_pins(so, root=ROOT):
+def _run_pins(so, root=ROOT, suites=PINS):
     env = dict(os.environ, MOLC_ORACLE_LIB=so)
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS], cwd=root,
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *suites], cwd=root,
                        env=env, capture_output=True, text=True, timeout=600)
     return r.returncode, r.stdout[-2000:]
 
@@ -116,13 +134,16 @@ def _py_tree(py_text, out_dir, name):
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     src = open(SRC).read()
     variants = {"control": src}
-    for name, (old, new) in MUTANTS.items():
-        assert src.count(old) == 1, name       # the text to mutate is where the pins expect it, once
-        variants[name] = src.replace(old, new)
+    suites = {"control": PINS + PINS_ERR}
+    for table, pins in ((MUTANTS, PINS), (ERR_MUTANTS, PINS_ERR)):
+        for name, (old, new) in table.items():
+            assert src.count(old) == 1, name       # the text to mutate is where the pins expect it, once
+            variants[name] = src.replace(old, new)
+            suites[name] = pins
     workers = max(1, min(len(variants), os.cpu_count() or 1))
     with ThreadPoolExecutor(workers) as ex:
         libs = dict(zip(variants, ex.map(lambda kv: _compile(kv[1], str(tmp_path), kv[0]), variants.items())))
-        results = dict(zip(libs, ex.map(_run_pins, libs.values())))
+        results = dict(zip(libs, ex.map(lambda n: _run_pins(libs[n], suites=suites[n]), libs)))
         # the Python mutants run against the control's library from trees of their own
         py_src = open(os.path.join(ROOT, "oracle", "__init__.py")).read()
         trees = {}
