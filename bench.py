@@ -68,7 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the sweeps (warmup + steps) in --precision, for profiler captures")
-    ap.add_argument("--tiled", action="store_true", help="--workload batch64: plans with the tiled FP32 sweep")
+    ap.add_argument("--tiled", action="store_true",
+                    help="--workload batch64 and --kernel-only: plans with the tiled FP32 sweep")
     ap.add_argument("--no-batch", action="store_true", help="leave the batched pattern out of the default line")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the --kernel-only sweeps (fp64: also the device's FP64 FMA rate)")
@@ -492,7 +493,7 @@ def run_kernel_only(args):
     import paper_2305_11998_gb300 as molc
     wl = synth.WORKLOADS[args.workload]
     d = wl.inputs(seed=0)
-    P = molc.Plan.from_workload(wl)
+    P = molc.Plan.from_workload(wl, tiled=args.tiled)
     dev = torch.device("cuda")
     prec = args.precision
     k, B, bnd = (torch.tensor(d[x], device=dev) for x in ("kappa", "B", "bnd"))
@@ -505,7 +506,7 @@ def run_kernel_only(args):
     for _ in range(args.steps):
         P.sweep(prec, k, B, wl.c, wl.dt, I, bnd, out=out)
     parts, n = P.kernel_time_parts()
-    line = {"workload": wl.name, "precision": prec, "launches": n,
+    line = {"workload": wl.name, "precision": prec, "tiled": P.info.fp32_tile_items > 0, "launches": n,
             "kernel_ms": {k_: v / max(n, 1) for k_, v in parts.items()}, "updates": P.info.n_updates,
             "device_status": P.device_status()}
     if prec == "fp64":
