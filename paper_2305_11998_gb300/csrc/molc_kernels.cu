@@ -359,37 +359,45 @@ __device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsign
 
 // Asynchronous copies (cp.async, sm_80+) of NP consecutive FP32 deviations from global to shared memory:
 // 16-byte pieces where NP * 4 bytes allow, else 8- or 4-byte pieces (the thread's deviations start at a multiple
-// of NP * 4 bytes of a 256-byte aligned state).
+// of NP * 4 bytes of a 256-byte aligned state).  The streamed state is read with the L2 policy `pol`
+// (evict-first), so that it does not push the cell tables and segment records out of L2.
 template <int NP>
-__device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src) {
+__device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src, unsigned long long pol) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   if constexpr (NP % 4 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 4)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
+      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
   } else if constexpr (NP % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < NP; i += 2)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
   } else {
 #pragma unroll
     for (int i = 0; i < NP; ++i)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4 * i), "l"(src + i) : "memory");
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d + 4 * i), "l"(src + i),
+                   "l"(pol)
+                   : "memory");
   }
 }
 // Warp-cooperative forms for odd NP: the 32 threads of a warp hold 32 x NP consecutive floats of a bundle step
 // slot (128 NP bytes, 16-byte aligned), moved as 8 NP pieces of 16 bytes by the first 8 NP lanes (one
 // instruction per lane for NP <= 4) instead of NP scalar accesses per thread.
 template <int NP>
-__device__ __forceinline__ void copy_warp_chunk_async(float *dst_smem, const float *src, int lane) {
+__device__ __forceinline__ void copy_warp_chunk_async(float *dst_smem, const float *src, int lane,
+                                                      unsigned long long pol) {
   constexpr int kPieces = 8 * NP;
 #pragma unroll
   for (int j = 0; j < (kPieces + 31) / 32; ++j) {
     const int k = lane + 32 * j;
     if (k < kPieces)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
                        (unsigned)__cvta_generic_to_shared(dst_smem + 4 * k)),
-                   "l"(src + 4 * k)
+                   "l"(src + 4 * k), "l"(pol)
                    : "memory");
   }
 }
@@ -524,10 +532,10 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
 #pragma unroll
   for (int k = 0; k < kSteps - 1; ++k) {
     if constexpr (COOP) {
-      if (k < nmax) copy_warp_chunk_async<NP>(&sdev[k][wofs], Iw + k * stride, lane);
+      if (k < nmax) copy_warp_chunk_async<NP>(&sdev[k][wofs], Iw + k * stride, lane, pol_stream);
     }
     if (k < nseg) {
-      if constexpr (!COOP) copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride);
+      if constexpr (!COOP) copy_dev_async<NP>(&sdev[k][tid * NP], I + k * stride, pol_stream);
       if (k < kSteps - 2) {
         copy16_async(&stab[k][tid], cd + (int64_t)recs[k].x * L.gc);
         copy4_async(&sdB[k][tid], cdB + (int64_t)recs[k].x * L.gc);
@@ -555,10 +563,11 @@ __device__ __forceinline__ void sweep_fp32_body(const PlanView &v, const SweepAr
         if constexpr (COOP) {
           __syncwarp();   // every lane is done with the slot refilled here (read at step s-1)
           if (s + kSteps - 1 < nmax)
-            copy_warp_chunk_async<NP>(&sdev[(u + kSteps - 1) % kSteps][wofs], Iw + (kSteps - 1) * stride, lane);
+            copy_warp_chunk_async<NP>(&sdev[(u + kSteps - 1) % kSteps][wofs], Iw + (kSteps - 1) * stride, lane,
+                                      pol_stream);
         } else {
           if (s + kSteps - 1 < nseg)
-            copy_dev_async<NP>(&sdev[(u + kSteps - 1) % kSteps][tid * NP], I + (kSteps - 1) * stride);
+            copy_dev_async<NP>(&sdev[(u + kSteps - 1) % kSteps][tid * NP], I + (kSteps - 1) * stride, pol_stream);
         }
         if (s + kSteps - 2 < nseg) {
           const int c2 = recs[(u + kSteps - 2) % kSteps].x;
