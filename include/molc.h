@@ -58,7 +58,10 @@ typedef enum { MOLC_RAYS_UNIFORM = 0, MOLC_RAYS_PAPER = 1 } molc_layout;
 /* flags for molc_create */
 #define MOLC_AREA_RENORM 1u /* scale A_{k,s} per (cell, azimuth) so that sum over C(i,m) of A = cell area */
 #define MOLC_HOST_ONLY 2u   /* build the characteristic grid on the host only (no device memory, no GPU needed):
-                               only molc_plan_get_info, molc_tracks_export and molc_destroy accept such a plan */
+                               only molc_plan_get_info, molc_intensity_count, molc_intensity_bytes,
+                               molc_tracks_export, molc_plan_retile (the tiles are re-cut on the host) and
+                               molc_destroy accept such a plan; every other call that takes it returns
+                               MOLC_ERR_INVALID_ARG */
 #define MOLC_FACES 8u       /* also accumulate the face moments of Eq. 16 in every molc_sweep (device memory for
                                6 FP64 sums per (face, group); FP64 reductions per segment, so sweeps are slower);
                                read them with molc_face_moments */

@@ -2102,6 +2102,7 @@ void molc_batch_destroy(molc_batch *b) {
 
 molc_status molc_ray_balance(const molc_plan *p, double *max_rel_residual) {
   if (!p || !max_rel_residual) return fail(MOLC_ERR_INVALID_ARG, "ray_balance: NULL argument");
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "ray_balance: the plan was created with MOLC_HOST_ONLY");
   if (!p->d_balance) return fail(MOLC_ERR_INVALID_ARG, "ray_balance: the plan was created without MOLC_BALANCE");
   DeviceGuard dg(p->device);
   unsigned long long bits = 0;
@@ -2236,6 +2237,7 @@ molc_status molc_kernel_timing(molc_plan *p, int enable) {
 
 molc_status molc_kernel_time_parts(molc_plan *p, double *parts_ms, int *launches) {
   if (!p || !parts_ms || !launches) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: NULL argument");
+  if (p->host_only) return fail(MOLC_ERR_INVALID_ARG, "kernel_time: the plan was created with MOLC_HOST_ONLY");
   DeviceGuard dg(p->device);
   double tot[3] = {0, 0, 0};
   if (p->n_timed > 0) {

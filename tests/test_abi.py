@@ -112,3 +112,51 @@ def test_balance_check_does_not_combine_with_face_moments():
         molc.Plan.from_workload(wl, host_only=True, faces=True, balance=True)
     P = molc.Plan.from_workload(wl, host_only=True, balance=True)
     P.close()
+
+
+def test_host_only_plans_are_refused_by_device_calls():
+    """A MOLC_HOST_ONLY plan holds nothing on a device: every call that would touch one returns
+    MOLC_ERR_INVALID_ARG naming MOLC_HOST_ONLY, before any CUDA call (the arguments are host buffers that are never
+    read); the host calls accept it."""
+    import ctypes as C
+    from paper_2305_11998_gb300 import molc as mm
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    P = molc.Plan.from_workload(wl, host_only=True, tiled=True)
+    lib = molc.load()
+    buf = np.zeros(1 << 16)                      # host memory standing in for every device array
+    ptr = C.c_void_p(buf.ctypes.data)
+    mom = mm._Moments(*([buf.ctypes.data] * len(mm.MOMENTS)))
+    d, n = C.c_double(), C.c_int()
+    parts = (C.c_double * 3)()
+    calls = {
+        "intensity_init": lambda: lib.molc_intensity_init(P._h, 1, ptr, ptr, None),
+        "sweep": lambda: lib.molc_sweep(P._h, 1, ptr, ptr, 1.0, 1.0, ptr, ptr, C.byref(mom), None),
+        "sweep_closure": lambda: lib.molc_sweep_closure(P._h, 0, ptr, ptr, 1.0, 1.0, ptr, ptr, C.byref(mom), ptr,
+                                                        ptr, ptr, None),
+        "sweep_static_scratch": lambda: lib.molc_sweep_static_scratch(P._h, 1, ptr, ptr, 1.0, 1.0, ptr, ptr,
+                                                                      C.byref(mom), None),
+        "closure": lambda: lib.molc_closure(P._h, C.byref(mom), 1.0, ptr, ptr, ptr, None, None),
+        "grey_coefficients": lambda: lib.molc_grey_coefficients(P._h, C.byref(mom), ptr, ptr, ptr, None),
+        "face_moments": lambda: lib.molc_face_moments(P._h, 0, ptr, 1.0, C.byref(mom), None),
+        "intensity_export": lambda: lib.molc_intensity_export(P._h, 1, ptr, 0, 1, ptr, None),
+        "intensity_import": lambda: lib.molc_intensity_import(P._h, 0, ptr, 0, 1, ptr, ptr, None),
+        "ray_balance": lambda: lib.molc_ray_balance(P._h, C.byref(d)),
+        "kernel_timing": lambda: lib.molc_kernel_timing(P._h, 1),
+        "kernel_time": lambda: lib.molc_kernel_time(P._h, C.byref(d), C.byref(n)),
+        "kernel_time_parts": lambda: lib.molc_kernel_time_parts(P._h, parts, C.byref(n)),
+        "device_status": lambda: lib.molc_device_status(P._h, C.byref(n)),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
+        assert b"MOLC_HOST_ONLY" in lib.molc_last_error(), (name, lib.molc_last_error())
+    plans = (C.c_void_p * 1)(P._h)
+    out = C.c_void_p()
+    assert lib.molc_batch_create(plans, 1, C.byref(out)) == 1 and not out.value
+    assert b"MOLC_HOST_ONLY" in lib.molc_last_error()
+    # the host calls
+    assert P.intensity_count() == P.info.n_updates
+    assert lib.molc_intensity_bytes(P._h, 1) > 0 and lib.molc_intensity_bytes(P._h, 0) > 0
+    assert P.tracks()["cell"].size == P.info.n_segments
+    P.retile(tile_cells=4)
+    assert P.info.fp32_tile_cells == 4
+    P.close()
