@@ -189,8 +189,9 @@ molc_status molc_intensity_init(molc_plan *plan, molc_precision prec, void *I, c
  * place by this step's Ibar.  Entering intensity: bnd[edge][g] (isotropic per edge; edges left, right,
  * bottom, top).  Writes the cell moments E, Fx, Fy, Nxx, Nxy, Nyy of every group into *out (the areas
  * A = l w of Eq. 14 weight the segment averages).
- *   prec   MOLC_FP64: all arithmetic in FP64.  MOLC_FP32: segment arithmetic in FP32, moment accumulation and
- *          the cell assembly in FP64.
+ *   prec   MOLC_FP64: all arithmetic in FP64.  MOLC_FP32: segment arithmetic in FP32; each cell's moment sums
+ *          in FP32 within runs of at most 8 segments of one azimuth pair and as two-word FP32 sums (hi + lo,
+ *          about 48 significant bits) across the runs, then the cell assembly in FP64.
  *   kappa, B  device [G][cell] FP64;  c (cm/sh) > 0, dt (sh) > 0;  I: device state of precision prec;
  *   bnd    device [4][G] FP64;  out: device pointers, each [G][cell] FP64, overwritten.
  * Asynchronous on `stream`; no allocation. */
