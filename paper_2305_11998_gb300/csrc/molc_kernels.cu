@@ -1466,10 +1466,12 @@ cudaError_t launch_set_scale(const PlanView &v, molc_precision prec, const doubl
 // ---------------------------------------------------------------------------------------------------------
 // FP64 FMA throughput of this GPU (the bound of the plain FP64 sweep, which spends its time in FP64 exp/expm1
 // and FP64 atomics): every thread runs kFmaChains independent chains of kFmaIters dependent FMAs, so the FP64
-// pipe, not latency, limits the rate.  The result is written so that the work cannot be dropped.
+// pipe, not latency, limits the rate.  The chains' sum is compared with a value it never takes and stored, if it
+// did, to a static device variable, so that the work cannot be dropped and no pointer is needed.
 // ---------------------------------------------------------------------------------------------------------
 constexpr int kFmaChains = 8, kFmaIters = 4096;
-__global__ void __launch_bounds__(256) fp64_fma_kernel(double *sink, double a, double b) {
+__device__ double g_fma_sink;
+__global__ void __launch_bounds__(256) fp64_fma_kernel(double a, double b) {
   double x[kFmaChains];
 #pragma unroll
   for (int k = 0; k < kFmaChains; ++k) x[k] = threadIdx.x * 1e-3 + k;
@@ -1480,7 +1482,7 @@ __global__ void __launch_bounds__(256) fp64_fma_kernel(double *sink, double a, d
   double s = 0;
 #pragma unroll
   for (int k = 0; k < kFmaChains; ++k) s += x[k];
-  if (s == 12345.678) sink[0] = s;   // never true for the arguments used; keeps the chains live
+  if (s == 12345.678) g_fma_sink = s;   // never true for the arguments used; keeps the chains live
 }
 
 cudaError_t fp64_fma_rate(double *flops_per_s) {
@@ -1495,7 +1497,7 @@ cudaError_t fp64_fma_rate(double *flops_per_s) {
   float best = 0.f;
   for (int rep = 0; e == cudaSuccess && rep < 4; ++rep) {   // first run warms up; best of the other three
     cudaEventRecord(e0, 0);
-    fp64_fma_kernel<<<blocks, threads>>>(nullptr, 0.999999, 1e-7);
+    fp64_fma_kernel<<<blocks, threads>>>(0.999999, 1e-7);
     cudaEventRecord(e1, 0);
     e = cudaEventSynchronize(e1);
     if (e == cudaSuccess) e = cudaGetLastError();
