@@ -357,31 +357,46 @@ __device__ __forceinline__ void store_dev(float *p, const float (&v)[NP], unsign
   }
 }
 
+// One cp.async of `bytes` (4, 8 or 16) from global to shared memory; with the L2 policy `pol` when HINT.  The
+// hinted form is used only where every copy's address is formed in registers with no constant offset folded into
+// the instruction (up to 4 polar cosines: one copy per thread or one piece per lane); the other polar counts copy
+// several pieces at constant offsets from one address and take the plain form.
+template <bool HINT, int BYTES>
+__device__ __forceinline__ void cp_async_piece(unsigned dst, const float *src, unsigned long long pol) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async copies 4, 8 or 16 bytes");
+  if constexpr (HINT) {
+    if constexpr (BYTES == 16)
+      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                   : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], %2, %3;" ::"r"(dst), "l"(src),
+                   "n"(BYTES), "l"(pol)
+                   : "memory");
+  } else {
+    if constexpr (BYTES == 16)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+  }
+}
+
 // Asynchronous copies (cp.async, sm_80+) of NP consecutive FP32 deviations from global to shared memory:
 // 16-byte pieces where NP * 4 bytes allow, else 8- or 4-byte pieces (the thread's deviations start at a multiple
 // of NP * 4 bytes of a 256-byte aligned state).  The streamed state is read with the L2 policy `pol`
-// (evict-first), so that it does not push the cell tables and segment records out of L2.
+// (evict-first), so that it does not push the cell tables and segment records out of L2 (up to 4 polar cosines).
 template <int NP>
 __device__ __forceinline__ void copy_dev_async(float *dst_smem, const float *src, unsigned long long pol) {
+  constexpr bool kHint = NP <= 4;
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
   if constexpr (NP % 4 == 0) {
 #pragma unroll
-    for (int i = 0; i < NP; i += 4)
-      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+    for (int i = 0; i < NP; i += 4) cp_async_piece<kHint, 16>(d + 4 * i, src + i, pol);
   } else if constexpr (NP % 2 == 0) {
 #pragma unroll
-    for (int i = 0; i < NP; i += 2)
-      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+    for (int i = 0; i < NP; i += 2) cp_async_piece<kHint, 8>(d + 4 * i, src + i, pol);
   } else {
 #pragma unroll
-    for (int i = 0; i < NP; ++i)
-      asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;" ::"r"(d + 4 * i), "l"(src + i),
-                   "l"(pol)
-                   : "memory");
+    for (int i = 0; i < NP; ++i) cp_async_piece<kHint, 4>(d + 4 * i, src + i, pol);
   }
 }
 // Warp-cooperative forms for odd NP: the 32 threads of a warp hold 32 x NP consecutive floats of a bundle step
@@ -391,14 +406,12 @@ template <int NP>
 __device__ __forceinline__ void copy_warp_chunk_async(float *dst_smem, const float *src, int lane,
                                                       unsigned long long pol) {
   constexpr int kPieces = 8 * NP;
+  constexpr bool kHint = NP <= 4;
 #pragma unroll
   for (int j = 0; j < (kPieces + 31) / 32; ++j) {
     const int k = lane + 32 * j;
     if (k < kPieces)
-      asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(
-                       (unsigned)__cvta_generic_to_shared(dst_smem + 4 * k)),
-                   "l"(src + 4 * k), "l"(pol)
-                   : "memory");
+      cp_async_piece<kHint, 16>((unsigned)__cvta_generic_to_shared(dst_smem + 4 * k), src + 4 * k, pol);
   }
 }
 template <int NP>
