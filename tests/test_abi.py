@@ -64,6 +64,23 @@ def test_planner_matches_oracle_tracks(name, layout):
     P.close()
 
 
+def test_threaded_planner_matches_oracle_tracks():
+    """A grid large enough (cells x azimuth pairs >= 2^17) that molc_create traces the azimuth pairs and sums their
+    areas on several host threads: the same characteristic grid as the oracle's own generator."""
+    wl = synth.Workload("grid128", 128, 128, 6.0, 2, 0.001, 100.0, 2, 32, 2, 1)
+    P = molc.Plan.from_workload(wl, host_only=True)
+    assert wl.ncell * P.info.n_azim_pairs >= 1 << 17
+    tr = P.tracks()
+    ref = oracle.tracks(oracle.Geometry.from_workload(wl, spacing=wl.spacing, layout=0, renorm=1), "quad")
+    for k in ("dir_ray_off", "ray_seg_off", "entry", "cell"):
+        assert np.array_equal(tr[k], ref[k]), k
+    L = wl.L
+    assert np.max(np.abs(tr["width"] - ref["width"])) < 1e-14 * L
+    assert np.max(np.abs(tr["len"] - ref["len"])) < 1e-14 * L
+    assert np.max(np.abs(tr["area"] - ref["area"])) < 1e-14 * L * wl.h
+    P.close()
+
+
 def test_invalid_arguments_are_rejected():
     q = synth.product_quadrature(2, 8)
     with pytest.raises(molc.MolcError) as e:
