@@ -60,6 +60,27 @@ MUTANTS = {
                          "while (gap / (double)pieces > g.spacing) pieces += 1;"),
     # Eq. 11: 1/(c dt) with c left out
     "time_term_without_c": ("const R inv_cdt = R(1) / (R(c) * R(dt));", "const R inv_cdt = R(1) / R(dt);"),
+    # Eq. 13: alpha with the sign of its second term flipped
+    "alpha_sign": ("const R alpha = R(1) / tau - e / one_m_e;", "const R alpha = R(1) / tau + e / one_m_e;"),
+    # Eq. 12: the source term Q not divided by kappa~
+    "source_not_over_kappa_tilde": ("const R Iout = I * e + (Q / kt) * one_m_e;",
+                                    "const R Iout = I * e + Q * one_m_e;"),
+    # boundary condition: a characteristic entering through a vertical edge given the opposite edge's intensity
+    "entry_edge_x_swapped": ("ray.entry = xedge ? (dx > R(0) ? EDGE_L : EDGE_R)",
+                             "ray.entry = xedge ? (dx > R(0) ? EDGE_R : EDGE_L)"),
+    # Eq. 11: a previous state given as deviations from B used without adding B back
+    "previous_deviation_without_B": ("const R Iprev = I_prev ? (prev_dev ? B_i + R(I_prev[seg * Gsub + gi])",
+                                     "const R Iprev = I_prev ? (prev_dev ? R(I_prev[seg * Gsub + gi])"),
+    # Eq. 13: sin(zeta) from mu instead of mu^2
+    "sin_zeta_mu_not_squared": ("const R sinz = Fn<R>::sqrt(R(1) - mu * mu);",
+                                "const R sinz = Fn<R>::sqrt(R(1) - mu);"),
+    # Eq. 11: the stored I^{n-1} the outgoing intensity instead of the segment average
+    "state_stores_outgoing_intensity": (
+        "if (I_new) I_new[seg * Gsub + gi] = store_dev ? (double)(Ibar - B_i) : (double)Ibar;",
+        "if (I_new) I_new[seg * Gsub + gi] = store_dev ? (double)(Iout - B_i) : (double)Iout;"),
+    # Eq. 15: the cell volume formed with the x side twice (wrong for cells that are not square)
+    "cell_volume_x_side_twice": ("const R V = R(g->lx / g->nx) * R(g->ly / g->ny);",
+                                 "const R V = R(g->lx / g->nx) * R(g->lx / g->nx);"),
 }
 
 # mistakes in the oracle's running error bound (oracle_errmodel) that make the bound too small, run against

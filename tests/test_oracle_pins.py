@@ -313,6 +313,31 @@ def test_double_vs_quad_and_bookkeeping():
     assert np.array_equal(rp["E"], rd1["E"])
 
 
+def test_previous_state_as_deviations_is_the_same_state():
+    """I^{n-1} of Eq. 11 carried as deviations from B of each segment's cell (the form the GPU paths store) is the
+    same previous state as its segment averages: the stored deviations of a step are its averages minus B of the
+    cell, and a second step, with B changed, gives the same moments from either form."""
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(seed=0)
+    geom = oracle.Geometry.from_workload(wl)
+    cell = oracle.tracks(geom, "double")["cell"]
+    args = (d["kappa"], d["B"], d["c"], d["dt"], d["bnd"])
+    r1 = oracle.sweep(geom, *args, precision="quad")
+    r1d = oracle.sweep(geom, *args, precision="quad", I_as_deviation=True)
+    Bseg = d["B"].T[cell]
+    scale = np.max(np.abs(r1["I"]))
+    assert np.max(np.abs(r1d["I"] - (r1["I"] - Bseg))) < 1e-15 * scale
+    B2 = d["B"] * np.linspace(0.5, 1.5, d["B"].shape[1])       # the temperature moved: B differs per cell
+    args2 = (d["kappa"], B2, d["c"], d["dt"], d["bnd"])
+    dev2 = r1["I"] - B2.T[cell]                                # the same averages, referred to this step's B
+    ra = oracle.sweep(geom, *args2, I_prev=r1["I"], precision="quad")
+    rd = oracle.sweep(geom, *args2, I_prev=dev2, I_prev_is_deviation=True, precision="quad")
+    cE = d["c"] * ra["E"]
+    for k in ("E", "Fx", "Fy", "Nxx", "Nxy", "Nyy"):
+        ref = cE if k in ("Fx", "Fy", "Nxy") else np.abs(ra[k])
+        assert np.max(np.abs(rd[k] - ra[k]) / ref) < 1e-13, k
+
+
 def test_multistep_relaxes_towards_steady_state():
     # With fixed material and boundary the backward-Euler steps approach the steady solution: the change
     # between steps shrinks geometrically (factor <= 1/(1 + c dt kappa_min)).
