@@ -81,6 +81,24 @@ MUTANTS = {
     # Eq. 15: the cell volume formed with the x side twice (wrong for cells that are not square)
     "cell_volume_x_side_twice": ("const R V = R(g->lx / g->nx) * R(g->ly / g->ny);",
                                  "const R V = R(g->lx / g->nx) * R(g->lx / g->nx);"),
+    # Eq. 15: N_yy accumulated with Omega_x Omega_y
+    "Nyy_with_Omega_x": ("a[MOM_NYY * ncell + i] += wA * Oy * Oy * Ibar;",
+                         "a[MOM_NYY * ncell + i] += wA * Ox * Oy * Ibar;"),
+    # Sec. 2: E without its factor 1/c
+    "E_without_1_over_c": ("const R scale = q == MOM_D ? R(1) / (R(c) * V) : R(1) / V;",
+                           "const R scale = R(1) / V;"),
+    # Eq. 14 with MOLC_AREA_RENORM's reading: the renormalisation factor inverted
+    "renormalisation_inverted": ("r.area[s] = r.area[s] * (V / sum[r.cell[s]]);",
+                                 "r.area[s] = r.area[s] * (sum[r.cell[s]] / V);"),
+    # Sec. 3 grid: the uniform layout's widths from n + 1 bands for n characteristics
+    "uniform_width_n_plus_1": ("double wk = Lp / (double)n;", "double wk = Lp / (double)(n + 1);"),
+    # boundary condition: a characteristic entering through a horizontal edge given the opposite edge's intensity
+    "entry_edge_y_swapped": ("(dy > R(0) ? EDGE_B : EDGE_T);", "(dy > R(0) ? EDGE_T : EDGE_B);"),
+    # Eq. 11: the emission kappa B formed with the previous intensity instead of B
+    "emission_with_previous_intensity": ("const R Q = kap_i * B_i + inv_cdt * Iprev;",
+                                         "const R Q = kap_i * Iprev + inv_cdt * Iprev;"),
+    # Eq. 16: the face averages over the other side's length
+    "face_length_swapped": ("const R len = f < nxf ? hy : hx;", "const R len = f < nxf ? hx : hy;"),
 }
 
 # mistakes in the oracle's running error bound (oracle_errmodel) that make the bound too small, run against
@@ -116,6 +134,14 @@ PY_MUTANTS = {
     # Eq. 9: eta_x formed with K_R's y component
     "eta_x_with_KRy": ("ex = np.where(se > 0, ((kappa - kx) * Fx).sum(0) / safe, 0.0)",
                        "ex = np.where(se > 0, ((kappa - ky) * Fx).sum(0) / safe, 0.0)"),
+    # Eq. 9: eta_x divided by the sum of B instead of the sum of E
+    "eta_x_over_B": ("ex = np.where(se > 0, ((kappa - kx) * Fx).sum(0) / safe, 0.0)",
+                     "ex = np.where(se > 0, ((kappa - kx) * Fx).sum(0) / np.where(B.sum(0) > 0, B.sum(0), 1.0), 0.0)"),
+    # Eq. 9: K_R's y component weighted by |F_x|
+    "KRy_with_Fx": ("kE, kB, kx, ky = avg(E), avg(B), avg(np.abs(Fx)), avg(np.abs(Fy))",
+                    "kE, kB, kx, ky = avg(E), avg(B), avg(np.abs(Fx)), avg(np.abs(Fx))"),
+    # Eq. 7: f_yy formed from N_xx
+    "closure_fyy_from_Nxx": ("fyy = np.asarray(Nyy) / cE", "fyy = np.asarray(Nxx) / cE"),
 }
 
 

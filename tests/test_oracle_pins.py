@@ -283,6 +283,12 @@ def test_closure_trace_and_bounds():
     assert np.max(np.abs((r["Nxx"] + r["Nyy"] + r["Nzz"]) / cE - 1)) < 1e-14
     fxx, fxy, fyy = oracle.closure(r["E"], r["Nxx"], r["Nxy"], r["Nyy"], d["c"])
     assert np.all((fxx >= 0) & (fxx <= 1) & (fyy >= 0) & (fyy <= 1) & (np.abs(fxy) <= 0.5))
+    # f_zz = 1 - f_xx - f_yy is the zz factor of the separately summed N_zz (Omega_x^2 + Omega_y^2 + mu^2 = 1), in
+    # cells where the field is far from isotropic in the plane as well as elsewhere
+    assert np.max(np.abs(1 - fxx - fyy - r["Nzz"] / cE)) < 1e-14
+    assert np.max(np.abs(fxx - fyy)) > 1e-3
+    # the tensor is symmetric positive semidefinite: f_xx f_yy >= f_xy^2
+    assert np.all(fxx * fyy - fxy * fxy >= -1e-14)
 
 
 # ------------------------------------------------------------------------------------------------------------
