@@ -99,6 +99,28 @@ MUTANTS = {
                                          "const R Q = kap_i * Iprev + inv_cdt * Iprev;"),
     # Eq. 16: the face averages over the other side's length
     "face_length_swapped": ("const R len = f < nxf ? hy : hx;", "const R len = f < nxf ? hx : hy;"),
+    # Eq. 16: N_xy of the faces with Omega_x^2
+    "face_Nxy_with_Omega_x_squared": ("fa[MOM_NXY * nf + f] += ww * Ox * Oy * I;",
+                                      "fa[MOM_NXY * nf + f] += ww * Ox * Ox * I;"),
+    # Sec. 3 grid: cell index i = ix ny + iy instead of iy nx + ix
+    "cell_index_transposed": ("ray.cell.push_back((int)(iy * g.nx + ix));",
+                              "ray.cell.push_back((int)(ix * g.ny + iy));"),
+    # Sec. 3 grid: a segment given to the cell of its start instead of the cell holding it
+    "segment_cell_at_its_start": ("R m = R(0.5) * (a + b);", "R m = a;"),
+    # Sec. 3 grid: the uniform layout's count rounded down (bands wider than the spacing)
+    "uniform_count_rounded_down": ("long n = (long)std::ceil(Lp / g.spacing - 1e-9);",
+                                   "long n = (long)std::floor(Lp / g.spacing);"),
+    # Sec. 3 grid: the paper layout's vertices projected on the wrong normal
+    "paper_projection_sign": ("auto proj = [&](double x, double y) { return -dy * x + dx * y; };",
+                              "auto proj = [&](double x, double y) { return dy * x + dx * y; };"),
+    # Sec. 3 grid: coincident vertex projections not merged (zero-width characteristics)
+    "paper_projections_not_merged": ("if (u.empty() || x - u.back() > merge) u.push_back(x);", "u.push_back(x);"),
+    # Eq. 16: a crossing in x given the face on the lower side of the step
+    "upwind_x_face_lower_index": (
+        "f = px != ix ? iy * (g.nx + 1) + std::max(px, ix) : nxf + std::max(py, iy) * g.nx + ix;",
+        "f = px != ix ? iy * (g.nx + 1) + std::min(px, ix) : nxf + std::max(py, iy) * g.nx + ix;"),
+    # Eq. 16: characteristics entering through the right edge given the left edge's faces
+    "entry_face_right_as_left": ("ray.entry == EDGE_R ? iy * (g.nx + 1) + g.nx", "ray.entry == EDGE_R ? iy * (g.nx + 1)"),
 }
 
 # mistakes in the oracle's running error bound (oracle_errmodel) that make the bound too small, run against
