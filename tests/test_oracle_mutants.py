@@ -138,6 +138,16 @@ ERR_MUTANTS = {
         "? u * (3 * std::fabs(dstate * rr) + 5 * std::fabs((Br - Bc) * rr) + std::fabs(dd))"),
     # the error of the hardware 2^x approximation left out of e^-tau
     "ex2_error_ignored": ("const double rh = 3.5 * u * tau + em.e_exp;", "const double rh = 3.5 * u * tau;"),
+    # the entering intensity's error not transmitted to the outgoing one (thick segments)
+    "thick_out_without_incoming_error": ("const double out_thick = e * eps_in + om * eps_d",
+                                         "const double out_thick = om * eps_d"),
+    # the roundings of the FP32 moment sums left out of the cell bound
+    "summation_term_dropped": ("ob[i] = (E + ksum * em->u * D + 8 * u64 * (D + P)) * scale;",
+                               "ob[i] = (E + 8 * u64 * (D + P)) * scale;"),
+    # the roundings of the FP32 cell table (the stored deviation and the B_ref step) left out of d
+    "table_roundings_dropped": (
+        "? u * (3 * std::fabs(dstate * rr) + 5 * std::fabs((Br - Bc) * rr) + std::fabs(dd)) + rr * eps_state",
+        "? u * std::fabs(dd) + rr * eps_state"),
 }
 
 # the same for the oracle's Python part (oracle/__init__.py): name -> (exact text, the mistaken text)
