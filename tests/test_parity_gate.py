@@ -122,3 +122,28 @@ def test_fp32_factors_held_to_their_absolute_tolerance(refs):
         assert df / f[g, i] < parity.TOL["fp32"]           # the moment alone passes its own check
         check = failing_check(got, r, "fp32", c)
         assert check == ("fxx" if fails else None), (df, check)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_carried_state_check(refs, prec):
+    """parity.check_state: the carried segment averages are held per segment, direction and group to the bound of
+    the path's state (plus the FP64 roundings of the absolute values); one value beyond it fails."""
+    wl = synth.WORKLOADS["fc16_g4_d32"]
+    d = wl.inputs(seed=0)
+    geom = oracle.Geometry.from_workload(wl)
+    r = parity.reference(geom, d, prec, wl.n_polar, want_I=True)
+    Bseg = d["B"].T[oracle.tracks(geom, "double")["cell"]]
+    dev, err = np.asarray(r["I"]), np.asarray(r["I_err"])
+    exact = dev + Bseg
+    assert parity.check_state(exact, dev, Bseg, err, prec)["state_bound_use"] <= 1.0
+    allow = err + 4 * parity.U64 * np.abs(exact)
+    s, g = np.unravel_index(np.argmax(allow), allow.shape)
+    for factor, fails in ((0.5, False), (2.0, True)):
+        got = exact.copy()
+        got[s, g] += factor * allow[s, g]
+        try:
+            parity.check_state(got, dev, Bseg, err, prec)
+            failed = False
+        except AssertionError:
+            failed = True
+        assert failed is fails, factor
